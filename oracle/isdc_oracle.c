@@ -1,0 +1,666 @@
+/*
+ * isdc_oracle.c -- plain, slow, obviously correct FP64 CPU oracle for
+ * inexact spectral deferred corrections (Speck, Ruprecht, Minion, Emmett,
+ * Krause, "Inexact spectral deferred corrections", arXiv:1401.7824).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may import, call, link or execute
+ * anything under oracle/.  The product path (the CUDA library) never does, and
+ * this file shares no code, header, table or helper with it.
+ *
+ * What it computes, step by step in the paper's order and notation:
+ *   - Gauss-Lobatto collocation nodes tau_1=0 < ... < tau_M=1 on [0,1] and the
+ *     integration matrices Q (Q[m][j] = int_0^{tau_m} l_j) and
+ *     S (node-to-node, S_m^{m+1} = Q_{m+1} - Q_m)            -- Sec. 2, Eq. 2
+ *   - the semi-implicit SDC sweep                             -- Sec. 2, Eq. 4
+ *       u_{m+1}^{k+1} = u_m^{k+1} + dt_m[f^I(u_{m+1}^{k+1}) - f^I(u_{m+1}^k)]
+ *                     + dt_m[f^E(u_m^{k+1}) - f^E(u_m^k)] + S_m^{m+1}F(u^k)
+ *     with f^I(u) = A u, A = nu * L_h (5-point 2D / 7-point 3D Laplacian,
+ *     zero Dirichlet ghosts, W = I in Eq. 5), and f^E(u) = u - u^3
+ *     (or none, or lambda_E*u for the Dahlquist order test);
+ *   - each implicit Euler solve (I - dt_m A) x = b done either exactly
+ *     (sine-transform diagonalisation: classical SDC with an exact spatial
+ *     solve, Sec. 3), by multigrid until a tolerance (classical SDC, Sec. 3),
+ *     or by L fixed V-cycles started from u_{m+1}^k (ISDC, Sec. 3 and Sec. 4.3);
+ *   - the max-norm SDC residual after every sweep               -- Sec. 3.
+ *
+ * The multigrid solver is not described in the paper (Acknowledgments); the
+ * one here is textbook geometric multigrid: vertex-centred coarsening
+ * n_c = (n-1)/2 down to side 3, rediscretised coarse operators I - a L_{2h},
+ * full-weighting restriction, (bi/tri)linear prolongation, one recursive call
+ * per level (V-cycle), zero coarse initial guess, exact dense solve on the
+ * side-3 grid, and either damped Jacobi or red-black Gauss-Seidel smoothing.
+ *
+ * Grid layout: interior points only, x fastest.  With 1-based interior
+ * indices i,j,k in 1..n the array index is (i-1) + n*((j-1) + n*(k-1)).
+ * h = 1/(n+1).  Everything is IEEE double, built with -ffp-contract=off.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_M 16
+
+/* ------------------------------------------------------------------------ */
+/* Problem description passed from Python (ctypes mirrors this layout).      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int    ndim;        /* 2 or 3 */
+    int    n;           /* interior points per side, 2^j - 1 */
+    double nu;          /* diffusion coefficient in f^I = nu L_h u */
+    int    M;           /* number of Gauss-Lobatto nodes, 2..ORC_MAX_M */
+    double dt;          /* time step Delta t */
+    int    reaction;    /* f^E: 0 none, 1 u - u^3, 2 lambda_e * u */
+    double lambda_e;    /* coefficient for reaction 2 */
+    int    smoother;    /* 0 damped Jacobi, 1 red-black Gauss-Seidel */
+    int    nu1, nu2;    /* pre- and post-smoothing sweeps */
+    double omega;       /* Jacobi damping */
+    int    solver;      /* 0 ISDC: L V-cycles; 1 classical: MG until mg_tol;
+                           2 classical: exact sine-transform solve */
+    int    guess;       /* multigrid start: 0 u_{m+1}^k (Sec. 4.3), 1 zero,
+                           2 u_m^{k+1} */
+    double tol;         /* SDC residual tolerance */
+    int    max_sweeps;  /* cap for the until-tolerance mode */
+    double mg_tol;      /* classical SDC: max-norm residual of the node solve */
+    int    mg_max_cycles;
+} orc_problem;
+
+/* ------------------------------------------------------------------------ */
+/* Legendre polynomials and quadrature nodes (Sec. 2: collocation nodes).   */
+/* ------------------------------------------------------------------------ */
+
+/* P_n(x) and P_n'(x) on [-1,1] by the three-term recurrence. */
+static void legendre(int n, double x, double *p, double *dp)
+{
+    double p0 = 1.0, p1 = x;
+    if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+    for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+    }
+    *p = p1;
+    /* (x^2 - 1) P_n'(x) = n (x P_n - P_{n-1}) */
+    *dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+/* Gauss-Legendre nodes/weights on [-1,1]: roots of P_n by Newton. */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre(n, z, &p, &dp);
+            double dz = p / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p, dp;
+        legendre(n, z, &p, &dp);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/*
+ * Gauss-Lobatto nodes on [0,1]: the end points plus the roots of P'_{M-1}
+ * mapped from [-1,1].  The roots of P'_{M-1} are found by Newton's method on
+ * P'_{M-1}, using P''_{M-1} from the Legendre ODE
+ * (1-x^2) P'' = 2x P' - n(n+1) P.
+ */
+int orc_lobatto_nodes(int M, double *tau)
+{
+    if (M < 2 || M > ORC_MAX_M) return 1;
+    int n = M - 1;
+    double z[ORC_MAX_M];
+    z[0] = -1.0;
+    z[M - 1] = 1.0;
+    for (int i = 1; i < M - 1; ++i) {
+        double x = -cos(M_PI * i / n); /* Chebyshev-Lobatto start */
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre(n, x, &p, &dp);
+            double d2p = (2.0 * x * dp - n * (n + 1.0) * p) / (1.0 - x * x);
+            double dx = dp / d2p;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        z[i] = x;
+    }
+    for (int i = 0; i < M; ++i) tau[i] = 0.5 * (z[i] + 1.0);
+    tau[0] = 0.0;
+    tau[M - 1] = 1.0;
+    return 0;
+}
+
+/* Lagrange basis polynomial l_j over the nodes tau, evaluated at s. */
+static double lagrange(int M, const double *tau, int j, double s)
+{
+    double v = 1.0;
+    for (int i = 0; i < M; ++i)
+        if (i != j) v *= (s - tau[i]) / (tau[j] - tau[i]);
+    return v;
+}
+
+/*
+ * Q[m][j] = int_0^{tau_m} l_j(s) ds (row-major, M x M).  l_j has degree M-1,
+ * so an M-point Gauss-Legendre rule on [0, tau_m] integrates it exactly.
+ */
+int orc_q_matrix(int M, const double *tau, double *Q)
+{
+    if (M < 2 || M > ORC_MAX_M) return 1;
+    double gx[ORC_MAX_M], gw[ORC_MAX_M];
+    gauss_legendre(M, gx, gw);
+    for (int m = 0; m < M; ++m) {
+        double half = 0.5 * tau[m];
+        for (int j = 0; j < M; ++j) {
+            double acc = 0.0;
+            for (int g = 0; g < M; ++g)
+                acc += gw[g] * lagrange(M, tau, j, half * (gx[g] + 1.0));
+            Q[m * M + j] = half * acc;
+        }
+    }
+    return 0;
+}
+
+/* S_m^{m+1} = Q_{m+1} - Q_m, m = 0..M-2 (rows of an (M-1) x M matrix). Eq. 2 */
+int orc_s_matrix(int M, const double *Q, double *S)
+{
+    if (M < 2 || M > ORC_MAX_M) return 1;
+    for (int m = 0; m < M - 1; ++m)
+        for (int j = 0; j < M; ++j)
+            S[m * M + j] = Q[(m + 1) * M + j] - Q[m * M + j];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid helpers.                                                             */
+/* ------------------------------------------------------------------------ */
+static long npoints(int d, int n) { return d == 2 ? (long)n * n : (long)n * n * n; }
+
+static long idx(int d, int n, int i, int j, int k)
+{
+    if (d == 2) return (i - 1) + (long)n * (j - 1);
+    return (i - 1) + (long)n * ((j - 1) + (long)n * (k - 1));
+}
+
+/* Value at 1-based interior index; zero on (or beyond) the Dirichlet boundary. */
+static double val(const double *u, int d, int n, int i, int j, int k)
+{
+    if (i < 1 || i > n || j < 1 || j > n) return 0.0;
+    if (d == 3 && (k < 1 || k > n)) return 0.0;
+    return u[idx(d, n, i, j, k)];
+}
+
+static int kmax(int d, int n) { return d == 3 ? n : 1; }
+
+/* Sum of the 2d nearest neighbours of (i,j,k). */
+static double neighbour_sum(const double *u, int d, int n, int i, int j, int k)
+{
+    double s = val(u, d, n, i - 1, j, k) + val(u, d, n, i + 1, j, k)
+             + val(u, d, n, i, j - 1, k) + val(u, d, n, i, j + 1, k);
+    if (d == 3) s += val(u, d, n, i, j, k - 1) + val(u, d, n, i, j, k + 1);
+    return s;
+}
+
+/* L_h u at one point: (sum of neighbours - 2d u) / h^2. */
+static double laplacian_at(const double *u, int d, int n, int i, int j, int k)
+{
+    double h = 1.0 / (n + 1);
+    return (neighbour_sum(u, d, n, i, j, k) - 2.0 * d * val(u, d, n, i, j, k)) / (h * h);
+}
+
+/* out = L_h u (5-point in 2D, 7-point in 3D). */
+void orc_laplacian(int d, int n, const double *u, double *out)
+{
+    for (int k = 1; k <= kmax(d, n); ++k)
+        for (int j = 1; j <= n; ++j)
+            for (int i = 1; i <= n; ++i)
+                out[idx(d, n, i, j, k)] = laplacian_at(u, d, n, i, j, k);
+}
+
+/* r = b - (I - a L_h) x */
+void orc_residual(int d, int n, double a, const double *x, const double *b, double *r)
+{
+    for (int k = 1; k <= kmax(d, n); ++k)
+        for (int j = 1; j <= n; ++j)
+            for (int i = 1; i <= n; ++i) {
+                long p = idx(d, n, i, j, k);
+                r[p] = b[p] - (x[p] - a * laplacian_at(x, d, n, i, j, k));
+            }
+}
+
+/* max_p |v_p| */
+static double max_abs(const double *v, long N)
+{
+    double m = 0.0;
+    for (long p = 0; p < N; ++p) {
+        double a = fabs(v[p]);
+        if (a > m || a != a) m = a; /* a NaN propagates */
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multigrid components.                                                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One damped-Jacobi sweep on (I - a L_h) x = b:
+ *   x_new = x_old + omega (b - (I - a L_h) x_old) / (1 + 2 d a / h^2),
+ * every point from the old iterate.  'old' is scratch of N values.
+ */
+void orc_smooth_jacobi(int d, int n, double a, double omega, double *x, const double *b,
+                       double *old)
+{
+    double h = 1.0 / (n + 1);
+    double diag = 1.0 + 2.0 * d * a / (h * h);
+    memcpy(old, x, sizeof(double) * npoints(d, n));
+    for (int k = 1; k <= kmax(d, n); ++k)
+        for (int j = 1; j <= n; ++j)
+            for (int i = 1; i <= n; ++i) {
+                long p = idx(d, n, i, j, k);
+                double r = b[p] - (old[p] - a * laplacian_at(old, d, n, i, j, k));
+                x[p] = old[p] + omega * r / diag;
+            }
+}
+
+/*
+ * One red-black Gauss-Seidel sweep on (I - a L_h) x = b.  A point is red when
+ * i+j(+k) is even (1-based interior indices); all red points are relaxed
+ * first, then all black points, each solving its own row exactly:
+ *   x_p = (b_p + (a/h^2) * sum of neighbours) / (1 + 2 d a / h^2).
+ */
+void orc_smooth_rbgs(int d, int n, double a, double *x, const double *b)
+{
+    double h = 1.0 / (n + 1);
+    double diag = 1.0 + 2.0 * d * a / (h * h);
+    for (int colour = 0; colour < 2; ++colour)
+        for (int k = 1; k <= kmax(d, n); ++k)
+            for (int j = 1; j <= n; ++j)
+                for (int i = 1; i <= n; ++i) {
+                    int parity = (d == 3) ? (i + j + k) % 2 : (i + j) % 2;
+                    if (parity != colour) continue;
+                    long p = idx(d, n, i, j, k);
+                    x[p] = (b[p] + a * neighbour_sum(x, d, n, i, j, k) / (h * h)) / diag;
+                }
+}
+
+/* 1D full-weighting / linear-interpolation weight between fine i and coarse I. */
+static double hat(int i, int I)
+{
+    int off = i - 2 * I;
+    if (off == 0) return 1.0;
+    if (off == 1 || off == -1) return 0.5;
+    return 0.0;
+}
+
+/*
+ * Full-weighting restriction from the fine grid (side n) to the coarse grid
+ * (side nc = (n-1)/2).  Coarse point I sits on fine point 2I; weights are the
+ * tensor product of (1/4, 1/2, 1/4): 1/16 [1 2 1; 2 4 2; 1 2 1] in 2D, /64 in 3D.
+ */
+void orc_restrict_fw(int d, int n, const double *r, double *rc)
+{
+    int nc = (n - 1) / 2;
+    for (int K = 1; K <= kmax(d, nc); ++K)
+        for (int J = 1; J <= nc; ++J)
+            for (int I = 1; I <= nc; ++I) {
+                double acc = 0.0;
+                int kc = (d == 3) ? 2 * K : 1;
+                int klo = (d == 3) ? kc - 1 : 1, khi = (d == 3) ? kc + 1 : 1;
+                for (int k = klo; k <= khi; ++k)
+                    for (int j = 2 * J - 1; j <= 2 * J + 1; ++j)
+                        for (int i = 2 * I - 1; i <= 2 * I + 1; ++i) {
+                            double w = 0.5 * hat(i, I) * 0.5 * hat(j, J);
+                            if (d == 3) w *= 0.5 * hat(k, K);
+                            acc += w * val(r, d, n, i, j, k);
+                        }
+                rc[idx(d, nc, I, J, K)] = acc;
+            }
+}
+
+/*
+ * x += P e_c with P the (bi/tri)linear interpolation from the coarse grid
+ * (side nc) to the fine grid (side n = 2 nc + 1); coarse values beyond the
+ * interior are the zero Dirichlet ghosts.
+ */
+void orc_prolong_add(int d, int nc, const double *ec, double *x)
+{
+    int n = 2 * nc + 1;
+    for (int k = 1; k <= kmax(d, n); ++k)
+        for (int j = 1; j <= n; ++j)
+            for (int i = 1; i <= n; ++i) {
+                double acc = 0.0;
+                int Klo = (d == 3) ? k / 2 : 1, Khi = (d == 3) ? (k + 1) / 2 : 1;
+                for (int K = Klo; K <= Khi; ++K)
+                    for (int J = j / 2; J <= (j + 1) / 2; ++J)
+                        for (int I = i / 2; I <= (i + 1) / 2; ++I) {
+                            double w = hat(i, I) * hat(j, J);
+                            if (d == 3) w *= hat(k, K);
+                            acc += w * val(ec, d, nc, I, J, K);
+                        }
+                x[idx(d, n, i, j, k)] += acc;
+            }
+}
+
+/*
+ * Exact solve of (I - a L_h) x = b on a small grid by assembling the dense
+ * matrix column by column (applying the operator to unit vectors) and Gaussian
+ * elimination with partial pivoting.  Used on the coarsest multigrid level.
+ */
+void orc_dense_solve(int d, int n, double a, const double *b, double *x)
+{
+    long N = npoints(d, n);
+    double *A = (double *)malloc(sizeof(double) * N * N);
+    double *e = (double *)calloc(N, sizeof(double));
+    double *col = (double *)malloc(sizeof(double) * N);
+    double *rhs = (double *)malloc(sizeof(double) * N);
+    double *zero = (double *)calloc(N, sizeof(double));
+    for (long c = 0; c < N; ++c) {
+        e[c] = 1.0;
+        /* column c of (I - a L_h) = -(residual of x=e with b=0) */
+        orc_residual(d, n, a, e, zero, col);
+        for (long r = 0; r < N; ++r) A[r * N + c] = -col[r];
+        e[c] = 0.0;
+    }
+    for (long r = 0; r < N; ++r) rhs[r] = b[r];
+    for (long c = 0; c < N; ++c) {
+        long piv = c;
+        for (long r = c + 1; r < N; ++r)
+            if (fabs(A[r * N + c]) > fabs(A[piv * N + c])) piv = r;
+        if (piv != c) {
+            for (long q = 0; q < N; ++q) {
+                double t = A[c * N + q]; A[c * N + q] = A[piv * N + q]; A[piv * N + q] = t;
+            }
+            double t = rhs[c]; rhs[c] = rhs[piv]; rhs[piv] = t;
+        }
+        for (long r = c + 1; r < N; ++r) {
+            double f = A[r * N + c] / A[c * N + c];
+            for (long q = c; q < N; ++q) A[r * N + q] -= f * A[c * N + q];
+            rhs[r] -= f * rhs[c];
+        }
+    }
+    for (long r = N - 1; r >= 0; --r) {
+        double s = rhs[r];
+        for (long q = r + 1; q < N; ++q) s -= A[r * N + q] * x[q];
+        x[r] = s / A[r * N + r];
+    }
+    free(A); free(e); free(col); free(rhs); free(zero);
+}
+
+/* Multigrid hierarchy: level 0 is the fine grid, sides n_l = (n_{l-1}-1)/2 down to 3. */
+typedef struct {
+    int d, levels;
+    int side[32];
+    double *x[32], *b[32], *r[32], *tmp[32];
+} orc_mg;
+
+static void mg_alloc(orc_mg *mg, int d, int n)
+{
+    memset(mg, 0, sizeof(*mg));
+    mg->d = d;
+    int s = n, l = 0;
+    for (;;) {
+        mg->side[l] = s;
+        long N = npoints(d, s);
+        mg->x[l] = (double *)calloc(N, sizeof(double));
+        mg->b[l] = (double *)calloc(N, sizeof(double));
+        mg->r[l] = (double *)calloc(N, sizeof(double));
+        mg->tmp[l] = (double *)calloc(N, sizeof(double));
+        ++l;
+        if (s <= 3) break;
+        s = (s - 1) / 2;
+    }
+    mg->levels = l;
+}
+
+static void mg_free(orc_mg *mg)
+{
+    for (int l = 0; l < mg->levels; ++l) {
+        free(mg->x[l]); free(mg->b[l]); free(mg->r[l]); free(mg->tmp[l]);
+    }
+}
+
+static void smooth(const orc_problem *P, int n, double a, double *x, const double *b, double *tmp)
+{
+    if (P->smoother == 0) orc_smooth_jacobi(P->ndim, n, a, P->omega, x, b, tmp);
+    else orc_smooth_rbgs(P->ndim, n, a, x, b);
+}
+
+/* One V-cycle on level l for (I - a L_{h_l}) x = b, x updated in place. */
+static void vcycle(const orc_problem *P, orc_mg *mg, int l, double a, double *x, const double *b)
+{
+    int d = P->ndim, n = mg->side[l];
+    if (l == mg->levels - 1) { /* coarsest grid: exact solve */
+        orc_dense_solve(d, n, a, b, x);
+        return;
+    }
+    for (int s = 0; s < P->nu1; ++s) smooth(P, n, a, x, b, mg->tmp[l]);
+    orc_residual(d, n, a, x, b, mg->r[l]);
+    orc_restrict_fw(d, n, mg->r[l], mg->b[l + 1]);
+    memset(mg->x[l + 1], 0, sizeof(double) * npoints(d, mg->side[l + 1]));
+    vcycle(P, mg, l + 1, a, mg->x[l + 1], mg->b[l + 1]);
+    orc_prolong_add(d, mg->side[l + 1], mg->x[l + 1], x);
+    for (int s = 0; s < P->nu2; ++s) smooth(P, n, a, x, b, mg->tmp[l]);
+}
+
+/* Public single V-cycle (for multigrid tests). */
+int orc_vcycle(const orc_problem *P, double a, double *x, const double *b)
+{
+    orc_mg mg;
+    mg_alloc(&mg, P->ndim, P->n);
+    vcycle(P, &mg, 0, a, x, b);
+    mg_free(&mg);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact solve by sine-transform diagonalisation.                           */
+/* ------------------------------------------------------------------------ */
+
+/* Apply T[p][i] = sin(i p pi / (n+1)) along one axis (stride 'st'). */
+static void sine_along_axis(int d, int n, int axis, double *u, const double *T)
+{
+    long N = npoints(d, n);
+    long st = 1;
+    for (int a = 0; a < axis; ++a) st *= n;
+    double *line = (double *)malloc(sizeof(double) * n);
+    for (long base = 0; base < N; ++base) {
+        if ((base / st) % n != 0) continue; /* first point of each line */
+        for (int p = 0; p < n; ++p) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += T[p * n + i] * u[base + i * st];
+            line[p] = acc;
+        }
+        for (int p = 0; p < n; ++p) u[base + p * st] = line[p];
+    }
+    free(line);
+}
+
+/*
+ * Exact solve of (I - a L_h) x = b.  The sine modes
+ * v_p(i) = prod_axes sin(i p pi/(n+1)) are eigenvectors of L_h with eigenvalues
+ * lambda_p = -(4/h^2) sum_axes sin^2(p pi h / 2); the 1D sine matrix T
+ * satisfies T T = (n+1)/2 I.  So x = (2/(n+1))^d T^d diag(1/(1 - a lambda)) T^d b.
+ */
+void orc_solve_exact(int d, int n, double a, const double *b, double *x)
+{
+    long N = npoints(d, n);
+    double h = 1.0 / (n + 1);
+    double *T = (double *)malloc(sizeof(double) * n * n);
+    for (int p = 1; p <= n; ++p)
+        for (int i = 1; i <= n; ++i)
+            T[(p - 1) * n + (i - 1)] = sin(M_PI * (double)i * (double)p / (n + 1));
+    memcpy(x, b, sizeof(double) * N);
+    for (int ax = 0; ax < d; ++ax) sine_along_axis(d, n, ax, x, T);
+    double *lam1 = (double *)malloc(sizeof(double) * n);
+    for (int p = 1; p <= n; ++p) {
+        double s = sin(M_PI * p * h / 2.0);
+        lam1[p - 1] = -4.0 * s * s / (h * h);
+    }
+    double scale = pow(2.0 / (n + 1), d);
+    for (int k = 1; k <= kmax(d, n); ++k)
+        for (int j = 1; j <= n; ++j)
+            for (int i = 1; i <= n; ++i) {
+                double lam = lam1[i - 1] + lam1[j - 1] + (d == 3 ? lam1[k - 1] : 0.0);
+                x[idx(d, n, i, j, k)] *= scale / (1.0 - a * lam);
+            }
+    for (int ax = 0; ax < d; ++ax) sine_along_axis(d, n, ax, x, T);
+    free(T); free(lam1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Right-hand side f = f^E + f^I of the ODE system (Sec. 2, Sec. 3).         */
+/* ------------------------------------------------------------------------ */
+static double f_explicit(const orc_problem *P, double u)
+{
+    if (P->reaction == 1) return u - u * u * u;
+    if (P->reaction == 2) return P->lambda_e * u;
+    return 0.0;
+}
+
+/* fE = f^E(u) pointwise, fI = nu L_h u */
+static void eval_f(const orc_problem *P, const double *u, double *fE, double *fI)
+{
+    long N = npoints(P->ndim, P->n);
+    orc_laplacian(P->ndim, P->n, u, fI);
+    for (long p = 0; p < N; ++p) {
+        fI[p] *= P->nu;
+        fE[p] = f_explicit(P, u[p]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One ISDC / SDC time step.                                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Advance u (N values, in place) by one time step of length dt.
+ *
+ * n_sweeps > 0: exactly that many sweeps; n_sweeps == 0: sweep until the SDC
+ * residual drops below tol, at most max_sweeps.  n_vcycles is L for solver 0.
+ * Outputs: *sweeps_out, *vcycles_out (V-cycles spent on node solves),
+ * res_hist[k-1] = residual after sweep k (room for max(n_sweeps, max_sweeps)),
+ * nodes_out (optional, M*N): the node values U_1..U_M after the last sweep.
+ * nodes_in (optional, M*N): initial node values instead of spreading u; its
+ * first node must equal u (Lobatto: tau_1 = 0).
+ * Returns 0 on success (converged or fixed count), 1 when the cap is hit
+ * without convergence, 2 on a non-finite residual, 3 on a bad argument.
+ */
+int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
+                  int *sweeps_out, long *vcycles_out, double *res_hist, double *nodes_out,
+                  const double *nodes_in)
+{
+    const int d = P->ndim, n = P->n, M = P->M;
+    if ((d != 2 && d != 3) || n < 1 || M < 2 || M > ORC_MAX_M) return 3;
+    const long N = npoints(d, n);
+    double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M], S[ORC_MAX_M * ORC_MAX_M];
+    orc_lobatto_nodes(M, tau);
+    orc_q_matrix(M, tau, Q);
+    orc_s_matrix(M, Q, S);
+
+    /* node values U_m (m = 0..M-1 here, 0-based), old iterate, f^E and f^I */
+    double *U = (double *)malloc(sizeof(double) * M * N);
+    double *Uold = (double *)malloc(sizeof(double) * M * N);
+    double *FE = (double *)malloc(sizeof(double) * M * N);
+    double *FI = (double *)malloc(sizeof(double) * M * N);
+    double *FEold = (double *)malloc(sizeof(double) * M * N);
+    double *FIold = (double *)malloc(sizeof(double) * M * N);
+    double *u0 = (double *)malloc(sizeof(double) * N);
+    double *rhs = (double *)malloc(sizeof(double) * N);
+    double *x = (double *)malloc(sizeof(double) * N);
+    double *res = (double *)malloc(sizeof(double) * N);
+    double *fe_new = (double *)malloc(sizeof(double) * N);
+    double *tmp = (double *)malloc(sizeof(double) * N);
+    orc_mg mg;
+    mg_alloc(&mg, d, n);
+
+    /* Initial iterate: u_0 spread to every node (the paper does not state it). */
+    memcpy(u0, u, sizeof(double) * N);
+    for (int m = 0; m < M; ++m) {
+        memcpy(U + m * N, nodes_in ? nodes_in + m * N : u0, sizeof(double) * N);
+        eval_f(P, U + m * N, FE + m * N, FI + m * N);
+    }
+
+    int k = 0, status = 0;
+    long vcycles = 0;
+    int cap = n_sweeps > 0 ? n_sweeps : P->max_sweeps;
+    for (;;) {
+        /* keep u^k and F(u^k) for the whole sweep */
+        memcpy(Uold, U, sizeof(double) * M * N);
+        memcpy(FEold, FE, sizeof(double) * M * N);
+        memcpy(FIold, FI, sizeof(double) * M * N);
+
+        /* node 0 is t_0 = T_n (Lobatto): u_0^{k+1} = u_0, nothing to solve */
+        for (int m = 0; m < M - 1; ++m) {
+            double dtm = P->dt * (tau[m + 1] - tau[m]);
+            double a = dtm * P->nu; /* (I - dt_m A) with A = nu L_h */
+            const double *Um_new = U + m * N;
+            for (long p = 0; p < N; ++p) fe_new[p] = f_explicit(P, Um_new[p]);
+            /* Eq. 4 with the implicit unknown moved left:
+             * (I - dt_m A) u_{m+1}^{k+1} = u_m^{k+1}
+             *     + dt_m [f^E(u_m^{k+1}) - f^E(u_m^k)] - dt_m f^I(u_{m+1}^k)
+             *     + S_m^{m+1} F(u^k),   S_m^{m+1}F = dt sum_j s_{m,j} f(u_j^k) */
+            for (long p = 0; p < N; ++p) {
+                double sf = 0.0;
+                for (int j = 0; j < M; ++j)
+                    sf += S[m * M + j] * (FEold[j * N + p] + FIold[j * N + p]);
+                rhs[p] = Um_new[p] + dtm * (fe_new[p] - FEold[m * N + p])
+                       - dtm * FIold[(m + 1) * N + p] + P->dt * sf;
+            }
+            /* initial guess for the spatial solver (Sec. 4.3) */
+            if (P->guess == 0) memcpy(x, Uold + (m + 1) * N, sizeof(double) * N);
+            else if (P->guess == 1) memset(x, 0, sizeof(double) * N);
+            else memcpy(x, Um_new, sizeof(double) * N);
+
+            if (P->solver == 2) {
+                orc_solve_exact(d, n, a, rhs, x);
+            } else if (P->solver == 1) {
+                for (int c = 0; c < P->mg_max_cycles; ++c) {
+                    orc_residual(d, n, a, x, rhs, tmp);
+                    if (max_abs(tmp, N) <= P->mg_tol) break;
+                    vcycle(P, &mg, 0, a, x, rhs);
+                    ++vcycles;
+                }
+            } else {
+                for (int c = 0; c < n_vcycles; ++c) {
+                    vcycle(P, &mg, 0, a, x, rhs);
+                    ++vcycles;
+                }
+            }
+            memcpy(U + (m + 1) * N, x, sizeof(double) * N);
+        }
+        ++k;
+
+        /* F(u^{k+1}) and the SDC residual
+         * max_m max_x | u_0 + dt sum_j q_{m,j} f(u_j^{k+1}) - u_m^{k+1} |   (Sec. 3) */
+        for (int m = 0; m < M; ++m) eval_f(P, U + m * N, FE + m * N, FI + m * N);
+        double R = 0.0;
+        for (int m = 0; m < M; ++m)
+            for (long p = 0; p < N; ++p) {
+                double qf = 0.0;
+                for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
+                double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
+                if (r > R || r != r) R = r;
+            }
+        if (res_hist) res_hist[k - 1] = R;
+        if (!(R == R) || isinf(R)) { status = 2; break; }
+        if (n_sweeps > 0) {
+            if (k >= n_sweeps) break;
+        } else {
+            if (R < P->tol) break;
+            if (k >= cap) { status = 1; break; }
+        }
+    }
+
+    memcpy(u, U + (M - 1) * N, sizeof(double) * N); /* Lobatto: tau_M = 1 */
+    if (nodes_out) memcpy(nodes_out, U, sizeof(double) * M * N);
+    if (sweeps_out) *sweeps_out = k;
+    if (vcycles_out) *vcycles_out = vcycles;
+    free(U); free(Uold); free(FE); free(FI); free(FEold); free(FIold);
+    free(u0); free(rhs); free(x); free(res); free(fe_new); free(tmp);
+    mg_free(&mg);
+    return status;
+}
