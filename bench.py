@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ISDC hot path.
+
+One bench step = one ISDC time step of the workload (Sec. 2 Eq. 4, Sec. 3):
+spread, SDC sweeps with L V-cycles per node solve until the max-norm SDC
+residual is below 1e-10, u <- u_M.  Metric: DOF-sweeps/s = (interior points)
+x (sweeps executed) / wall time, whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, timed on host cores)
+
+Multi-GPU (torchrun, one rank per GPU): every rank integrates its own copy of
+the workload (independent replicas, no collective on the data path), weak
+scaling.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import isdc_inputs as W  # noqa: E402
+
+FP64_OPS_PER_SM_CLK = 2      # DFMA/DADD issue per SM per clock on GB300 (measured 0.598 T DFMA/s at ~1.98 GHz)
+FP32_OPS_PER_SM_CLK = 128
+SMS = 152
+SM_MAX_MHZ = 2070.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def workloads():
+    return {
+        "3d_n255_M5_fp64": W.workload_3d_255(),
+        "3d_n255_M5_mixed": W.Workload("3d_n255_M5_mixed", 3, 255, 0.1, 5, 0.02, 20, 2, 1, 2, 2,
+                                       vcycle_fp32=True, seed=2),
+        "3d_n511_M5_mixed": W.workload_3d_511_mixed(),
+        "2d_n127_M3_fp64": W.workload_2d_127(),
+    }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def traffic_for(workload: str, cls: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (profiles/ncu_traffic.txt: workload class sha bytes)."""
+    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1401_7824_gb300", "csrc", "kernels.cuh"), "rb").read())
+    sha = sha.hexdigest()[:16]
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")) as f:
+            for line in f:
+                p = line.split()
+                if len(p) == 4 and not line.startswith("#") and p[0] == workload and p[1] == cls and p[2] == sha:
+                    return float(p[3])
+    except OSError:
+        pass
+    return None
+
+
+def roofline(prof: dict, workload: str, fp32_vcycle: bool):
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    r = prof[dom]
+    per_launch_s = r["total_ms"] / 1e3 / r["launches"]
+    bytes_l = r["bytes"] / r["launches"]
+    dp_l = r["fp64_ops"] / r["launches"]
+    sp_l = r["fp32_ops"] / r["launches"]
+    dp_peak = SMS * FP64_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    sp_peak = SMS * FP32_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    t_hbm = bytes_l / (hbm * 1e9)
+    t_dp = dp_l / dp_peak
+    t_sp = sp_l / sp_peak
+    out = {"kernel": dom, "launches": r["launches"], "us_per_launch": per_launch_s * 1e6,
+           "algorithmic_bytes_per_launch": bytes_l, "fp64_ops_per_launch": dp_l, "fp32_ops_per_launch": sp_l}
+    if t_hbm >= max(t_dp, t_sp):
+        ach = bytes_l / per_launch_s / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   peak_source=f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
+    elif t_dp >= t_sp:
+        ach = dp_l / per_launch_s / 1e12
+        out.update(bound="alu", achieved=ach, peak=dp_peak / 1e12, unit="T FP64-op/s", frac=ach / (dp_peak / 1e12),
+                   peak_source="derived: 152 SMs x 2 FP64 add/mul/FMA per SM-clock x 2070 MHz",
+                   hbm_frac=bytes_l / per_launch_s / 1e9 / hbm)
+    else:
+        ach = sp_l / per_launch_s / 1e12
+        out.update(bound="alu", achieved=ach, peak=sp_peak / 1e12, unit="T FP32-op/s", frac=ach / (sp_peak / 1e12),
+                   peak_source="derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                   hbm_frac=bytes_l / per_launch_s / 1e9 / hbm)
+    out["traffic"] = traffic_for(workload, dom)
+    total = sum(v["total_ms"] for v in prof.values())
+    out["shares"] = {k: round(v["total_ms"] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
+    return out
+
+
+def oracle_sweep_rate(w, n_override=None, sweeps=1):
+    """DOF-sweeps/s of the FP64 CPU oracle on one SDC sweep of the workload
+    (single-threaded plain C)."""
+    import oracle as O
+    n = n_override or w.n
+    p = O.Problem(w.ndim, n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
+                  reaction=w.reaction)
+    u0 = W.initial_condition(w.ndim, n, w.seed)
+    O.build()
+    t0 = time.perf_counter()
+    O.isdc_step(p, u0, sweeps, w.n_vcycles)
+    dt = time.perf_counter() - t0
+    return n ** w.ndim * sweeps / dt, dt, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    w = workloads()[args.workload]
+    n_sample = 127 if w.ndim == 3 and w.n > 127 else w.n
+    for _ in range(args.warmup):
+        oracle_sweep_rate(w, n_sample)
+    total_dof_sweeps, total_t = 0.0, 0.0
+    for _ in range(args.steps):
+        rate, dt, n = oracle_sweep_rate(w, n_sample)
+        total_dof_sweeps += n ** w.ndim
+        total_t += dt
+    value = total_dof_sweeps / total_t
+    sample = (f"each step: 1 SDC sweep ({w.M - 1} node solves x {w.n_vcycles} V-cycles + residual) of the "
+              f"workload's equation and parameters on a {n_sample}^{w.ndim} grid, from its seeded initial state")
+    line = {"metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w),
+            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w):
+    N = w.n ** w.ndim
+    state_bytes = (3 * w.M + 2) * N * 8
+    return {"workload": w.name, "ndim": w.ndim, "n": w.n, "dofs": N, "M": w.M, "nodes": "gauss-lobatto",
+            "nu": w.nu, "dt": w.dt, "L_vcycles": w.n_vcycles,
+            "smoother": ("rbgs" if w.smoother == 1 else "wjacobi") + f" V({w.nu1},{w.nu2})",
+            "reaction": "u-u^3", "tol": w.tol, "vcycle_precision": "fp32" if w.vcycle_fp32 else "fp64",
+            "l2": f"inputs larger than L2 (node state {state_bytes / 1e9:.2f} GB > {L2_BYTES / 1e6:.0f} MB L2)"
+            if state_bytes > L2_BYTES else "inputs fit in L2 (latency-bound case)",
+            "parallelism": "replicas (one independent instance per GPU)"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1401_7824_gb300 as G
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workloads()[args.workload]
+    N = w.n ** w.ndim
+    u0 = W.initial_condition(w.ndim, w.n, w.seed)
+    g = G.Isdc(w.ndim, w.n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
+               vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200)
+    stream = torch.cuda.current_stream()
+    u = torch.from_numpy(u0).cuda()
+    for _ in range(args.warmup):
+        st = g.step(u, 0, w.n_vcycles)
+    torch.cuda.synchronize()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    g.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweeps, vcycles, statuses = [], [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        statuses.append(g.step(u, 0, w.n_vcycles))
+        s, v = g.stats()
+        sweeps.append(s)
+        vcycles.append(v)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = g.profile_read()
+    g.profile(False)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    residual = g.residual()
+    dof_sweeps = float(N * sum(sweeps))
+
+    # end to end through the public C ABI with host buffers: H2D + step + D2H each step
+    uh = torch.from_numpy(u0).pin_memory()
+    g.step_host(uh.numpy(), 0, w.n_vcycles)  # first call allocates the device staging buffer
+    barrier()
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(args.steps):
+        g.step_host(uh.numpy(), 0, w.n_vcycles)
+        e2e_sweeps += g.stats()[0]
+    e2e_t = time.perf_counter() - t0
+    barrier()
+
+    if world > 1:
+        t = torch.tensor([elapsed, e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        work = torch.tensor([dof_sweeps, float(N * e2e_sweeps)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(work, op=dist.ReduceOp.SUM)
+        elapsed, e2e_t = float(t[0]), float(t[1])
+        dof_sweeps, e2e_work = float(work[0]), float(work[1])
+    else:
+        e2e_work = float(N * e2e_sweeps)
+
+    value = dof_sweeps / elapsed
+    line = {
+        "metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if not w.vcycle_fp32 else "f64 (FP32 V-cycles)",
+        "data": "synthetic (seeded sin-mode initial data + N(0, 0.01^2) noise)",
+        "config": config_of(w),
+        "steps_per_s": world * args.steps / elapsed,
+        "sweeps_per_step": sweeps, "vcycles_per_step": vcycles, "residual_last_step": residual,
+        "converged": all(s == 0 for s in statuses),
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "roofline": roofline(prof, w.name, w.vcycle_fp32),
+        "clocks": clk,
+        "e2e": {"value": e2e_work / e2e_t, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": N * 8},
+    }
+    g.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, n = oracle_sweep_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": "DOF-sweeps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"1 SDC sweep of step 1 of the workload ({n}^{w.ndim} grid, "
+                                          f"{w.M - 1} node solves x {w.n_vcycles} V-cycles + residual), "
+                                          f"{dt:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="3d_n255_M5_fp64", choices=sorted(workloads()))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * isdc.h -- C ABI of the GB300 (sm_103a) implementation of inexact spectral
+ * deferred corrections (ISDC; Speck, Ruprecht, Minion, Emmett, Krause,
+ * arXiv:1401.7824).
+ *
+ * Problem (Sec. 2, Eq. 1): u(t) = u_0 + int_{T_0}^t f(u(s)) ds with
+ *   f(u) = f^I(u) + f^E(u),  f^I(u) = A u,  A = nu * L_h,
+ * L_h the 5-point (2D) or 7-point (3D) Laplacian on the interior points of the
+ * unit square/cube with zero Dirichlet values (Sec. 3, the linearly implicit
+ * case with W = I), and f^E(u) = u - u^3 or 0 (explicit part of Eq. 4).
+ *
+ * One time step [T_n, T_n + dt] runs semi-implicit SDC sweeps (Sec. 2, Eq. 4)
+ * over M Gauss-Lobatto nodes; every implicit Euler solve
+ * (I - dt_m A) u_{m+1}^{k+1} = rhs is replaced by L geometric-multigrid
+ * V-cycles started from u_{m+1}^k (Sec. 3, Sec. 4.3).  Sweeps stop when the
+ * max-norm SDC residual (Sec. 3) drops below a tolerance, or after a fixed
+ * count.
+ *
+ * Layout of every grid array: float64, interior points only, x fastest:
+ * index i + n*(j + n*k) for 0-based i, j, k in [0, n).  h = 1/(n+1).
+ *
+ * Conventions:
+ *  - Device pointers are CUDA global-memory pointers valid on the device that
+ *    was current when the context was created.  The caller owns every buffer
+ *    it passes; the library never frees or keeps them past the call.
+ *  - Work is ordered on the context's stream.  Calls that return host values
+ *    (isdc_residual, isdc_stats, isdc_step with n_sweeps = 0, isdc_step_host)
+ *    synchronise that stream.
+ *  - Errors are return codes; nothing aborts or traps.  isdc_last_error()
+ *    describes the last failure.  A context is not thread-safe; separate
+ *    contexts are independent.
+ */
+#ifndef ISDC_H
+#define ISDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isdc_ctx isdc_ctx;
+
+typedef enum {
+    ISDC_OK = 0,
+    ISDC_ERR_INVALID_ARG = 1,   /* bad size, parameter or NULL pointer            */
+    ISDC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement   */
+    ISDC_ERR_OOM = 3,           /* device allocation failed                       */
+    ISDC_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed    */
+    ISDC_ERR_NOT_CONVERGED = 5, /* soft: max_sweeps reached; u holds the last sweep */
+    ISDC_ERR_NONFINITE = 6      /* the SDC residual became NaN or Inf             */
+} isdc_status;
+
+/* Collocation node families (Sec. 2).  Gauss-Lobatto is implemented. */
+typedef enum {
+    ISDC_NODES_GAUSS_LOBATTO = 0,
+    ISDC_NODES_RADAU_RIGHT = 1,
+    ISDC_NODES_GAUSS_LEGENDRE = 2
+} isdc_node_type;
+
+typedef enum { ISDC_SMOOTHER_JACOBI = 0, ISDC_SMOOTHER_RBGS = 1 } isdc_smoother;
+typedef enum { ISDC_REACTION_NONE = 0, ISDC_REACTION_ALLEN_CAHN = 1 } isdc_reaction;
+
+typedef struct {
+    int    smoother;      /* isdc_smoother: damped Jacobi (default) or red-black Gauss-Seidel */
+    int    nu1, nu2;      /* pre/post smoothing sweeps per level (default 1, 1) */
+    double omega;         /* Jacobi damping (default 2/3) */
+    int    vcycle_fp32;   /* 0: V-cycles in FP64.  1: FP32 V-cycles in defect-correction
+                             form (FP64 defect b - (I - dt_m A)x, FP32 cycle on the error,
+                             FP64 update); node values, S F, residuals stay FP64. */
+    int    reaction;      /* isdc_reaction (default ISDC_REACTION_ALLEN_CAHN) */
+    double tol;           /* SDC residual tolerance for n_sweeps == 0 (default 1e-10) */
+    int    max_sweeps;    /* sweep cap for n_sweeps == 0 (default 100) */
+    double mg_tol;        /* classical SDC (n_vcycles == 0): stop the node solve when the
+                             max-norm residual of (I - dt_m A)x = b is <= mg_tol (default 1e-12) */
+    int    mg_max_cycles; /* cap on V-cycles per node solve in that mode (default 50) */
+    void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
+                             non-blocking stream.  To run on the legacy default stream pass
+                             cudaStreamLegacy ((void*)1), for the per-thread default stream
+                             cudaStreamPerThread ((void*)2). */
+} isdc_options;
+
+/* Fill *opt with the defaults listed above.  Returns ISDC_ERR_INVALID_ARG for NULL. */
+isdc_status isdc_default_options(isdc_options *opt);
+
+/*
+ * Collocation tables of Sec. 2 (Eq. 2) on the unit interval, host only (no
+ * GPU needed): nodes tau[M] (tau_1 = 0, tau_M = 1 for Gauss-Lobatto), the
+ * integration matrix Q[M*M] (Q[m*M+j] = integral from 0 to tau_m of the
+ * Lagrange basis polynomial l_j) and, if S is not NULL, the node-to-node matrix
+ * S[(M-1)*M] = Q_{m+1} - Q_m.  The S_m^{m+1} F(u) of Eq. 2 is
+ * dt * sum_j S[m*M+j] f(u_j).  Errors: UNSUPPORTED (node type), INVALID_ARG.
+ */
+isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double *tau, double *Q, double *S);
+
+/*
+ * Create a context for one problem: the collocation tables (Sec. 2, Eq. 2:
+ * nodes tau_m, Q, S_m^{m+1}, dt_m = dt (tau_{m+1} - tau_m)), the device node
+ * state (u_m, f(u_m) for every node) and the multigrid hierarchy (sides
+ * n, (n-1)/2, ... down to 3).
+ *   ndim   2 or 3
+ *   dims   ndim interior sides; all equal, each 2^j - 1 with j >= 2
+ *   nu     diffusion coefficient (> 0)
+ *   nodes  ISDC_NODES_GAUSS_LOBATTO (others: ISDC_ERR_UNSUPPORTED)
+ *   M      number of nodes, 2..7
+ *   dt     time-step length (> 0)
+ *   opt    options, or NULL for the defaults
+ *   out    receives the context (NULL on failure)
+ * Allocates device memory (cudaMalloc) on the current device.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+isdc_status isdc_create(int ndim, const int64_t *dims, double nu, isdc_node_type nodes, int M,
+                        double dt, const isdc_options *opt, isdc_ctx **out);
+
+/*
+ * Advance u by one time step (Sec. 2, Eq. 4; Sec. 3).
+ *   u          device pointer, N = n^ndim float64 values; on entry u(T_n), on
+ *              return u(T_n + dt) = u_M (Gauss-Lobatto: tau_M = 1)
+ *   n_sweeps   > 0: exactly that many sweeps (no host synchronisation);
+ *              0: sweep until the SDC residual < opt.tol, at most opt.max_sweeps
+ *   n_vcycles  L > 0: L V-cycles per node solve (ISDC);
+ *              0: classical SDC, V-cycles until the node residual <= opt.mg_tol
+ * The multigrid initial guess is always u_{m+1}^k (Sec. 4.3).  The initial
+ * iterate is u spread to all nodes, unless isdc_set_nodes() supplied one.
+ * Errors: INVALID_ARG, CUDA, NOT_CONVERGED (soft, u holds the last sweep),
+ * NONFINITE.
+ */
+isdc_status isdc_step(isdc_ctx *ctx, double *u, int n_sweeps, int n_vcycles);
+
+/*
+ * isdc_step for a HOST buffer: copies u (N float64 in host memory, pinned or
+ * pageable) to the device, runs the step, copies the result back and
+ * synchronises.  Same arguments and errors as isdc_step.
+ */
+isdc_status isdc_step_host(isdc_ctx *ctx, double *u_host, int n_sweeps, int n_vcycles);
+
+/* Max-norm SDC residual after the last sweep of the last step (Sec. 3), to
+ * *res (host).  Synchronises.  Errors: INVALID_ARG, CUDA. */
+isdc_status isdc_residual(const isdc_ctx *ctx, double *res);
+
+/* Sweeps and V-cycles (node solves only) spent by the last step, to host
+ * pointers (either may be NULL).  Synchronises. */
+isdc_status isdc_stats(const isdc_ctx *ctx, int *sweeps, int64_t *vcycles);
+
+/* Residual after each sweep of the last step: copies min(cap, sweeps) values
+ * to hist (host) and the sweep count to *count.  Only filled in the
+ * until-tolerance mode (n_sweeps == 0) and in fixed mode with record = 1 in
+ * isdc_set_record_history(). */
+isdc_status isdc_residual_history(const isdc_ctx *ctx, double *hist, int cap, int *count);
+
+/* Record the residual of every sweep in fixed-sweep mode too (one device-to-
+ * host copy per sweep, no extra synchronisation until the step ends). */
+isdc_status isdc_set_record_history(isdc_ctx *ctx, int record);
+
+/* Copy the M node values u_1..u_M of the last sweep (M*N float64, node-major)
+ * to the device buffer dst.  Checkpoint / inspection. */
+isdc_status isdc_get_nodes(const isdc_ctx *ctx, double *dst);
+
+/* Use the M*N node values in the device buffer src as the initial iterate of
+ * the NEXT isdc_step instead of spreading u (resume from a checkpoint).  The
+ * first node must equal that step's u.  Applies to one step only. */
+isdc_status isdc_set_nodes(isdc_ctx *ctx, const double *src);
+
+/*
+ * Standalone multigrid solve on one implicit Euler system of Sec. 3,
+ * (I - a L_h) x = b, with the context's grid and smoother: n_cycles V-cycles
+ * from the initial x (FP64 or FP32 per opt.vcycle_fp32).  x, b: device, N
+ * float64 each; x is updated in place.  Uses the context's hierarchy.
+ */
+isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, int n_cycles);
+
+/* Per-kernel-class timing (not from the paper: instrumentation for the
+ * roofline).  While enabled, every launch of the context is bracketed by CUDA
+ * events on its stream, and the algorithmic bytes and floating-point
+ * operations of the launch (a model: every input read once, every output
+ * written once; one op = one add, multiply or fused multiply-add) are summed.
+ * Enabling resets the sums. */
+typedef struct {
+    char    name[32];   /* kernel class, e.g. "smooth_fine", "sweep_end" */
+    int64_t launches;
+    double  total_ms;   /* sum of event-timed launch durations */
+    double  bytes;      /* algorithmic bytes, summed over launches */
+    double  fp64_ops;   /* algorithmic FP64 operations, summed */
+    double  fp32_ops;   /* algorithmic FP32 operations, summed */
+} isdc_kernel_stat;
+
+isdc_status isdc_profile_enable(isdc_ctx *ctx, int enable);
+
+/* Synchronise and copy up to cap class records (classes with launches only)
+ * to out; *count receives the number of such classes. */
+isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int *count);
+
+/* Message for the last failure of ctx, or of isdc_create when ctx is NULL. */
+const char *isdc_last_error(const isdc_ctx *ctx);
+
+/* Free the context and its device memory (synchronises its stream). */
+void isdc_destroy(isdc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISDC_H */

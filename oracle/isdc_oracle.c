@@ -664,3 +664,31 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     mg_free(&mg);
     return status;
 }
+
+/*
+ * SDC residual of given node values (Sec. 3): with f_j = f(U_j),
+ *   R = max_m max_x | u_0 + dt sum_j q_{m,j} f_j - U_m |,   u_0 = U_1.
+ * U: M*N node values.  Used to check a result at sizes where running the
+ * whole step on the CPU is too slow.
+ */
+double orc_sdc_residual(const orc_problem *P, const double *U)
+{
+    const int M = P->M;
+    const long N = npoints(P->ndim, P->n);
+    double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M];
+    orc_lobatto_nodes(M, tau);
+    orc_q_matrix(M, tau, Q);
+    double *FE = (double *)malloc(sizeof(double) * M * N);
+    double *FI = (double *)malloc(sizeof(double) * M * N);
+    for (int m = 0; m < M; ++m) eval_f(P, U + m * N, FE + m * N, FI + m * N);
+    double R = 0.0;
+    for (int m = 0; m < M; ++m)
+        for (long p = 0; p < N; ++p) {
+            double qf = 0.0;
+            for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
+            double r = fabs(U[p] + P->dt * qf - U[m * N + p]);
+            if (r > R || r != r) R = r;
+        }
+    free(FE); free(FI);
+    return R;
+}

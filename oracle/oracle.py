@@ -112,6 +112,8 @@ def _L():
         lib.orc_vcycle.argtypes = [ctypes.POINTER(_Problem), D, dp, dp]
         lib.orc_isdc_step.argtypes = [ctypes.POINTER(_Problem), dp, I, I, ctypes.POINTER(I),
                                       ctypes.POINTER(ctypes.c_long), dp, dp, dp]
+        lib.orc_sdc_residual.argtypes = [ctypes.POINTER(_Problem), dp]
+        lib.orc_sdc_residual.restype = D
         for f in ("orc_lobatto_nodes", "orc_q_matrix", "orc_s_matrix", "orc_vcycle", "orc_isdc_step"):
             getattr(lib, f).restype = I
         _lib = lib
@@ -260,6 +262,14 @@ def isdc_step(problem: Problem, u, n_sweeps: int = 0, n_vcycles: int = 2,
     if st == 3:
         raise ValueError("invalid problem")
     return StepResult(u, sweeps.value, vcyc.value, hist[:sweeps.value].copy(), st, nodes)
+
+
+def sdc_residual(problem: Problem, nodes) -> float:
+    """Max-norm SDC residual (Sec. 3) of node values (shape (M,) + grid)."""
+    nodes = _f64(nodes)
+    assert nodes.shape == (problem.M,) + problem.shape
+    pc = problem._c()
+    return float(_L().orc_sdc_residual(ctypes.byref(pc), _p(nodes)))
 
 
 @dataclass

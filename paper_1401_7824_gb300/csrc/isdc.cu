@@ -1,0 +1,905 @@
+// isdc.cu -- host side of the GB300 ISDC library: collocation tables, device
+// state, the V-cycle and sweep drivers, and the C ABI declared in isdc.h.
+//
+// One time step (Sec. 2, Eq. 4 with W = I; Sec. 3):
+//   spread u to the M Gauss-Lobatto nodes, f_m = f(u_m)
+//   sweep k = 1, 2, ...:
+//     for m = 0..M-2: b = u_m + dt_m f^E(u_m) + C_m      (k_rhs, also stores f_m)
+//                     L V-cycles on (I - dt_m nu L_h) u_{m+1} = b, from u_{m+1}^k
+//     f_{M-1}, SDC residual R, next C_m                   (k_sweep_end)
+//   until R < tol (or a fixed sweep count); u <- u_{M-1} (tau = 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/isdc.h"
+#include "kernels.cuh"
+
+#define ISDC_API extern "C" __attribute__((visibility("default")))
+
+using namespace isdc;
+
+namespace {
+
+thread_local char g_create_error[512] = "";
+
+// ---------------------------------------------------------------------------
+// Collocation tables (Sec. 2, Eq. 2).
+// ---------------------------------------------------------------------------
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with zero
+// diagonal and squared off-diagonals beta (Sturm sequence count).
+int sturm_count(const std::vector<double>& beta, int size, double x) {
+  int count = 0;
+  double q = -x;  // leading principal minor ratio
+  if (q < 0) ++count;
+  for (int k = 1; k < size; ++k) {
+    const double prev = (q == 0.0) ? 1e-300 : q;
+    q = -x - beta[k - 1] / prev;
+    if (q < 0) ++count;
+  }
+  return count;
+}
+
+// Gauss-Lobatto nodes on [0,1].  The interior nodes are the roots of
+// P'_{M-1}, i.e. of the Jacobi polynomial P^{(1,1)}_{M-2}: eigenvalues of its
+// Jacobi matrix (zero diagonal, squared off-diagonals k(k+2)/((2k+1)(2k+3))),
+// found by bisection on the Sturm count (Golub-Welsch).
+void lobatto_nodes(int M, double* tau) {
+  const int size = M - 2;
+  std::vector<double> beta(std::max(size, 1));
+  for (int k = 1; k < size; ++k) beta[k - 1] = double(k) * (k + 2) / ((2.0 * k + 1) * (2.0 * k + 3));
+  tau[0] = 0.0;
+  tau[M - 1] = 1.0;
+  for (int e = 0; e < size; ++e) {  // e-th smallest eigenvalue
+    double lo = -1.0, hi = 1.0;
+    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid == lo || mid == hi) break;
+      if (sturm_count(beta, size, mid) > e) hi = mid; else lo = mid;
+    }
+    tau[e + 1] = 0.5 * (0.5 * (lo + hi) + 1.0);
+  }
+}
+
+// Q[m][j] = int_0^{tau_m} l_j(s) ds, computed exactly: l_j expanded in powers
+// of x = 2s - 1 in [-1,1] and integrated term by term.
+void q_matrix(int M, const double* tau, double* Q) {
+  std::vector<double> x(M);
+  for (int i = 0; i < M; ++i) x[i] = 2.0 * tau[i] - 1.0;
+  for (int j = 0; j < M; ++j) {
+    std::vector<double> c(1, 1.0);  // coefficients, ascending powers
+    double denom = 1.0;
+    for (int i = 0; i < M; ++i) {
+      if (i == j) continue;
+      std::vector<double> nc(c.size() + 1, 0.0);
+      for (size_t k = 0; k < c.size(); ++k) {
+        nc[k + 1] += c[k];
+        nc[k] -= x[i] * c[k];
+      }
+      c.swap(nc);
+      denom *= (x[j] - x[i]);
+    }
+    auto antider = [&](double t) {
+      double acc = 0.0, pw = t;
+      for (size_t k = 0; k < c.size(); ++k) {
+        acc += c[k] * pw / double(k + 1);
+        pw *= t;
+      }
+      return acc;
+    };
+    const double base = antider(-1.0);
+    for (int m = 0; m < M; ++m) Q[m * M + j] = 0.5 * (antider(x[m]) - base) / denom;
+  }
+}
+
+// Inverse of the dense matrix of H = I - a L_h on a side-3 grid (Gauss-Jordan
+// with partial pivoting), row-major, Np x Np.
+void coarse_inverse(int dim, double a, std::vector<double>& inv) {
+  const int n = 3, Np = dim == 2 ? 9 : 27;
+  const double h = 1.0 / (n + 1), c = a / (h * h), d = 1.0 + 2.0 * dim * c;
+  std::vector<double> A(Np * Np, 0.0);
+  for (int p = 0; p < Np; ++p) {
+    const int i = p % n, j = (p / n) % n, k = dim == 3 ? p / (n * n) : 0;
+    A[p * Np + p] = d;
+    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+    for (int q = 0; q < 2 * dim; ++q) {
+      const int ii = nb[q][0], jj = nb[q][1], kk = nb[q][2];
+      if (ii < 0 || ii >= n || jj < 0 || jj >= n || kk < 0 || kk >= (dim == 3 ? n : 1)) continue;
+      A[p * Np + (ii + n * (jj + n * kk))] = -c;
+    }
+  }
+  inv.assign(Np * Np, 0.0);
+  for (int p = 0; p < Np; ++p) inv[p * Np + p] = 1.0;
+  for (int col = 0; col < Np; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Np; ++r)
+      if (std::fabs(A[r * Np + col]) > std::fabs(A[piv * Np + col])) piv = r;
+    if (piv != col)
+      for (int q = 0; q < Np; ++q) {
+        std::swap(A[col * Np + q], A[piv * Np + q]);
+        std::swap(inv[col * Np + q], inv[piv * Np + q]);
+      }
+    const double s = 1.0 / A[col * Np + col];
+    for (int q = 0; q < Np; ++q) { A[col * Np + q] *= s; inv[col * Np + q] *= s; }
+    for (int r = 0; r < Np; ++r) {
+      if (r == col) continue;
+      const double f = A[r * Np + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < Np; ++q) { A[r * Np + q] -= f * A[col * Np + q]; inv[r * Np + q] -= f * inv[col * Np + q]; }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid hierarchy in one precision.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Hier {
+  int nlev = 0;         // levels: sides n, (n-1)/2, ..., 3
+  int lb = 0;           // first level handled by the single-block bottom kernel
+  int side[kMaxLevels] = {};
+  size_t npts[kMaxLevels] = {};
+  T* x[kMaxLevels] = {};  // level unknown (level 0: not owned, except FP32 mode)
+  T* b[kMaxLevels] = {};  // level right-hand side (level 0: not owned, except FP32 mode)
+  T* t[kMaxLevels] = {};  // Jacobi ping-pong partner
+  T* r[kMaxLevels] = {};  // residual before restriction
+  T* Ainv = nullptr;      // dense side-3 inverses, one slot per node plus one spare
+  size_t bottom_smem = 0;
+};
+
+// Kernel classes timed by the built-in profiler (isdc_profile_*).
+enum ProfClass {
+  PC_SPREAD, PC_EVAL_F, PC_RHS, PC_SWEEP_END, PC_SMOOTH0, PC_RESIDUAL0, PC_RESTRICT0, PC_PROLONG0,
+  PC_SMOOTHC, PC_RESIDUALC, PC_RESTRICTC, PC_PROLONGC, PC_BOTTOM, PC_DEFECT, PC_UPDATE, PC_RESNORM, PC_COUNT
+};
+const char* const kProfNames[PC_COUNT] = {
+    "spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine", "prolong_fine",
+    "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse", "bottom", "defect", "update",
+    "resnorm"};
+
+struct Profiler {
+  bool on = false;
+  struct Rec { cudaEvent_t e0, e1; int cls; };
+  std::vector<Rec> pool;
+  size_t used = 0;
+  double ms[PC_COUNT] = {}, bytes[PC_COUNT] = {}, dp_ops[PC_COUNT] = {}, sp_ops[PC_COUNT] = {};
+  long long launches[PC_COUNT] = {};
+};
+
+}  // namespace
+
+struct isdc_ctx {
+  int dim = 0, n = 0, M = 0;
+  size_t N = 0;
+  double nu = 0, dt = 0, h = 0;
+  isdc_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double tau[kMaxM] = {}, Q[kMaxM * kMaxM] = {}, S[kMaxM * kMaxM] = {};
+  SweepTables tables{};
+  double* U = nullptr;  // M node arrays, node-major
+  double* F = nullptr;  // f(u_m), M arrays
+  double* C = nullptr;  // sweep constants, M-1 arrays
+  double* b = nullptr;  // right-hand side of the current node solve
+  double* u_dev = nullptr;  // device copy of u for isdc_step_host
+  Hier<double> h64;
+  Hier<float> h32;
+  unsigned long long* d_scal = nullptr;  // [0] SDC residual bits, [1] node-residual bits
+  unsigned long long* h_scal = nullptr;  // pinned mirror of d_scal
+  unsigned long long* h_hist = nullptr;  // pinned residual bits per sweep
+  int hist_cap = 0;
+  int record_history = 0;
+  int last_sweeps = 0, hist_count = 0;
+  long long last_vcycles = 0;
+  int nodes_pending = 0;
+  int spare_slot = 0;  // Ainv slot for isdc_vcycles
+  Profiler prof;
+  char err[512] = "";
+};
+
+namespace {
+
+isdc_status fail(isdc_ctx* ctx, isdc_status st, const char* fmt, ...) {
+  char* dst = ctx ? ctx->err : g_create_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? ISDC_ERR_OOM : ISDC_ERR_CUDA,       \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define LAUNCH_CHECK(ctx) CUDA_TRY(ctx, cudaGetLastError())
+
+// Events around every launch while profiling is on; the algorithmic bytes and
+// FP operations of the launch (a model: each input read once, each output
+// written once; one op = one add, multiply or fused multiply-add) are summed
+// on the host.
+void prof_flush(isdc_ctx* ctx) {
+  Profiler& P = ctx->prof;
+  if (!P.used) return;
+  cudaEventSynchronize(P.pool[P.used - 1].e1);
+  for (size_t q = 0; q < P.used; ++q) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, P.pool[q].e0, P.pool[q].e1) == cudaSuccess) P.ms[P.pool[q].cls] += t;
+  }
+  P.used = 0;
+}
+
+struct ProfScope {
+  isdc_ctx* ctx;
+  int idx = -1;
+  ProfScope(isdc_ctx* c, int cls, double bytes, double ops, bool fp64) : ctx(c) {
+    Profiler& P = ctx->prof;
+    if (!P.on) return;
+    if (P.used == P.pool.size()) {
+      if (P.pool.size() >= 16384) {
+        prof_flush(ctx);
+      } else {
+        Profiler::Rec r{};
+        if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+        if (cudaEventCreate(&r.e1) != cudaSuccess) { cudaEventDestroy(r.e0); return; }
+        P.pool.push_back(r);
+      }
+    }
+    idx = int(P.used++);
+    P.pool[idx].cls = cls;
+    cudaEventRecord(P.pool[idx].e0, ctx->stream);
+    P.launches[cls] += 1;
+    P.bytes[cls] += bytes;
+    (fp64 ? P.dp_ops[cls] : P.sp_ops[cls]) += ops;
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(ctx->prof.pool[idx].e1, ctx->stream);
+  }
+};
+
+inline double nb_ops(int dim) { return dim == 2 ? 3.0 : 5.0; }
+
+inline dim3 pt_grid(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
+inline dim3 rb_grid(int dim, int s) { return dim3(((s + 1) / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
+const dim3 kBlock(kBX, kBY, 1);
+
+inline size_t pow_dim(int dim, size_t s) { return dim == 2 ? s * s : s * s * s; }
+
+int bottom_threshold(int dim) { return dim == 2 ? 63 : 15; }
+
+template <typename T>
+isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
+  int s = ctx->n, l = 0;
+  for (;;) {
+    H.side[l] = s;
+    H.npts[l] = pow_dim(ctx->dim, s);
+    ++l;
+    if (s <= 3) break;
+    s = (s - 1) / 2;
+  }
+  H.nlev = l;
+  H.lb = 0;
+  while (H.side[H.lb] > bottom_threshold(ctx->dim)) ++H.lb;
+  for (int q = 0; q < H.nlev; ++q) {
+    const size_t bytes = H.npts[q] * sizeof(T);
+    const bool global_level = q < H.lb;
+    if (q > 0 || own_level0) {
+      if (global_level || q == H.lb) {
+        CUDA_TRY(ctx, cudaMalloc(&H.x[q], bytes));
+        CUDA_TRY(ctx, cudaMalloc(&H.b[q], bytes));
+      }
+    }
+    if (global_level) {
+      CUDA_TRY(ctx, cudaMalloc(&H.r[q], bytes));
+      if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) CUDA_TRY(ctx, cudaMalloc(&H.t[q], bytes));
+    }
+  }
+  size_t sm = 0;
+  for (int q = H.lb; q < H.nlev; ++q) sm += 3 * H.npts[q] * sizeof(T);
+  H.bottom_smem = sm;
+  const size_t ainv = size_t(ctx->M) * (ctx->dim == 2 ? 81 : 729) * sizeof(T);
+  CUDA_TRY(ctx, cudaMalloc(&H.Ainv, ainv));
+  return ISDC_OK;
+}
+
+template <typename T>
+void free_hier(Hier<T>& H, bool own_level0) {
+  for (int q = 0; q < H.nlev; ++q) {
+    if (q > 0 || own_level0) {
+      cudaFree(H.x[q]);
+      cudaFree(H.b[q]);
+    }
+    cudaFree(H.r[q]);
+    cudaFree(H.t[q]);
+  }
+  cudaFree(H.Ainv);
+}
+
+// Upload the dense side-3 inverse for a = dt_m nu into a slot.
+template <typename T>
+isdc_status upload_ainv(isdc_ctx* ctx, Hier<T>& H, int slot, double a) {
+  std::vector<double> inv;
+  coarse_inverse(ctx->dim, a, inv);
+  std::vector<T> tv(inv.begin(), inv.end());
+  const size_t each = ctx->dim == 2 ? 81 : 729;
+  CUDA_TRY(ctx, cudaMemcpyAsync(H.Ainv + slot * each, tv.data(), each * sizeof(T), cudaMemcpyHostToDevice,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // tv is a host temporary
+  return ISDC_OK;
+}
+
+template <typename T, int DIM>
+void configure_bottom(const Hier<T>& H) {
+  cudaFuncSetAttribute(k_bottom<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(H.bottom_smem));
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle on (I - a L_h) x = b (textbook geometric multigrid; the paper's
+// solver is not described).  x0/b0 are the level-0 arrays in precision T.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* home, const T* b, bool& zero,
+                         int sweeps) {
+  // x: where the level's iterate lives now; home: its own array (Jacobi
+  // ping-pongs between home and H.t[l]).
+  const int s = H.side[l];
+  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  for (int it = 0; it < sweeps; ++it) {
+    if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) {
+      T* out = (x == H.t[l]) ? home : H.t[l];
+      {
+        const double Np = double(H.npts[l]);
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 2.0 : 3.0) * Np * sizeof(T),
+                     (zero ? 1.0 : nb_ops(DIM) + 4.0) * Np, sizeof(T) == 8);
+        k_jacobi<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(c), T(d), T(ctx->opt.omega / d), x, b,
+                                                                        out, zero ? 1 : 0);
+      }
+      LAUNCH_CHECK(ctx);
+      x = out;
+    } else {
+      const T cd = T(c / d), id = T(1.0 / d);
+      const double Np = double(H.npts[l]);
+      {
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 1.0 : 1.5) * Np * sizeof(T),
+                     (zero ? 1.0 : nb_ops(DIM) + 2.0) * 0.5 * Np, sizeof(T) == 8);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, cd, id, 0, x, b, zero ? 1 : 0);
+      }
+      LAUNCH_CHECK(ctx);
+      {
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), (nb_ops(DIM) + 2.0) * 0.5 * Np,
+                     sizeof(T) == 8);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, cd, id, 1, x, b, 0);
+      }
+      LAUNCH_CHECK(ctx);
+    }
+    zero = false;
+  }
+  return ISDC_OK;
+}
+
+template <typename T, int DIM>
+isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T* b0, bool zero0) {
+  T* xcur[kMaxLevels];
+  isdc_status st;
+  // downward leg on the levels above the bottom block
+  for (int l = 0; l < H.lb; ++l) {
+    T* home = (l == 0) ? x0 : H.x[l];
+    T* x = home;
+    const T* b = (l == 0) ? b0 : H.b[l];
+    bool zero = (l == 0) ? zero0 : true;
+    const int s = H.side[l];
+    if (ctx->opt.nu1 == 0 && zero) {
+      CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(T), ctx->stream));
+      zero = false;
+    }
+    if ((st = smooth_level<T, DIM>(ctx, H, l, a, x, home, b, zero, ctx->opt.nu1)) != ISDC_OK) return st;
+    const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+    const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+    {
+      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * Np * sizeof(T), (nb_ops(DIM) + 3.0) * Np,
+                   sizeof(T) == 8);
+      k_residual<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(c), T(d), x, b, H.r[l]);
+    }
+    LAUNCH_CHECK(ctx);
+    const int sc = H.side[l + 1];
+    {
+      ProfScope ps(ctx, l == 0 ? PC_RESTRICT0 : PC_RESTRICTC, (Np + Nc) * sizeof(T), (DIM == 2 ? 9.0 : 27.0) * Nc,
+                   sizeof(T) == 8);
+      k_restrict<T, DIM><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, H.r[l], H.b[l + 1]);
+    }
+    LAUNCH_CHECK(ctx);
+    xcur[l] = x;
+  }
+  // bottom levels in one block
+  {
+    BottomParams<T> P{};
+    P.nlev = H.nlev - H.lb;
+    for (int q = 0; q < P.nlev; ++q) {
+      const int s = H.side[H.lb + q];
+      const double h = 1.0 / (s + 1), c = a / (h * h);
+      P.side[q] = s;
+      P.c[q] = T(c);
+      P.d[q] = T(1.0 + 2.0 * DIM * c);
+    }
+    P.smoother = ctx->opt.smoother;
+    P.nu1 = ctx->opt.nu1;
+    P.nu2 = ctx->opt.nu2;
+    P.omega = T(ctx->opt.omega);
+    P.Ainv = H.Ainv + size_t(slot) * (DIM == 2 ? 81 : 729);
+    const T* bb = H.lb == 0 ? b0 : H.b[H.lb];
+    T* xb = H.lb == 0 ? x0 : H.x[H.lb];
+    const int load_x = (H.lb == 0 && !zero0) ? 1 : 0;
+    {
+      ProfScope ps(ctx, PC_BOTTOM, (2.0 + load_x) * double(H.npts[H.lb]) * sizeof(T), 0.0, sizeof(T) == 8);
+      k_bottom<T, DIM><<<1, kBottomThreads, H.bottom_smem, ctx->stream>>>(P, bb, xb, load_x);
+    }
+    LAUNCH_CHECK(ctx);
+    xcur[H.lb] = xb;
+  }
+  // upward leg
+  for (int l = H.lb - 1; l >= 0; --l) {
+    const int sc = H.side[l + 1], s = H.side[l];
+    T* home = (l == 0) ? x0 : H.x[l];
+    T* x = xcur[l];
+    {
+      const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+      ProfScope ps(ctx, l == 0 ? PC_PROLONG0 : PC_PROLONGC, (2.0 * Np + Nc) * sizeof(T),
+                   (DIM == 2 ? 6.25 : 8.875) * Np, sizeof(T) == 8);
+      k_prolong_add<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
+    }
+    LAUNCH_CHECK(ctx);
+    bool zero = false;
+    if ((st = smooth_level<T, DIM>(ctx, H, l, a, x, home, l == 0 ? b0 : H.b[l], zero, ctx->opt.nu2)) != ISDC_OK)
+      return st;
+    xcur[l] = x;
+  }
+  if (xcur[0] != x0)
+    CUDA_TRY(ctx, cudaMemcpyAsync(x0, xcur[0], H.npts[0] * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+  return ISDC_OK;
+}
+
+// One V-cycle of the node solve with unknown x (FP64 device array) in the
+// context's precision.
+template <int DIM>
+isdc_status node_vcycle(isdc_ctx* ctx, int slot, double a, double* x, const double* b) {
+  if (!ctx->opt.vcycle_fp32) return vcycle<double, DIM>(ctx, ctx->h64, slot, a, x, b, false);
+  // defect correction: r = b - H x in FP64 -> FP32, FP32 V-cycle on H e = r from e = 0, x += e
+  const int s = ctx->n;
+  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  Hier<float>& H = ctx->h32;
+  const double Np = double(ctx->N);
+  {
+    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 3.0) * Np, true);
+    k_defect<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, c, d, x, b, H.b[0]);
+  }
+  LAUNCH_CHECK(ctx);
+  isdc_status st = vcycle<float, DIM>(ctx, H, slot, a, H.x[0], H.b[0], true);
+  if (st != ISDC_OK) return st;
+  {
+    ProfScope ps(ctx, PC_UPDATE, 20.0 * Np, 1.0 * Np, true);
+    k_update<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, x, H.x[0]);
+  }
+  LAUNCH_CHECK(ctx);
+  return ISDC_OK;
+}
+
+template <int DIM>
+isdc_status node_residual_norm(isdc_ctx* ctx, double a, const double* x, const double* b, double* out) {
+  const int s = ctx->n;
+  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal + 1, 0, sizeof(unsigned long long), ctx->stream));
+  {
+    ProfScope ps(ctx, PC_RESNORM, 16.0 * double(ctx->N), (nb_ops(DIM) + 3.0) * double(ctx->N), true);
+    k_resnorm<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, c, d, x, b, ctx->d_scal + 1);
+  }
+  LAUNCH_CHECK(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  unsigned long long bits = ctx->h_scal[1];
+  std::memcpy(out, &bits, sizeof(double));
+  return ISDC_OK;
+}
+
+inline double bits_to_double(unsigned long long b) {
+  double v;
+  std::memcpy(&v, &b, sizeof v);
+  return v;
+}
+
+template <int DIM>
+isdc_status sweep_end(isdc_ctx* ctx) {
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
+  const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
+  {
+    const double M = ctx->M, Np = double(ctx->N);
+    ProfScope ps(ctx, PC_SWEEP_END, (3.0 * M - 1.0) * 8.0 * Np, (2.0 * M * M + 7.0 * M - 1.0 + nb_ops(DIM)) * Np,
+                 true);
+    k_sweep_end<DIM><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->N, nu_h2, ctx->opt.reaction,
+                                                                      ctx->tables, ctx->U, ctx->F, ctx->C,
+                                                                      ctx->d_scal);
+  }
+  LAUNCH_CHECK(ctx);
+  return ISDC_OK;
+}
+
+template <int DIM>
+isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
+  const int n = ctx->n, M = ctx->M;
+  const size_t N = ctx->N;
+  const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
+  isdc_status st;
+  if (ctx->nodes_pending) {
+    for (int m = 0; m < M; ++m) {
+      {
+        ProfScope ps(ctx, PC_EVAL_F, 16.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
+        k_eval_f<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, ctx->U + m * N,
+                                                                   ctx->F + m * N);
+      }
+      LAUNCH_CHECK(ctx);
+    }
+    ctx->nodes_pending = 0;
+  } else {
+    {
+      ProfScope ps(ctx, PC_SPREAD, (1.0 + 2.0 * M) * 8.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
+      k_spread<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, ctx->opt.reaction, M, u, ctx->U,
+                                                                 ctx->F);
+    }
+    LAUNCH_CHECK(ctx);
+  }
+  if ((st = sweep_end<DIM>(ctx)) != ISDC_OK) return st;  // C_m of the first sweep
+
+  const bool until_tol = n_sweeps <= 0;
+  const int cap = until_tol ? ctx->opt.max_sweeps : n_sweeps;
+  long long vcycles = 0;
+  int k = 0;
+  isdc_status result = ISDC_OK;
+  ctx->hist_count = 0;
+  for (;;) {
+    for (int m = 0; m < M - 1; ++m) {
+      const double dtm = ctx->tables.dtm[m];
+      {
+        ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
+                     (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
+        k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, ctx->U + m * N,
+                                                                ctx->C + m * N, ctx->b,
+                                                                m >= 1 ? ctx->F + m * N : nullptr);
+      }
+      LAUNCH_CHECK(ctx);
+      double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
+      const double a = dtm * ctx->nu;
+      if (n_vcycles > 0) {
+        for (int c = 0; c < n_vcycles; ++c)
+          if ((st = node_vcycle<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+        vcycles += n_vcycles;
+      } else {  // classical SDC: multigrid to a tolerance (Sec. 3)
+        for (int c = 0; c < ctx->opt.mg_max_cycles; ++c) {
+          double rn;
+          if ((st = node_residual_norm<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
+          if (!(rn > ctx->opt.mg_tol)) break;
+          if ((st = node_vcycle<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+          ++vcycles;
+        }
+      }
+    }
+    ++k;
+    if ((st = sweep_end<DIM>(ctx)) != ISDC_OK) return st;
+    if (until_tol || ctx->record_history) {
+      if (k - 1 < ctx->hist_cap)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_hist + (k - 1), ctx->d_scal, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+      ctx->hist_count = std::min(k, ctx->hist_cap);
+    }
+    if (until_tol) {
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      const double R = bits_to_double(ctx->h_hist[k - 1]);
+      if (!std::isfinite(R)) { result = fail(ctx, ISDC_ERR_NONFINITE, "SDC residual is %g after sweep %d", R, k); break; }
+      if (R < ctx->opt.tol) break;
+      if (k >= cap) {
+        result = fail(ctx, ISDC_ERR_NOT_CONVERGED, "SDC residual %g >= tol %g after %d sweeps", R, ctx->opt.tol, k);
+        break;
+      }
+    } else if (k >= cap) {
+      break;
+    }
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(u, ctx->U + (M - 1) * N, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->last_sweeps = k;
+  ctx->last_vcycles = vcycles;
+  return result;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
+  if (!opt) return ISDC_ERR_INVALID_ARG;
+  opt->smoother = ISDC_SMOOTHER_JACOBI;
+  opt->nu1 = 1;
+  opt->nu2 = 1;
+  opt->omega = 2.0 / 3.0;
+  opt->vcycle_fp32 = 0;
+  opt->reaction = ISDC_REACTION_ALLEN_CAHN;
+  opt->tol = 1e-10;
+  opt->max_sweeps = 100;
+  opt->mg_tol = 1e-12;
+  opt->mg_max_cycles = 50;
+  opt->stream = nullptr;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double* tau, double* Q, double* S) {
+  if (nodes != ISDC_NODES_GAUSS_LOBATTO) {
+    snprintf(g_create_error, sizeof g_create_error, "only Gauss-Lobatto nodes are implemented");
+    return ISDC_ERR_UNSUPPORTED;
+  }
+  if (M < 2 || M > kMaxM || !tau || !Q) {
+    snprintf(g_create_error, sizeof g_create_error, "M must be in [2, %d] and tau, Q non-NULL", kMaxM);
+    return ISDC_ERR_INVALID_ARG;
+  }
+  lobatto_nodes(M, tau);
+  q_matrix(M, tau, Q);
+  if (S)
+    for (int m = 0; m < M - 1; ++m)
+      for (int j = 0; j < M; ++j) S[m * M + j] = Q[(m + 1) * M + j] - Q[m * M + j];
+  return ISDC_OK;
+}
+
+ISDC_API void isdc_destroy(isdc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->U);
+  cudaFree(ctx->F);
+  cudaFree(ctx->C);
+  cudaFree(ctx->b);
+  cudaFree(ctx->u_dev);
+  free_hier(ctx->h64, false);
+  free_hier(ctx->h32, true);
+  cudaFree(ctx->d_scal);
+  cudaFreeHost(ctx->h_scal);
+  cudaFreeHost(ctx->h_hist);
+  for (auto& r : ctx->prof.pool) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_node_type nodes, int M, double dt,
+                                 const isdc_options* opt, isdc_ctx** out) {
+  if (!out) return fail(nullptr, ISDC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return fail(nullptr, ISDC_ERR_INVALID_ARG, "ndim must be 2 or 3 (got %d)", ndim);
+  if (!dims) return fail(nullptr, ISDC_ERR_INVALID_ARG, "dims is NULL");
+  const int64_t n = dims[0];
+  for (int a = 1; a < ndim; ++a)
+    if (dims[a] != n) return fail(nullptr, ISDC_ERR_UNSUPPORTED, "only equal sides are implemented");
+  if (n < 3 || ((n + 1) & n) != 0) return fail(nullptr, ISDC_ERR_INVALID_ARG, "side must be 2^j - 1 with j >= 2 (got %lld)", (long long)n);
+  if ((ndim == 2 && n > 46339) || (ndim == 3 && n > 1289))
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "grid too large for 32-bit point indices");
+  if (nodes != ISDC_NODES_GAUSS_LOBATTO) return fail(nullptr, ISDC_ERR_UNSUPPORTED, "only Gauss-Lobatto nodes are implemented");
+  if (M < 2 || M > kMaxM) return fail(nullptr, ISDC_ERR_INVALID_ARG, "M must be in [2, %d] (got %d)", kMaxM, M);
+  if (!(nu > 0) || !std::isfinite(nu) || !(dt > 0) || !std::isfinite(dt))
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "nu and dt must be positive and finite");
+  isdc_options o;
+  if (opt) o = *opt; else isdc_default_options(&o);
+  if (o.smoother != ISDC_SMOOTHER_JACOBI && o.smoother != ISDC_SMOOTHER_RBGS)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown smoother %d", o.smoother);
+  if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "nu1, nu2 must be in [0, 16] with nu1 + nu2 >= 1");
+  if (o.reaction != ISDC_REACTION_NONE && o.reaction != ISDC_REACTION_ALLEN_CAHN)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown reaction %d", o.reaction);
+  if (o.max_sweeps < 1 || o.max_sweeps > 100000 || o.mg_max_cycles < 1)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps and mg_max_cycles must be >= 1");
+
+  isdc_ctx* ctx = new isdc_ctx();
+  ctx->dim = ndim;
+  ctx->n = int(n);
+  ctx->N = pow_dim(ndim, size_t(n));
+  ctx->M = M;
+  ctx->nu = nu;
+  ctx->dt = dt;
+  ctx->h = 1.0 / double(n + 1);
+  ctx->opt = o;
+  auto bail = [&](isdc_status st) {
+    snprintf(g_create_error, sizeof g_create_error, "%s", ctx->err);
+    isdc_destroy(ctx);
+    return st;
+  };
+  if (o.stream) {
+    ctx->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      fail(ctx, ISDC_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+      return bail(ISDC_ERR_CUDA);
+    }
+    ctx->own_stream = true;
+  }
+  lobatto_nodes(M, ctx->tau);
+  q_matrix(M, ctx->tau, ctx->Q);
+  for (int m = 0; m < M - 1; ++m)
+    for (int j = 0; j < M; ++j) ctx->S[m * M + j] = ctx->Q[(m + 1) * M + j] - ctx->Q[m * M + j];
+  ctx->tables.M = M;
+  for (int m = 0; m < M; ++m)
+    for (int j = 0; j < M; ++j) {
+      ctx->tables.dtQ[m][j] = dt * ctx->Q[m * M + j];
+      if (m < M - 1) ctx->tables.dtS[m][j] = dt * ctx->S[m * M + j];
+    }
+  for (int m = 0; m < M - 1; ++m) ctx->tables.dtm[m] = dt * (ctx->tau[m + 1] - ctx->tau[m]);
+
+  const size_t N = ctx->N;
+  isdc_status st;
+#define CREATE_TRY(call)                                      \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      isdc_status s_ = e_ == cudaErrorMemoryAllocation ? ISDC_ERR_OOM : ISDC_ERR_CUDA; \
+      fail(ctx, s_, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return bail(s_);                                        \
+    }                                                         \
+  } while (0)
+  CREATE_TRY(cudaMalloc(&ctx->U, size_t(M) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->F, size_t(M) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->C, size_t(M - 1) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->b, N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->d_scal, 4 * sizeof(unsigned long long)));
+  CREATE_TRY(cudaMemset(ctx->d_scal, 0, 4 * sizeof(unsigned long long)));
+  CREATE_TRY(cudaMallocHost(&ctx->h_scal, 4 * sizeof(unsigned long long)));
+  ctx->hist_cap = std::max(o.max_sweeps, 1) + 1;
+  CREATE_TRY(cudaMallocHost(&ctx->h_hist, size_t(ctx->hist_cap) * sizeof(unsigned long long)));
+  if (o.vcycle_fp32) {
+    if ((st = alloc_hier(ctx, ctx->h32, true)) != ISDC_OK) return bail(st);
+    if (ndim == 2) configure_bottom<float, 2>(ctx->h32); else configure_bottom<float, 3>(ctx->h32);
+    for (int m = 0; m < M - 1; ++m)
+      if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
+  } else {
+    if ((st = alloc_hier(ctx, ctx->h64, false)) != ISDC_OK) return bail(st);
+    if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
+    for (int m = 0; m < M - 1; ++m)
+      if ((st = upload_ainv(ctx, ctx->h64, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
+  }
+  ctx->spare_slot = M - 1;
+  CREATE_TRY(cudaGetLastError());
+#undef CREATE_TRY
+  *out = ctx;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  if (!u) return fail(ctx, ISDC_ERR_INVALID_ARG, "u is NULL");
+  if (n_sweeps < 0 || n_vcycles < 0) return fail(ctx, ISDC_ERR_INVALID_ARG, "n_sweeps and n_vcycles must be >= 0");
+  return ctx->dim == 2 ? run_step<2>(ctx, u, n_sweeps, n_vcycles) : run_step<3>(ctx, u, n_sweeps, n_vcycles);
+}
+
+ISDC_API isdc_status isdc_step_host(isdc_ctx* ctx, double* u_host, int n_sweeps, int n_vcycles) {
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  if (!u_host) return fail(ctx, ISDC_ERR_INVALID_ARG, "u_host is NULL");
+  if (!ctx->u_dev) CUDA_TRY(ctx, cudaMalloc(&ctx->u_dev, ctx->N * sizeof(double)));
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->u_dev, u_host, ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  isdc_status st = isdc_step(ctx, ctx->u_dev, n_sweeps, n_vcycles);
+  if (st != ISDC_OK && st != ISDC_ERR_NOT_CONVERGED && st != ISDC_ERR_NONFINITE) return st;
+  CUDA_TRY(ctx, cudaMemcpyAsync(u_host, ctx->u_dev, ctx->N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return st;
+}
+
+ISDC_API isdc_status isdc_residual(const isdc_ctx* cctx, double* res) {
+  isdc_ctx* ctx = const_cast<isdc_ctx*>(cctx);
+  if (!ctx || !res) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  *res = bits_to_double(ctx->h_scal[0]);
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_stats(const isdc_ctx* cctx, int* sweeps, int64_t* vcycles) {
+  isdc_ctx* ctx = const_cast<isdc_ctx*>(cctx);
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (sweeps) *sweeps = ctx->last_sweeps;
+  if (vcycles) *vcycles = ctx->last_vcycles;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_residual_history(const isdc_ctx* cctx, double* hist, int cap, int* count) {
+  isdc_ctx* ctx = const_cast<isdc_ctx*>(cctx);
+  if (!ctx || (!hist && cap > 0)) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int c = std::min(cap, ctx->hist_count);
+  for (int q = 0; q < c; ++q) hist[q] = bits_to_double(ctx->h_hist[q]);
+  if (count) *count = ctx->hist_count;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_set_record_history(isdc_ctx* ctx, int record) {
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  ctx->record_history = record ? 1 : 0;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_get_nodes(const isdc_ctx* cctx, double* dst) {
+  isdc_ctx* ctx = const_cast<isdc_ctx*>(cctx);
+  if (!ctx || !dst) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->U, size_t(ctx->M) * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_set_nodes(isdc_ctx* ctx, const double* src) {
+  if (!ctx || !src) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, src, size_t(ctx->M) * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  ctx->nodes_pending = 1;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_vcycles(isdc_ctx* ctx, double a, double* x, const double* b, int n_cycles) {
+  if (!ctx || !x || !b) return ISDC_ERR_INVALID_ARG;
+  if (!(a > 0) || !std::isfinite(a) || n_cycles < 0) return fail(ctx, ISDC_ERR_INVALID_ARG, "need a > 0, n_cycles >= 0");
+  isdc_status st;
+  if (ctx->opt.vcycle_fp32) st = upload_ainv(ctx, ctx->h32, ctx->spare_slot, a);
+  else st = upload_ainv(ctx, ctx->h64, ctx->spare_slot, a);
+  if (st != ISDC_OK) return st;
+  for (int c = 0; c < n_cycles; ++c) {
+    st = ctx->dim == 2 ? node_vcycle<2>(ctx, ctx->spare_slot, a, x, b) : node_vcycle<3>(ctx, ctx->spare_slot, a, x, b);
+    if (st != ISDC_OK) return st;
+  }
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_profile_enable(isdc_ctx* ctx, int enable) {
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  prof_flush(ctx);
+  Profiler& P = ctx->prof;
+  if (enable) {
+    std::fill(P.ms, P.ms + PC_COUNT, 0.0);
+    std::fill(P.bytes, P.bytes + PC_COUNT, 0.0);
+    std::fill(P.dp_ops, P.dp_ops + PC_COUNT, 0.0);
+    std::fill(P.sp_ops, P.sp_ops + PC_COUNT, 0.0);
+    std::fill(P.launches, P.launches + PC_COUNT, 0LL);
+  }
+  P.on = enable != 0;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_profile_read(isdc_ctx* ctx, isdc_kernel_stat* out, int cap, int* count) {
+  if (!ctx || (!out && cap > 0)) return ISDC_ERR_INVALID_ARG;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  const Profiler& P = ctx->prof;
+  int c = 0;
+  for (int k = 0; k < PC_COUNT; ++k) {
+    if (!P.launches[k]) continue;
+    if (c < cap) {
+      isdc_kernel_stat& o = out[c];
+      std::memset(&o, 0, sizeof o);
+      snprintf(o.name, sizeof o.name, "%s", kProfNames[k]);
+      o.launches = P.launches[k];
+      o.total_ms = P.ms[k];
+      o.bytes = P.bytes[k];
+      o.fp64_ops = P.dp_ops[k];
+      o.fp32_ops = P.sp_ops[k];
+    }
+    ++c;
+  }
+  if (count) *count = c;
+  return ISDC_OK;
+}
+
+ISDC_API const char* isdc_last_error(const isdc_ctx* ctx) { return ctx ? ctx->err : g_create_error; }

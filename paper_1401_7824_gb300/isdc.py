@@ -1,0 +1,297 @@
+"""Thin ctypes binding of the C ABI in include/isdc.h (libisdc.so).
+
+Every function has the name of the C entry point it calls and only marshals
+arguments (torch tensors -> device pointers, options -> the C struct).  All
+compute runs in the CUDA kernels of libisdc.so; there is no fallback: if the
+library cannot be loaded, or a tensor is not a contiguous float64 CUDA
+tensor, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+ISDC_OK = 0
+ISDC_ERR_INVALID_ARG = 1
+ISDC_ERR_UNSUPPORTED = 2
+ISDC_ERR_OOM = 3
+ISDC_ERR_CUDA = 4
+ISDC_ERR_NOT_CONVERGED = 5
+ISDC_ERR_NONFINITE = 6
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
+                6: "NONFINITE"}
+
+ISDC_NODES_GAUSS_LOBATTO = 0
+ISDC_NODES_RADAU_RIGHT = 1
+ISDC_NODES_GAUSS_LEGENDRE = 2
+ISDC_SMOOTHER_JACOBI = 0
+ISDC_SMOOTHER_RBGS = 1
+ISDC_REACTION_NONE = 0
+ISDC_REACTION_ALLEN_CAHN = 1
+
+
+class isdc_options(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega", ctypes.c_double), ("vcycle_fp32", ctypes.c_int), ("reaction", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
+                ("mg_max_cycles", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class isdc_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("fp64_ops", ctypes.c_double), ("fp32_ops", ctypes.c_double)]
+
+
+class IsdcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_ctx_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libisdc.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    I, D, V = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "isdc_default_options": (I, [ctypes.POINTER(isdc_options)]),
+        "isdc_collocation_tables": (I, [I, I, _dp, _dp, _dp]),
+        "isdc_create": (I, [I, ctypes.POINTER(ctypes.c_int64), D, I, I, D, ctypes.POINTER(isdc_options),
+                            ctypes.POINTER(_ctx_p)]),
+        "isdc_step": (I, [_ctx_p, V, I, I]),
+        "isdc_step_host": (I, [_ctx_p, V, I, I]),
+        "isdc_residual": (I, [_ctx_p, _dp]),
+        "isdc_stats": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),
+        "isdc_residual_history": (I, [_ctx_p, _dp, I, ctypes.POINTER(I)]),
+        "isdc_set_record_history": (I, [_ctx_p, I]),
+        "isdc_get_nodes": (I, [_ctx_p, V]),
+        "isdc_set_nodes": (I, [_ctx_p, V]),
+        "isdc_vcycles": (I, [_ctx_p, D, V, V, I]),
+        "isdc_profile_enable": (I, [_ctx_p, I]),
+        "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
+        "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
+        "isdc_destroy": (None, [_ctx_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, ctx=None, soft=()):
+    if st != ISDC_OK and st not in soft:
+        raise IsdcError(st, load().isdc_last_error(ctx).decode(errors="replace"))
+    return st
+
+
+def _dev_ptr(t, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} values, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --- C entry points ---------------------------------------------------------
+def isdc_default_options() -> isdc_options:
+    o = isdc_options()
+    _check(load().isdc_default_options(ctypes.byref(o)))
+    return o
+
+
+def isdc_collocation_tables(M: int, nodes: int = ISDC_NODES_GAUSS_LOBATTO):
+    """Host-only tables (tau, Q, S) as nested lists."""
+    tau = (ctypes.c_double * M)()
+    Q = (ctypes.c_double * (M * M))()
+    S = (ctypes.c_double * ((M - 1) * M))()
+    _check(load().isdc_collocation_tables(nodes, M, tau, Q, S))
+    return (list(tau), [list(Q[m * M:(m + 1) * M]) for m in range(M)],
+            [list(S[m * M:(m + 1) * M]) for m in range(M - 1)])
+
+
+def isdc_create(ndim, n, nu, M, dt, options: isdc_options | None = None,
+                nodes: int = ISDC_NODES_GAUSS_LOBATTO):
+    dims = (ctypes.c_int64 * ndim)(*([n] * ndim))
+    out = _ctx_p()
+    st = load().isdc_create(ndim, dims, nu, nodes, M, dt,
+                            ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def isdc_step(ctx, u, n_sweeps: int, n_vcycles: int) -> int:
+    """u: float64 CUDA tensor (n^ndim values).  Returns OK or NOT_CONVERGED."""
+    return _check(load().isdc_step(ctx, _dev_ptr(u), n_sweeps, n_vcycles), ctx, soft=(ISDC_ERR_NOT_CONVERGED,))
+
+
+def isdc_step_host(ctx, u_host, n_sweeps: int, n_vcycles: int) -> int:
+    """u_host: contiguous float64 host buffer (numpy array or CPU tensor)."""
+    import numpy as np
+    if isinstance(u_host, np.ndarray):
+        if u_host.dtype != np.float64 or not u_host.flags.c_contiguous:
+            raise TypeError("expected a contiguous float64 array")
+        ptr = ctypes.c_void_p(u_host.ctypes.data)
+    else:
+        import torch
+        if u_host.is_cuda or u_host.dtype != torch.float64 or not u_host.is_contiguous():
+            raise TypeError("expected a contiguous float64 CPU tensor")
+        ptr = ctypes.c_void_p(u_host.data_ptr())
+    return _check(load().isdc_step_host(ctx, ptr, n_sweeps, n_vcycles), ctx, soft=(ISDC_ERR_NOT_CONVERGED,))
+
+
+def isdc_residual(ctx) -> float:
+    r = ctypes.c_double()
+    _check(load().isdc_residual(ctx, ctypes.byref(r)), ctx)
+    return r.value
+
+
+def isdc_stats(ctx):
+    s, v = ctypes.c_int(), ctypes.c_int64()
+    _check(load().isdc_stats(ctx, ctypes.byref(s), ctypes.byref(v)), ctx)
+    return s.value, v.value
+
+
+def isdc_residual_history(ctx, cap: int = 100000):
+    cnt = ctypes.c_int()
+    _check(load().isdc_residual_history(ctx, None, 0, ctypes.byref(cnt)), ctx)
+    buf = (ctypes.c_double * max(1, min(cap, cnt.value)))()
+    _check(load().isdc_residual_history(ctx, buf, min(cap, cnt.value), ctypes.byref(cnt)), ctx)
+    return list(buf[:min(cap, cnt.value)])
+
+
+def isdc_set_record_history(ctx, record: bool):
+    _check(load().isdc_set_record_history(ctx, 1 if record else 0), ctx)
+
+
+def isdc_get_nodes(ctx, dst):
+    _check(load().isdc_get_nodes(ctx, _dev_ptr(dst)), ctx)
+
+
+def isdc_set_nodes(ctx, src):
+    _check(load().isdc_set_nodes(ctx, _dev_ptr(src)), ctx)
+
+
+def isdc_vcycles(ctx, a: float, x, b, n_cycles: int):
+    _check(load().isdc_vcycles(ctx, a, _dev_ptr(x), _dev_ptr(b, x.numel()), n_cycles), ctx)
+
+
+def isdc_profile_enable(ctx, enable: bool):
+    _check(load().isdc_profile_enable(ctx, 1 if enable else 0), ctx)
+
+
+def isdc_profile_read(ctx):
+    """{class name: dict(launches, total_ms, bytes, fp64_ops, fp32_ops)}"""
+    cnt = ctypes.c_int()
+    buf = (isdc_kernel_stat * 64)()
+    _check(load().isdc_profile_read(ctx, buf, 64, ctypes.byref(cnt)), ctx)
+    out = {}
+    for r in buf[:min(cnt.value, 64)]:
+        out[r.name.decode()] = dict(launches=r.launches, total_ms=r.total_ms, bytes=r.bytes,
+                                    fp64_ops=r.fp64_ops, fp32_ops=r.fp32_ops)
+    return out
+
+
+def isdc_last_error(ctx=None) -> str:
+    return load().isdc_last_error(ctx).decode(errors="replace")
+
+
+def isdc_destroy(ctx):
+    if ctx:
+        load().isdc_destroy(ctx)
+
+
+# --- convenience wrapper ------------------------------------------------------
+class Isdc:
+    """One ISDC problem on the GPU.  By default it runs on torch's current
+    CUDA stream so that torch events and tensors order with it."""
+
+    def __init__(self, ndim, n, nu, M, dt, *, smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1,
+                 omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
+                 max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, stream=None):
+        import torch
+        o = isdc_default_options()
+        o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
+        o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
+        o.mg_tol, o.mg_max_cycles = mg_tol, mg_max_cycles
+        s = stream if stream is not None else torch.cuda.current_stream()
+        # torch's default stream has handle 0, which the C ABI reads as "create a
+        # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.
+        o.stream = ctypes.c_void_p(s.cuda_stream if s.cuda_stream else 1)
+        self.stream = s
+        self.ndim, self.n, self.M = ndim, n, M
+        self.N = n ** ndim
+        self.ctx = isdc_create(ndim, n, nu, M, dt, o)
+
+    def step(self, u, n_sweeps=0, n_vcycles=2):
+        return isdc_step(self.ctx, u, n_sweeps, n_vcycles)
+
+    def step_host(self, u_host, n_sweeps=0, n_vcycles=2):
+        return isdc_step_host(self.ctx, u_host, n_sweeps, n_vcycles)
+
+    def residual(self):
+        return isdc_residual(self.ctx)
+
+    def stats(self):
+        return isdc_stats(self.ctx)
+
+    def history(self):
+        return isdc_residual_history(self.ctx)
+
+    def record_history(self, on=True):
+        isdc_set_record_history(self.ctx, on)
+
+    def nodes(self):
+        import torch
+        out = torch.empty((self.M,) + (self.n,) * self.ndim, dtype=torch.float64, device="cuda")
+        isdc_get_nodes(self.ctx, out)
+        return out
+
+    def set_nodes(self, nodes):
+        isdc_set_nodes(self.ctx, nodes.contiguous())
+
+    def vcycles(self, a, x, b, n_cycles):
+        isdc_vcycles(self.ctx, a, x, b, n_cycles)
+
+    def profile(self, on=True):
+        isdc_profile_enable(self.ctx, on)
+
+    def profile_read(self):
+        return isdc_profile_read(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            isdc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

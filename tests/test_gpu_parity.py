@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances: FP64 path relative L2 <= 1e-12 per step;
+FP32-V-cycle path relative L2 <= 1e-9 once both reach SDC residual <= 1e-10."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import make_gpu, rel_l2, to_dev
+from isdc_inputs import initial_condition, workload_2d_127, workload_3d_255
+
+pytestmark = pytest.mark.gpu
+
+J, RB = O.SMOOTHER_JACOBI, O.SMOOTHER_RBGS
+
+
+# --- V-cycles on one implicit Euler system (Sec. 3) ---------------------------
+VCYCLE_CASES = [
+    # ndim, n, smoother, nu1, nu2, a
+    (2, 63, J, 1, 1, 0.01),
+    (2, 127, RB, 2, 2, 0.003),
+    (2, 255, J, 1, 2, 0.02),     # odd sweep count: result lands in the ping-pong buffer
+    (3, 31, RB, 2, 2, 0.004),
+    (3, 63, J, 1, 1, 0.001),
+    (3, 15, RB, 0, 2, 0.05),     # no pre-smoothing
+    (3, 7, RB, 2, 2, 0.3),       # bottom block only
+    (2, 3, J, 1, 1, 0.7),        # coarsest grid only: exact solve
+    (3, 127, RB, 2, 2, 0.0005),
+]
+
+
+@pytest.mark.parametrize("case", VCYCLE_CASES)
+def test_vcycles_match_oracle_fp64(case):
+    d, n, sm, nu1, nu2, a = case
+    p = O.Problem(d, n, 0.1, 3, 0.05, smoother=sm, nu1=nu1, nu2=nu2)
+    rng = np.random.default_rng(n * 7 + d)
+    x0 = rng.standard_normal(p.shape)
+    b = rng.standard_normal(p.shape)
+    ref = x0.copy()
+    for _ in range(3):
+        ref = O.vcycle(p, a, ref, b)
+    g = make_gpu(p)
+    x = to_dev(x0)
+    g.vcycles(a, x, to_dev(b), 3)
+    got = x.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", VCYCLE_CASES[:6])
+def test_vcycles_fp32_defect_correction(case):
+    d, n, sm, nu1, nu2, a = case
+    p = O.Problem(d, n, 0.1, 3, 0.05, smoother=sm, nu1=nu1, nu2=nu2)
+    rng = np.random.default_rng(n * 11 + d)
+    x0, b = rng.standard_normal(p.shape), rng.standard_normal(p.shape)
+    ref = O.vcycle(p, a, x0, b)
+    g = make_gpu(p, vcycle_fp32=True)
+    x = to_dev(x0)
+    g.vcycles(a, x, to_dev(b), 1)
+    got = x.cpu().numpy()
+    # one FP32 cycle on the error: FP32 rounding of the correction only
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref - x0).max()
+
+
+# --- whole time steps (Sec. 2 Eq. 4, Sec. 3) ----------------------------------
+STEP_CASES = [
+    # ndim, n, nu, M, dt, reaction, smoother, nu1, nu2, L
+    (2, 63, 0.1, 3, 0.05, O.REACTION_ALLEN_CAHN, J, 1, 1, 2),
+    (3, 31, 0.1, 5, 0.02, O.REACTION_ALLEN_CAHN, RB, 2, 2, 2),
+    (2, 31, 0.5, 7, 0.01, O.REACTION_ALLEN_CAHN, RB, 2, 2, 1),
+    (3, 15, 0.05, 3, 0.05, O.REACTION_NONE, J, 1, 1, 2),
+    (2, 127, 1.0, 2, 0.002, O.REACTION_ALLEN_CAHN, RB, 1, 1, 3),
+    (3, 63, 0.3, 3, 0.01, O.REACTION_ALLEN_CAHN, J, 2, 1, 2),
+]
+
+
+@pytest.mark.parametrize("case", STEP_CASES)
+def test_steps_match_oracle_fp64(case):
+    d, n, nu, M, dt, reaction, sm, nu1, nu2, L = case
+    p = O.Problem(d, n, nu, M, dt, reaction=reaction, smoother=sm, nu1=nu1, nu2=nu2, max_sweeps=100)
+    u0 = initial_condition(d, n, seed=100 + n + d)
+    ref = O.integrate(p, u0, 3, 0, L)
+    g = make_gpu(p)
+    g.record_history(True)
+    u = to_dev(u0)
+    for s in range(3):
+        g.step(u, ref.sweeps[s], L)
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-12
+        hist = g.history()
+        np.testing.assert_allclose(hist, ref.residuals[s], rtol=1e-6, atol=1e-14)
+
+
+def test_workload_2d_127_ten_steps():
+    """The 127^2 workload at full size: 10 steps, sweeps to residual 1e-10."""
+    w = workload_2d_127()
+    p = O.Problem(2, w.n, w.nu, w.M, w.dt, smoother=J, max_sweeps=100)
+    u0 = initial_condition(2, w.n, w.seed)
+    ref = O.integrate(p, u0, w.steps, 0, w.n_vcycles)
+    assert all(s == 0 for s in ref.status)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    for s in range(w.steps):
+        g.step(u, ref.sweeps[s], w.n_vcycles)
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-12
+    # the until-tolerance mode reaches the same collocation solution
+    u2 = to_dev(u0)
+    for s in range(w.steps):
+        g.step(u2, 0, w.n_vcycles)
+        sweeps, vcyc = g.stats()
+        assert abs(sweeps - ref.sweeps[s]) <= 1 and vcyc == sweeps * (w.M - 1) * w.n_vcycles
+        assert g.residual() < w.tol
+    assert rel_l2(u2.cpu().numpy(), ref.u) <= 1e-9
+
+
+def test_workload_3d_255_one_sweep_full_size():
+    """The 255^3, M=5, V(2,2) red-black Gauss-Seidel workload at full size:
+    one sweep element by element against the oracle."""
+    w = workload_3d_255()
+    p = O.Problem(3, w.n, w.nu, w.M, w.dt, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, w.n, w.seed)
+    ref = O.isdc_step(p, u0, 1, w.n_vcycles, want_nodes=True)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    g.step(u, 1, w.n_vcycles)
+    nodes = g.nodes().cpu().numpy()
+    for m in range(w.M):
+        assert rel_l2(nodes[m], ref.nodes[m]) <= 1e-12
+    assert abs(g.residual() - ref.residuals[0]) <= 1e-10 * ref.residuals[0]
+
+
+def test_workload_3d_255_converged_residual_full_size():
+    """Full size until the SDC residual is below 1e-10: the oracle recomputes
+    the residual of the GPU's node values (a property at any size)."""
+    w = workload_3d_255()
+    p = O.Problem(3, w.n, w.nu, w.M, w.dt, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, w.n, w.seed)
+    g = make_gpu(O.Problem(3, w.n, w.nu, w.M, w.dt, smoother=RB, nu1=2, nu2=2, max_sweeps=200))
+    u = to_dev(u0)
+    st = g.step(u, 0, w.n_vcycles)
+    assert st == 0
+    R = g.residual()
+    assert R < 1e-10
+    nodes = g.nodes().cpu().numpy()
+    R_oracle = O.sdc_residual(p, nodes)
+    assert abs(R_oracle - R) <= 1e-13, (R, R_oracle)
+    np.testing.assert_array_equal(nodes[0], u0)
+    np.testing.assert_array_equal(nodes[-1], u.cpu().numpy())
+
+
+# --- mixed precision ----------------------------------------------------------
+@pytest.mark.parametrize("case", [(3, 63, 0.1, 5, 0.02, RB, 2, 2), (2, 127, 0.1, 3, 0.05, J, 1, 1),
+                                  (3, 31, 0.8, 3, 0.02, J, 1, 1)])
+def test_fp32_vcycles_converge_to_fp64_oracle(case):
+    d, n, nu, M, dt, sm, nu1, nu2 = case
+    p = O.Problem(d, n, nu, M, dt, smoother=sm, nu1=nu1, nu2=nu2, max_sweeps=150)
+    u0 = initial_condition(d, n, seed=300 + n)
+    ref = O.integrate(p, u0, 2, 0, 2)
+    assert all(s == 0 for s in ref.status)
+    g = make_gpu(p, vcycle_fp32=True)
+    u = to_dev(u0)
+    for s in range(2):
+        assert g.step(u, 0, 2) == 0
+        assert g.residual() < 1e-10
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-9
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_collocation_solution_is_a_fixed_point_on_gpu(fp32):
+    p = O.Problem(3, 15, 0.3, 5, 0.03, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, 15, seed=3)
+    pe = O.Problem(3, 15, 0.3, 5, 0.03, solver=O.SOLVER_EXACT, tol=1e-14, max_sweeps=300)
+    coll = O.isdc_step(pe, u0, 0, 0, want_nodes=True).nodes
+    g = make_gpu(p, vcycle_fp32=fp32)
+    g.set_nodes(to_dev(coll))
+    u = to_dev(u0)
+    g.step(u, 1, 2)
+    moved = np.abs(g.nodes().cpu().numpy() - coll).max()
+    assert moved <= (1e-11 if fp32 else 1e-13), moved
+
+
+# --- classical SDC and statuses -------------------------------------------------
+def test_classical_sdc_mode_matches_oracle():
+    p = O.Problem(2, 63, 1.0, 3, 0.01, reaction=O.REACTION_NONE, smoother=J, solver=O.SOLVER_MG_TOL,
+                  mg_tol=1e-9, tol=1e-9)
+    u0 = initial_condition(2, 63, seed=8)
+    ref = O.isdc_step(p, u0, 0, 0)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    g.step(u, ref.sweeps, 0)
+    sweeps, vcyc = g.stats()
+    assert sweeps == ref.sweeps
+    assert abs(vcyc - ref.vcycles) <= 2
+    assert rel_l2(u.cpu().numpy(), ref.u) <= 1e-9
+
+
+def test_not_converged_is_soft_and_keeps_last_sweep():
+    p = O.Problem(2, 31, 0.1, 3, 0.05, smoother=J, tol=1e-30, max_sweeps=3)
+    u0 = initial_condition(2, 31, seed=4)
+    ref = O.isdc_step(p, u0, 3, 2)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    import paper_1401_7824_gb300 as G
+    assert g.step(u, 0, 2) == G.ISDC_ERR_NOT_CONVERGED
+    assert rel_l2(u.cpu().numpy(), ref.u) <= 1e-12
+
+
+def test_nonfinite_input_reports_status():
+    import paper_1401_7824_gb300 as G
+    p = O.Problem(2, 31, 0.1, 3, 0.05)
+    u0 = initial_condition(2, 31, seed=4)
+    u0[5, 5] = np.nan
+    g = make_gpu(p)
+    with pytest.raises(G.IsdcError) as e:
+        g.step(to_dev(u0), 0, 2)
+    assert e.value.status == G.ISDC_ERR_NONFINITE
+
+
+def test_step_host_equals_device_step():
+    p = O.Problem(3, 31, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, 31, seed=12)
+    g = make_gpu(p)
+    ud = to_dev(u0)
+    g.step(ud, 4, 2)
+    uh = u0.copy()
+    g.step_host(uh, 4, 2)
+    np.testing.assert_array_equal(uh, ud.cpu().numpy())
+
+
+def test_invalid_arguments_are_rejected():
+    import paper_1401_7824_gb300 as G
+    with pytest.raises(G.IsdcError) as e:
+        G.isdc_create(2, 64, 0.1, 3, 0.05)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG
+    with pytest.raises(G.IsdcError) as e:
+        G.isdc_create(2, 63, 0.1, 3, 0.05, nodes=G.ISDC_NODES_RADAU_RIGHT)
+    assert e.value.status == G.ISDC_ERR_UNSUPPORTED
+    with pytest.raises(G.IsdcError) as e:
+        G.isdc_create(3, 31, -1.0, 3, 0.05)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG

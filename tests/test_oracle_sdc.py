@@ -192,3 +192,16 @@ def test_workload_2d_127_isdc_matches_exact_solve_sdc():
     assert all(ka >= kb for ka, kb in zip(a.sweeps, b.sweeps))
     rel = np.linalg.norm(a.u - b.u) / np.linalg.norm(b.u)
     assert rel < 1e-9, rel
+
+
+def test_sdc_residual_of_nodes_matches_step_history():
+    p = O.Problem(2, 15, 0.2, 5, 0.02, reaction=O.REACTION_ALLEN_CAHN)
+    u0 = initial_condition(2, 15, seed=9)
+    r = O.isdc_step(p, u0, 3, 2, want_nodes=True)
+    assert abs(O.sdc_residual(p, r.nodes) - r.residuals[-1]) <= 1e-15 * max(1.0, r.residuals[-1])
+    # zero at the collocation solution, and equal to max|U_m - u_0| when f = 0
+    coll = _collocation_solution(p, u0)
+    assert O.sdc_residual(p, coll) < 1e-13
+    p0 = O.Problem(2, 15, 1e-300, 5, 0.02, reaction=O.REACTION_NONE)
+    nodes = np.stack([u0] + [u0 + 0.1 * m for m in range(1, 5)])
+    assert abs(O.sdc_residual(p0, nodes) - 0.4) < 1e-12
