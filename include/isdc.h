@@ -48,7 +48,9 @@ typedef enum {
     ISDC_ERR_OOM = 3,           /* device allocation failed                       */
     ISDC_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed    */
     ISDC_ERR_NOT_CONVERGED = 5, /* soft: max_sweeps reached; u holds the last sweep */
-    ISDC_ERR_NONFINITE = 6      /* the SDC residual became NaN or Inf             */
+    ISDC_ERR_NONFINITE = 6,     /* the SDC residual became NaN or Inf             */
+    ISDC_ERR_SCRATCH_TOO_SMALL = 7 /* isdc_vcycles_static: the grid's multigrid buffers do not
+                                      fit in its static scratch array                  */
 } isdc_status;
 
 /* Collocation node families (Sec. 2).  Gauss-Lobatto is implemented. */
@@ -168,6 +170,39 @@ isdc_status isdc_set_nodes(isdc_ctx *ctx, const double *src);
  * float64 each; x is updated in place.  Uses the context's hierarchy.
  */
 isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, int n_cycles);
+
+/*
+ * isdc_vcycles_static -- the same multigrid solve as isdc_vcycles, for callers
+ * that cannot allocate device memory.  (The paper has no counterpart; this is
+ * an interface for integrators.)  Examples: code running under another
+ * framework's memory manager that has already reserved the device memory,
+ * real-time loops that must never call cudaMalloc, or code that must not
+ * allocate while other work is being captured into a CUDA graph.
+ *
+ * Runs n_cycles V-cycles (FP64) on (I - a L_h) x = b on the ndim-dimensional
+ * grid of side n (2^j - 1), with the given smoother (ISDC_SMOOTHER_*), nu1/nu2
+ * sweeps and Jacobi damping omega, on 'stream' (a cudaStream_t; NULL is the
+ * legacy default stream).  x, b: device, n^ndim float64 each, x updated in
+ * place; the caller owns both.  Asynchronous on the stream.
+ *
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
+ * coarse grids, the fine-grid residual (and Jacobi) buffers and the side-3
+ * inverse live in one static device array of ISDC_STATIC_SCRATCH_BYTES that
+ * every GPU which loads this library keeps until the process exits.  Grids
+ * whose buffers exceed it (2D sides above 1023, 3D sides above 127) are
+ * rejected with ISDC_ERR_SCRATCH_TOO_SMALL before any GPU work.
+ *
+ * The first call on each device (with that device current) looks up the
+ * array's device address and sets the bottom kernels' shared-memory limit;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (everything a call needs is
+ * rewritten by that call), so calls that overlap on the GPU -- on different
+ * streams or from different host threads -- race and must not be issued.
+ * Errors: INVALID_ARG, SCRATCH_TOO_SMALL, UNSUPPORTED, CUDA.
+ */
+#define ISDC_STATIC_SCRATCH_BYTES (48u << 20)
+isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoother, int nu1, int nu2, double omega,
+                                double *x, const double *b, int n_cycles, void *stream);
 
 /* Per-kernel-class timing (not from the paper: instrumentation for the
  * roofline).  While enabled, every launch of the context is bracketed by CUDA

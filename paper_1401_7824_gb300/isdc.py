@@ -20,8 +20,10 @@ ISDC_ERR_OOM = 3
 ISDC_ERR_CUDA = 4
 ISDC_ERR_NOT_CONVERGED = 5
 ISDC_ERR_NONFINITE = 6
+ISDC_ERR_SCRATCH_TOO_SMALL = 7
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
-                6: "NONFINITE"}
+                6: "NONFINITE", 7: "SCRATCH_TOO_SMALL"}
+ISDC_STATIC_SCRATCH_BYTES = 48 << 20
 
 ISDC_NODES_GAUSS_LOBATTO = 0
 ISDC_NODES_RADAU_RIGHT = 1
@@ -83,6 +85,7 @@ def load(build_if_missing: bool = True):
         "isdc_get_nodes": (I, [_ctx_p, V]),
         "isdc_set_nodes": (I, [_ctx_p, V]),
         "isdc_vcycles": (I, [_ctx_p, D, V, V, I]),
+        "isdc_vcycles_static": (I, [I, ctypes.c_int64, D, I, I, I, D, V, V, I, V]),
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
         "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
@@ -194,6 +197,23 @@ def isdc_set_nodes(ctx, src):
 
 def isdc_vcycles(ctx, a: float, x, b, n_cycles: int):
     _check(load().isdc_vcycles(ctx, a, _dev_ptr(x), _dev_ptr(b, x.numel()), n_cycles), ctx)
+
+
+def isdc_vcycles_static(ndim, n, a: float, x, b, n_cycles: int, smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1,
+                        omega=2.0 / 3.0, stream=None):
+    """The allocation-free multigrid solve (no context; scratch in a static
+    device array).  Runs on `stream` (a torch CUDA stream; default: torch's
+    current stream).  Raises IsdcError with the status on failure."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    h = ctypes.c_void_p(s.cuda_stream if s.cuda_stream else None)
+    st = load().isdc_vcycles_static(ndim, n, a, smoother, nu1, nu2, omega, _dev_ptr(x), _dev_ptr(b, x.numel()),
+                                    n_cycles, h)
+    if st != ISDC_OK:
+        raise IsdcError(st, "isdc_vcycles_static failed"
+                        + (f" (its scratch holds {ISDC_STATIC_SCRATCH_BYTES} bytes: 2D sides up to 1023, "
+                           "3D sides up to 127)" if st == ISDC_ERR_SCRATCH_TOO_SMALL else ""))
+    return st
 
 
 def isdc_profile_enable(ctx, enable: bool):
