@@ -186,8 +186,8 @@ isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, in
  * place; the caller owns both.  Asynchronous on the stream.
  *
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
- * coarse grids, the fine-grid residual (and Jacobi) buffers and the side-3
- * inverse live in one static device array of ISDC_STATIC_SCRATCH_BYTES that
+ * coarse grids, the fine-grid residual (and Jacobi) buffers, the scaled
+ * right-hand side and the side-3 inverse live in one static device array of ISDC_STATIC_SCRATCH_BYTES that
  * every GPU which loads this library keeps until the process exits.  Grids
  * whose buffers exceed it (2D sides above 1023, 3D sides above 127) are
  * rejected with ISDC_ERR_SCRATCH_TOO_SMALL before any GPU work.
@@ -200,7 +200,7 @@ isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, in
  * streams or from different host threads -- race and must not be issued.
  * Errors: INVALID_ARG, SCRATCH_TOO_SMALL, UNSUPPORTED, CUDA.
  */
-#define ISDC_STATIC_SCRATCH_BYTES (48u << 20)
+#define ISDC_STATIC_SCRATCH_BYTES (64u << 20)
 isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoother, int nu1, int nu2, double omega,
                                 double *x, const double *b, int n_cycles, void *stream);
 
@@ -213,12 +213,18 @@ isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoother, int
 typedef struct {
     char    name[32];   /* kernel class, e.g. "smooth_fine", "sweep_end" */
     int64_t launches;
-    double  total_ms;   /* sum of event-timed launch durations */
+    double  total_ms;   /* sum of event-timed launch durations; -1 if the class was not timed */
     double  bytes;      /* algorithmic bytes, summed over launches */
     double  fp64_ops;   /* algorithmic FP64 operations, summed */
     double  fp32_ops;   /* algorithmic FP32 operations, summed */
 } isdc_kernel_stat;
 
+/* enable = 0: off.  Otherwise a bit mask over the kernel classes, in this
+ * order: spread, eval_f, rhs, sweep_end, smooth_fine, residual_fine,
+ * restrict_fine, prolong_fine, smooth_coarse, residual_coarse,
+ * restrict_coarse, prolong_coarse, bottom, defect, update, resnorm (bit 0 =
+ * spread).  Launch counts, bytes and ops are kept for every class; only the
+ * classes in the mask get events (-1 times them all). */
 isdc_status isdc_profile_enable(isdc_ctx *ctx, int enable);
 
 /* Synchronise and copy up to cap class records (classes with launches only)

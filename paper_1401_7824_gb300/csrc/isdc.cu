@@ -165,6 +165,7 @@ const char* const kProfNames[PC_COUNT] = {
 
 struct Profiler {
   bool on = false;
+  unsigned event_mask = 0;  // classes bracketed by CUDA events
   struct Rec { cudaEvent_t e0, e1; int cls; };
   std::vector<Rec> pool;
   size_t used = 0;
@@ -245,6 +246,10 @@ struct ProfScope {
   ProfScope(isdc_ctx* c, int cls, double bytes, double ops, bool fp64) : ctx(c) {
     Profiler& P = ctx->prof;
     if (!P.on) return;
+    P.launches[cls] += 1;
+    P.bytes[cls] += bytes;
+    (fp64 ? P.dp_ops[cls] : P.sp_ops[cls]) += ops;
+    if (!(P.event_mask & (1u << cls))) return;
     if (P.used == P.pool.size()) {
       if (P.pool.size() >= 16384) {
         prof_flush(ctx);
@@ -258,9 +263,6 @@ struct ProfScope {
     idx = int(P.used++);
     P.pool[idx].cls = cls;
     cudaEventRecord(P.pool[idx].e0, ctx->stream);
-    P.launches[cls] += 1;
-    P.bytes[cls] += bytes;
-    (fp64 ? P.dp_ops[cls] : P.sp_ops[cls]) += ops;
   }
   ~ProfScope() {
     if (idx >= 0) cudaEventRecord(ctx->prof.pool[idx].e1, ctx->stream);
@@ -268,6 +270,16 @@ struct ProfScope {
 };
 
 inline double nb_ops(int dim) { return dim == 2 ? 3.0 : 5.0; }
+
+// Row scaling of H = I - a L_h on a grid of side s: c = a/h^2, d = 1 + 2 dim c,
+// kappa = c / d.
+struct LevelCoef {
+  double c, d, kappa;
+};
+inline LevelCoef level_coef(int dim, int s, double a) {
+  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * dim * c;
+  return {c, d, c / d};
+}
 
 inline dim3 pt_grid(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
 inline dim3 rb_grid(int dim, int s) { return dim3(((s + 1) / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
@@ -325,12 +337,15 @@ void free_hier(Hier<T>& H, bool own_level0) {
   cudaFree(H.Ainv);
 }
 
-// Upload the dense side-3 inverse for a = dt_m nu into a slot.
+// Upload d * H^{-1} of the side-3 grid for a = dt_m nu into a slot (it acts
+// on the row-scaled right-hand side beta = b / d).
 template <typename T>
 isdc_status upload_ainv(isdc_ctx* ctx, Hier<T>& H, int slot, double a) {
   std::vector<double> inv;
   coarse_inverse(ctx->dim, a, inv);
-  std::vector<T> tv(inv.begin(), inv.end());
+  const double d3 = 1.0 + 2.0 * ctx->dim * a * 16.0;  // h = 1/4 on the side-3 grid
+  std::vector<T> tv(inv.size());
+  for (size_t q = 0; q < inv.size(); ++q) tv[q] = T(d3 * inv[q]);
   const size_t each = ctx->dim == 2 ? 81 : 729;
   CUDA_TRY(ctx, cudaMemcpyAsync(H.Ainv + slot * each, tv.data(), each * sizeof(T), cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -353,32 +368,31 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
   // x: where the level's iterate lives now; home: its own array (Jacobi
   // ping-pongs between home and H.t[l]).
   const int s = H.side[l];
-  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  const T kappa = T(level_coef(DIM, s, a).kappa);
   for (int it = 0; it < sweeps; ++it) {
     if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) {
       T* out = (x == H.t[l]) ? home : H.t[l];
       {
         const double Np = double(H.npts[l]);
         ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 2.0 : 3.0) * Np * sizeof(T),
-                     (zero ? 1.0 : nb_ops(DIM) + 4.0) * Np, sizeof(T) == 8);
-        k_jacobi<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(c), T(d), T(ctx->opt.omega / d), x, b,
-                                                                        out, zero ? 1 : 0);
+                     (zero ? 1.0 : nb_ops(DIM) + 3.0) * Np, sizeof(T) == 8);
+        k_jacobi<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, T(ctx->opt.omega), x, b, out,
+                                                                        zero ? 1 : 0);
       }
       LAUNCH_CHECK(ctx);
       x = out;
     } else {
-      const T cd = T(c / d), id = T(1.0 / d);
       const double Np = double(H.npts[l]);
       {
         ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 1.0 : 1.5) * Np * sizeof(T),
-                     (zero ? 1.0 : nb_ops(DIM) + 2.0) * 0.5 * Np, sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, cd, id, 0, x, b, zero ? 1 : 0);
+                     (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, sizeof(T) == 8);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, 0, x, b, zero ? 1 : 0);
       }
       LAUNCH_CHECK(ctx);
       {
-        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), (nb_ops(DIM) + 2.0) * 0.5 * Np,
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), (nb_ops(DIM) + 1.0) * 0.5 * Np,
                      sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, cd, id, 1, x, b, 0);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, 1, x, b, 0);
       }
       LAUNCH_CHECK(ctx);
     }
@@ -403,19 +417,29 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
       zero = false;
     }
     if ((st = smooth_level<T, DIM>(ctx, H, l, a, x, home, b, zero, ctx->opt.nu1)) != ISDC_OK) return st;
-    const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+    const LevelCoef lf = level_coef(DIM, s, a);
     const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+    // after a complete red-black sweep only the red rows carry a residual
+    const bool red_only = ctx->opt.smoother == ISDC_SMOOTHER_RBGS && ctx->opt.nu1 >= 1;
     {
-      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * Np * sizeof(T), (nb_ops(DIM) + 3.0) * Np,
-                   sizeof(T) == 8);
-      k_residual<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(c), T(d), x, b, H.r[l]);
+      const double f = red_only ? 0.5 : 1.0;
+      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * f * Np * sizeof(T),
+                   (nb_ops(DIM) + 2.0) * f * Np, sizeof(T) == 8);
+      if (red_only)
+        k_residual<T, DIM, true><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(lf.kappa), x, b, H.r[l]);
+      else
+        k_residual<T, DIM, false><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(lf.kappa), x, b, H.r[l]);
     }
     LAUNCH_CHECK(ctx);
     const int sc = H.side[l + 1];
     {
-      ProfScope ps(ctx, l == 0 ? PC_RESTRICT0 : PC_RESTRICTC, (Np + Nc) * sizeof(T), (DIM == 2 ? 9.0 : 27.0) * Nc,
-                   sizeof(T) == 8);
-      k_restrict<T, DIM><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, H.r[l], H.b[l + 1]);
+      const T ws = T(lf.d / (level_coef(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0)));
+      ProfScope ps(ctx, l == 0 ? PC_RESTRICT0 : PC_RESTRICTC, ((red_only ? 0.5 : 1.0) * Np + Nc) * sizeof(T),
+                   (red_only ? (DIM == 2 ? 6.0 : 15.0) : (DIM == 2 ? 9.0 : 27.0)) * Nc, sizeof(T) == 8);
+      if (red_only)
+        k_restrict<T, DIM, true><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
+      else
+        k_restrict<T, DIM, false><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
     }
     LAUNCH_CHECK(ctx);
     xcur[l] = x;
@@ -426,10 +450,12 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     P.nlev = H.nlev - H.lb;
     for (int q = 0; q < P.nlev; ++q) {
       const int s = H.side[H.lb + q];
-      const double h = 1.0 / (s + 1), c = a / (h * h);
+      const LevelCoef lf = level_coef(DIM, s, a);
       P.side[q] = s;
-      P.c[q] = T(c);
-      P.d[q] = T(1.0 + 2.0 * DIM * c);
+      P.kappa[q] = T(lf.kappa);
+      P.rscale[q] = q + 1 < P.nlev
+                        ? T(lf.d / (level_coef(DIM, H.side[H.lb + q + 1], a).d * (DIM == 2 ? 16.0 : 64.0)))
+                        : T(0);
     }
     P.smoother = ctx->opt.smoother;
     P.nu1 = ctx->opt.nu1;
@@ -452,10 +478,15 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     T* home = (l == 0) ? x0 : H.x[l];
     T* x = xcur[l];
     {
+      // a red half sweep follows: it overwrites the red points, so correct the black ones only
+      const bool black_only = ctx->opt.smoother == ISDC_SMOOTHER_RBGS && ctx->opt.nu2 >= 1;
       const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
-      ProfScope ps(ctx, l == 0 ? PC_PROLONG0 : PC_PROLONGC, (2.0 * Np + Nc) * sizeof(T),
-                   (DIM == 2 ? 6.25 : 8.875) * Np, sizeof(T) == 8);
-      k_prolong_add<T, DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
+      ProfScope ps(ctx, l == 0 ? PC_PROLONG0 : PC_PROLONGC, ((black_only ? 1.0 : 2.0) * Np + Nc) * sizeof(T),
+                   (black_only ? (DIM == 2 ? 1.25 : 1.75) : (DIM == 2 ? 2.0 : 2.5)) * Np, sizeof(T) == 8);
+      if (black_only)
+        k_prolong_add<T, DIM, true><<<pt_grid(DIM, sc + 1), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
+      else
+        k_prolong_add<T, DIM, false><<<pt_grid(DIM, sc + 1), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
     }
     LAUNCH_CHECK(ctx);
     bool zero = false;
@@ -468,23 +499,30 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
   return ISDC_OK;
 }
 
-// One V-cycle of the node solve with unknown x (FP64 device array) in the
-// context's precision.
+// n_cycles V-cycles of one node solve on (I - a L_h) x = b, x an FP64 device
+// array, beta = b/d.  FP64 mode: V-cycles on x.  FP32 mode (defect
+// correction): the fine-level residual of the node equation in FP64, rounded
+// to FP32, n_cycles FP32 V-cycles on the error equation from e = 0, and one
+// FP64 update x += e.
 template <int DIM>
-isdc_status node_vcycle(isdc_ctx* ctx, int slot, double a, double* x, const double* b) {
-  if (!ctx->opt.vcycle_fp32) return vcycle<double, DIM>(ctx, ctx->h64, slot, a, x, b, false);
-  // defect correction: r = b - H x in FP64 -> FP32, FP32 V-cycle on H e = r from e = 0, x += e
+isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles) {
+  isdc_status st;
+  if (!ctx->opt.vcycle_fp32) {
+    for (int c = 0; c < n_cycles; ++c)
+      if ((st = vcycle<double, DIM>(ctx, ctx->h64, slot, a, x, beta, false)) != ISDC_OK) return st;
+    return ISDC_OK;
+  }
+  if (n_cycles <= 0) return ISDC_OK;
   const int s = ctx->n;
-  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
   Hier<float>& H = ctx->h32;
   const double Np = double(ctx->N);
   {
-    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 3.0) * Np, true);
-    k_defect<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, c, d, x, b, H.b[0]);
+    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
+    k_defect<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, level_coef(DIM, s, a).kappa, x, beta, H.b[0]);
   }
   LAUNCH_CHECK(ctx);
-  isdc_status st = vcycle<float, DIM>(ctx, H, slot, a, H.x[0], H.b[0], true);
-  if (st != ISDC_OK) return st;
+  for (int c = 0; c < n_cycles; ++c)
+    if ((st = vcycle<float, DIM>(ctx, H, slot, a, H.x[0], H.b[0], c == 0)) != ISDC_OK) return st;
   {
     ProfScope ps(ctx, PC_UPDATE, 20.0 * Np, 1.0 * Np, true);
     k_update<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, x, H.x[0]);
@@ -496,11 +534,11 @@ isdc_status node_vcycle(isdc_ctx* ctx, int slot, double a, double* x, const doub
 template <int DIM>
 isdc_status node_residual_norm(isdc_ctx* ctx, double a, const double* x, const double* b, double* out) {
   const int s = ctx->n;
-  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  const LevelCoef lf = level_coef(DIM, s, a);
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal + 1, 0, sizeof(unsigned long long), ctx->stream));
   {
     ProfScope ps(ctx, PC_RESNORM, 16.0 * double(ctx->N), (nb_ops(DIM) + 3.0) * double(ctx->N), true);
-    k_resnorm<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, c, d, x, b, ctx->d_scal + 1);
+    k_resnorm<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, lf.kappa, lf.d, x, b, ctx->d_scal + 1);
   }
   LAUNCH_CHECK(ctx);
   CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(unsigned long long),
@@ -523,8 +561,9 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   {
     const double M = ctx->M, Np = double(ctx->N);
-    ProfScope ps(ctx, PC_SWEEP_END, (3.0 * M - 1.0) * 8.0 * Np, (2.0 * M * M + 7.0 * M - 1.0 + nb_ops(DIM)) * Np,
-                 true);
+    // f_{M-1}: nb+2; f^E: 2M; dt Q f: M(M-1); residual: 2(M-1); C: 4(M-1) - 1
+    ProfScope ps(ctx, PC_SWEEP_END, (3.0 * M - 1.0) * 8.0 * Np,
+                 (nb_ops(DIM) + 2.0 + 2.0 * M + M * (M - 1.0) + 6.0 * (M - 1.0) - 1.0) * Np, true);
     k_sweep_end<DIM><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->N, nu_h2, ctx->opt.reaction,
                                                                       ctx->tables, ctx->U, ctx->F, ctx->C,
                                                                       ctx->d_scal);
@@ -568,10 +607,12 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   for (;;) {
     for (int m = 0; m < M - 1; ++m) {
       const double dtm = ctx->tables.dtm[m];
+      const double inv_d0 = 1.0 / level_coef(DIM, n, dtm * ctx->nu).d;
       {
         ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
                      (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
-        k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, ctx->U + m * N,
+        k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
+                                                                ctx->U + m * N,
                                                                 ctx->C + m * N, ctx->b,
                                                                 m >= 1 ? ctx->F + m * N : nullptr);
       }
@@ -579,15 +620,14 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
       double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
       const double a = dtm * ctx->nu;
       if (n_vcycles > 0) {
-        for (int c = 0; c < n_vcycles; ++c)
-          if ((st = node_vcycle<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+        if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, n_vcycles)) != ISDC_OK) return st;
         vcycles += n_vcycles;
       } else {  // classical SDC: multigrid to a tolerance (Sec. 3)
         for (int c = 0; c < ctx->opt.mg_max_cycles; ++c) {
           double rn;
           if ((st = node_residual_norm<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
           if (!(rn > ctx->opt.mg_tol)) break;
-          if ((st = node_vcycle<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+          if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, 1)) != ISDC_OK) return st;
           ++vcycles;
         }
       }
@@ -739,7 +779,6 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   for (int m = 0; m < M; ++m)
     for (int j = 0; j < M; ++j) {
       ctx->tables.dtQ[m][j] = dt * ctx->Q[m * M + j];
-      if (m < M - 1) ctx->tables.dtS[m][j] = dt * ctx->S[m * M + j];
     }
   for (int m = 0; m < M - 1; ++m) ctx->tables.dtm[m] = dt * (ctx->tau[m + 1] - ctx->tau[m]);
 
@@ -856,11 +895,12 @@ ISDC_API isdc_status isdc_vcycles(isdc_ctx* ctx, double a, double* x, const doub
   if (ctx->opt.vcycle_fp32) st = upload_ainv(ctx, ctx->h32, ctx->spare_slot, a);
   else st = upload_ainv(ctx, ctx->h64, ctx->spare_slot, a);
   if (st != ISDC_OK) return st;
-  for (int c = 0; c < n_cycles; ++c) {
-    st = ctx->dim == 2 ? node_vcycle<2>(ctx, ctx->spare_slot, a, x, b) : node_vcycle<3>(ctx, ctx->spare_slot, a, x, b);
-    if (st != ISDC_OK) return st;
-  }
-  return ISDC_OK;
+  // the V-cycles act on the row-scaled system: beta = b / d (in the context's rhs buffer)
+  const double d0 = level_coef(ctx->dim, ctx->n, a).d;
+  k_scale<double><<<4 * 152, 256, 0, ctx->stream>>>(ctx->N, 1.0 / d0, b, ctx->b);
+  LAUNCH_CHECK(ctx);
+  return ctx->dim == 2 ? node_solve<2>(ctx, ctx->spare_slot, a, x, ctx->b, n_cycles)
+                       : node_solve<3>(ctx, ctx->spare_slot, a, x, ctx->b, n_cycles);
 }
 
 ISDC_API isdc_status isdc_profile_enable(isdc_ctx* ctx, int enable) {
@@ -875,6 +915,7 @@ ISDC_API isdc_status isdc_profile_enable(isdc_ctx* ctx, int enable) {
     std::fill(P.launches, P.launches + PC_COUNT, 0LL);
   }
   P.on = enable != 0;
+  P.event_mask = unsigned(enable);
   return ISDC_OK;
 }
 
@@ -891,7 +932,7 @@ ISDC_API isdc_status isdc_profile_read(isdc_ctx* ctx, isdc_kernel_stat* out, int
       std::memset(&o, 0, sizeof o);
       snprintf(o.name, sizeof o.name, "%s", kProfNames[k]);
       o.launches = P.launches[k];
-      o.total_ms = P.ms[k];
+      o.total_ms = (P.event_mask & (1u << k)) ? P.ms[k] : -1.0;
       o.bytes = P.bytes[k];
       o.fp64_ops = P.dp_ops[k];
       o.fp32_ops = P.sp_ops[k];

@@ -4,7 +4,9 @@
 // 0-based i, j, k in [0, n); the zero Dirichlet ghosts are implicit.  The
 // implicit operator of every node solve is H = I - a L_h (Sec. 3, Eq. 4 with
 // W = I and A = nu L_h, a = dt_m nu); with c = a/h^2 and d = 1 + 2*DIM*c,
-// H x = d x - c * (sum of the 2*DIM neighbours).
+// H x = d x - c * (sum of the 2*DIM neighbours).  The multigrid kernels work on
+// the row-scaled system x - kappa * (neighbour sum) = beta, kappa = c/d,
+// beta = b/d, so a Gauss-Seidel update is one FMA after the neighbour sum.
 //
 // Every kernel here is memory- or FP64-issue-bound stencil work on CUDA cores:
 // no tensor cores (there is no dense contraction on this path).
@@ -22,56 +24,55 @@ __device__ __forceinline__ int lin(int i, int j, int k, int n) {
   return DIM == 2 ? i + n * j : i + n * (j + n * k);
 }
 
-// Sum of the 2*DIM neighbours of (i,j,k); zero outside the interior.
+// Sum of the 2*DIM neighbours of (i,j,k); zero outside the interior.  Summed
+// as a tree (pairs per axis) for short FP64 dependency chains.
 template <typename T, int DIM>
 __device__ __forceinline__ T nbsum(const T* __restrict__ x, int i, int j, int k, int n, int p) {
   const int sy = n, sz = n * n;
-  T s = (i > 0 ? x[p - 1] : T(0)) + (i < n - 1 ? x[p + 1] : T(0));
-  s += (j > 0 ? x[p - sy] : T(0));
-  s += (j < n - 1 ? x[p + sy] : T(0));
+  const T sx = (i > 0 ? x[p - 1] : T(0)) + (i < n - 1 ? x[p + 1] : T(0));
+  const T syv = (j > 0 ? x[p - sy] : T(0)) + (j < n - 1 ? x[p + sy] : T(0));
   if (DIM == 3) {
-    s += (k > 0 ? x[p - sz] : T(0));
-    s += (k < n - 1 ? x[p + sz] : T(0));
+    const T szv = (k > 0 ? x[p - sz] : T(0)) + (k < n - 1 ? x[p + sz] : T(0));
+    return (sx + syv) + szv;
   }
-  return s;
+  return sx + syv;
 }
 
 template <typename T>
 __device__ __forceinline__ T reaction_term(int reaction, T u) {
-  // f^E(u) = u - u^3 (Allen-Cahn type) or nothing
-  return reaction ? u - u * u * u : T(0);
+  // f^E(u) = u - u^3 (Allen-Cahn type) or nothing; one multiply + one FMA
+  return reaction ? fma(-(u * u), u, u) : T(0);
 }
 
 // ---------------------------------------------------------------------------
 // Multigrid smoothers, residual and transfers (one thread per point).
 // ---------------------------------------------------------------------------
 
-// Damped Jacobi: xo = x + (omega/d) (b - H x).  zero_guess: x == 0.
+// Damped Jacobi: xo = x + omega (beta - x + kappa * sum) = x + (omega/d)(b - H x).
+// zero_guess: x == 0.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_jacobi(int n, T c, T d, T w_over_d, const T* __restrict__ x, const T* __restrict__ b,
+    k_jacobi(int n, T kappa, T omega, const T* __restrict__ x, const T* __restrict__ beta,
              T* __restrict__ xo, int zero_guess) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
   if (zero_guess) {
-    xo[p] = w_over_d * b[p];
+    xo[p] = omega * beta[p];
     return;
   }
   const T xp = x[p];
-  const T r = b[p] - (d * xp - c * nbsum<T, DIM>(x, i, j, k, n, p));
-  xo[p] = xp + w_over_d * r;
+  xo[p] = fma(omega, fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]) - xp, xp);
 }
 
 // Red-black Gauss-Seidel half sweep: colour 0 = red = (i+j+k) even in 1-based
-// interior indices.  Each thread owns one point of the colour:
-// x_p = (b_p + c * sum of neighbours) / d.  zero_guess (red pass from x == 0):
-// the neighbours are zero.
+// interior indices.  Each thread owns one point of the colour and solves its
+// row: x_p = beta_p + kappa * (sum of neighbours).  zero_guess (red pass from
+// x == 0): the neighbours are zero.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_rbgs(int n, T c_over_d, T inv_d, int colour, T* __restrict__ x, const T* __restrict__ b,
-           int zero_guess) {
+    k_rbgs(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
   const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   // (i+1)+(j+1)+(k+1) parity == colour  <=>  i parity == (colour + j + k + DIM) & 1
@@ -79,35 +80,59 @@ __global__ void __launch_bounds__(kBX* kBY)
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
   if (zero_guess) {
-    x[p] = inv_d * b[p];
+    x[p] = beta[p];
     return;
   }
-  x[p] = inv_d * b[p] + c_over_d * nbsum<T, DIM>(x, i, j, k, n, p);
+  x[p] = fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]);
 }
 
-// r = b - H x
-template <typename T, int DIM>
+// Scaled residual r' = beta - x + kappa * sum = (b - H x)/d.
+// RED_ONLY (launched with the red-black grid): right after a complete
+// red-black sweep every black row is satisfied, so only the red points carry
+// a residual; the black entries of r are left unwritten and never read.
+template <typename T, int DIM, bool RED_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_residual(int n, T c, T d, const T* __restrict__ x, const T* __restrict__ b,
-               T* __restrict__ r) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+    k_residual(int n, T kappa, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ r) {
+  const int t = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
+  const int i = RED_ONLY ? 2 * t + ((j + (DIM == 3 ? k : 0) + DIM) & 1) : t;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
-  r[p] = b[p] - (d * x[p] - c * nbsum<T, DIM>(x, i, j, k, n, p));
+  r[p] = fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]) - x[p];
 }
 
 // Full weighting to the coarse grid (side nc, fine side 2nc+1): coarse point
-// I sits on fine point 2I+1 (0-based); weights (1/4, 1/2, 1/4) per axis.
-template <typename T, int DIM>
+// I sits on fine point 2I+1 (0-based); weights (1/4, 1/2, 1/4) per axis.  The
+// input is the fine scaled residual r' = r/d_f and the output the coarse scaled
+// right-hand side beta_c = FW(r)/d_c, so the final factor is
+// wscale = d_f / (2^(2 DIM) d_c).
+// RED_ONLY: the residual vanishes at the black points (see k_residual); the
+// coarse point's own fine point and its edge neighbours are red, its face and
+// corner neighbours black, so full weighting keeps 5 (2D) or 13 (3D) terms.
+template <typename T, int DIM, bool RED_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_restrict(int nc, const T* __restrict__ r, T* __restrict__ bc) {
+    k_restrict(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= nc || J >= nc) return;
   const int n = 2 * nc + 1;
   const int fi = 2 * I + 1, fj = 2 * J + 1;
   T acc = T(0);
+  if (RED_ONLY) {
+    if (DIM == 2) {
+      const T* q = r + (fi + n * fj);
+      acc = fma(T(4), q[0], (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1])) * wscale;
+    } else {
+      const int nn = n * n;
+      const T* q = r + (fi + n * (fj + n * (2 * K + 1)));
+      const T e_xy = (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1]);
+      const T e_xz = (q[-nn - 1] + q[-nn + 1]) + (q[nn - 1] + q[nn + 1]);
+      const T e_yz = (q[-nn - n] + q[-nn + n]) + (q[nn - n] + q[nn + n]);
+      acc = fma(T(2), (e_xy + e_xz) + e_yz, T(8) * q[0]) * wscale;
+    }
+    bc[lin<DIM>(I, J, K, nc)] = acc;
+    return;
+  }
   if (DIM == 2) {
     T row[3];
 #pragma unroll
@@ -115,7 +140,7 @@ __global__ void __launch_bounds__(kBX* kBY)
       const T* q = r + (fi + n * (fj + dj));
       row[dj + 1] = (q[-1] + q[1]) + T(2) * q[0];
     }
-    acc = ((row[0] + row[2]) + T(2) * row[1]) * T(1.0 / 16.0);
+    acc = ((row[0] + row[2]) + T(2) * row[1]) * wscale;
   } else {
     const int fk = 2 * K + 1;
     T pl[3];
@@ -129,59 +154,98 @@ __global__ void __launch_bounds__(kBX* kBY)
       }
       pl[dk + 1] = (row[0] + row[2]) + T(2) * row[1];
     }
-    acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * T(1.0 / 64.0);
+    acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * wscale;
   }
   bc[lin<DIM>(I, J, K, nc)] = acc;
 }
 
 // x += P e_c: (bi/tri)linear interpolation from the coarse grid (side nc) to
-// the fine grid (side 2nc+1); coarse ghosts are zero.
-template <typename T, int DIM>
+// the fine grid (side n = 2nc+1); coarse ghosts are zero.  One thread per
+// coarse cell (I,J,K) in [0, nc]^DIM owns the fine points {2I, 2I+1} x
+// {2J, 2J+1} (x {2K, 2K+1}): the odd index coincides with coarse I, the even
+// one lies between coarse I-1 and I.  The interpolated values are built from
+// shared partial sums (2.5 operations per fine point in 3D).
+// BLACK_ONLY: the next operation on this level is a red half sweep, which
+// overwrites every red point without reading it, so only the black fine points
+// (1-based index sum odd) are corrected; the result is the same.
+template <typename T, int DIM, bool BLACK_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
     k_prolong_add(int nc, const T* __restrict__ ec, T* __restrict__ x) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I > nc || J > nc) return;
   const int n = 2 * nc + 1;
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= n || j >= n) return;
-  // fine 0-based i sits on coarse (i-1)/2 when i is odd; between (i-2)/2 and i/2 when even
-  int ci[2], cj[2], ck[2];
-  T wi[2], wj[2], wk[2];
-  int ni, nj, nk;
-  auto axis = [nc](int f, int* c, T* w, int* cnt) {
-    if (f & 1) {
-      c[0] = (f - 1) >> 1; w[0] = T(1); *cnt = 1;
-    } else {
-      int m = 0;
-      if (f > 0) { c[m] = (f - 2) >> 1; w[m] = T(0.5); ++m; }
-      if (f / 2 < nc) { c[m] = f >> 1; w[m] = T(0.5); ++m; }
-      *cnt = m;
+  const bool hi_i = I > 0, ok_i = I < nc, hi_j = J > 0, ok_j = J < nc;
+  const int fi = 2 * I, fj = 2 * J;
+  if (DIM == 2) {
+    // c_ji: j, i in {0: index-1, 1: index}
+    const T c00 = (hi_i && hi_j) ? ec[(I - 1) + nc * (J - 1)] : T(0);
+    const T c01 = (ok_i && hi_j) ? ec[I + nc * (J - 1)] : T(0);
+    const T c10 = (hi_i && ok_j) ? ec[(I - 1) + nc * J] : T(0);
+    const T c11 = (ok_i && ok_j) ? ec[I + nc * J] : T(0);
+    const T sx0 = c00 + c01, sx1 = c10 + c11, sy1 = c01 + c11;
+    T* xe = x + (fi + n * fj);  // (even, even); 2D fine points with ex+ey even are red
+    if (!BLACK_ONLY) xe[0] = fma(T(0.25), sx0 + sx1, xe[0]);
+    if (ok_i) xe[1] = fma(T(0.5), sy1, xe[1]);
+    if (ok_j) {
+      xe[n] = fma(T(0.5), sx1, xe[n]);
+      if (ok_i && !BLACK_ONLY) xe[n + 1] += c11;
     }
-  };
-  axis(i, ci, wi, &ni);
-  axis(j, cj, wj, &nj);
-  if (DIM == 3) axis(k, ck, wk, &nk); else { ck[0] = 0; wk[0] = T(1); nk = 1; }
-  T e = T(0);
-  for (int c3 = 0; c3 < nk; ++c3)
-    for (int c2 = 0; c2 < nj; ++c2) {
-      T line = T(0);
-      for (int c1 = 0; c1 < ni; ++c1) line += wi[c1] * ec[lin<DIM>(ci[c1], cj[c2], ck[c3], nc)];
-      e += (wj[c2] * wk[c3]) * line;
+  } else {
+    const bool hi_k = K > 0, ok_k = K < nc;
+    auto cv = [&](bool ok, int i, int j, int k) { return ok ? ec[i + nc * (j + nc * k)] : T(0); };
+    // c_kji
+    const T c000 = cv(hi_i && hi_j && hi_k, I - 1, J - 1, K - 1), c001 = cv(ok_i && hi_j && hi_k, I, J - 1, K - 1);
+    const T c010 = cv(hi_i && ok_j && hi_k, I - 1, J, K - 1), c011 = cv(ok_i && ok_j && hi_k, I, J, K - 1);
+    const T c100 = cv(hi_i && hi_j && ok_k, I - 1, J - 1, K), c101 = cv(ok_i && hi_j && ok_k, I, J - 1, K);
+    const T c110 = cv(hi_i && ok_j && ok_k, I - 1, J, K), c111 = cv(ok_i && ok_j && ok_k, I, J, K);
+    const T sx00 = c000 + c001, sx01 = c010 + c011, sx10 = c100 + c101, sx11 = c110 + c111;  // along x
+    const T sy0 = c001 + c011, sy1 = c101 + c111;                                          // along y at i
+    const T sz = c011 + c111;                                                              // along z at (j, i)
+    const T sxy0 = sx00 + sx01, sxy1 = sx10 + sx11, sxz = sx01 + sx11, syz = sy0 + sy1;
+    const T sxyz = sxy0 + sxy1;
+    const int nn = n * n;
+    T* xe = x + (fi + n * (fj + n * (2 * K)));  // (even, even, even)
+    // 3D fine points with ex+ey+ez odd are red
+    // even k plane
+    xe[0] = fma(T(0.125), sxyz, xe[0]);
+    if (ok_i && !BLACK_ONLY) xe[1] = fma(T(0.25), syz, xe[1]);
+    if (ok_j) {
+      if (!BLACK_ONLY) xe[n] = fma(T(0.25), sxz, xe[n]);
+      if (ok_i) xe[n + 1] = fma(T(0.5), sz, xe[n + 1]);
     }
-  x[lin<DIM>(i, j, k, n)] += e;
+    if (ok_k) {  // odd k plane
+      T* xo = xe + nn;
+      if (!BLACK_ONLY) xo[0] = fma(T(0.25), sxy1, xo[0]);
+      if (ok_i) xo[1] = fma(T(0.5), sy1, xo[1]);
+      if (ok_j) {
+        xo[n] = fma(T(0.5), sx11, xo[n]);
+        if (ok_i && !BLACK_ONLY) xo[n + 1] += c111;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Mixed precision: FP64 defect to FP32, FP32 correction added in FP64.
 // ---------------------------------------------------------------------------
+// Scaled defect in FP64, stored in FP32: r32 = fp32(beta - x + kappa * sum).
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_defect(int n, double c, double d, const double* __restrict__ x,
-             const double* __restrict__ b, float* __restrict__ r32) {
+    k_defect(int n, double kappa, const double* __restrict__ x, const double* __restrict__ beta,
+             float* __restrict__ r32) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
-  r32[p] = float(b[p] - (d * x[p] - c * nbsum<double, DIM>(x, i, j, k, n, p)));
+  r32[p] = float(fma(kappa, nbsum<double, DIM>(x, i, j, k, n, p), beta[p]) - x[p]);
+}
+
+// beta = b / d (scaling of a caller's right-hand side).
+template <typename T>
+__global__ void k_scale(size_t N, T s, const T* __restrict__ b, T* __restrict__ beta) {
+  for (size_t p = blockIdx.x * size_t(blockDim.x) + threadIdx.x; p < N; p += size_t(gridDim.x) * blockDim.x)
+    beta[p] = s * b[p];
 }
 
 template <int DIM>
@@ -202,8 +266,7 @@ constexpr int kMaxM = 7;
 // Collocation tables premultiplied by dt (Sec. 2, Eq. 2).
 struct SweepTables {
   int M;
-  double dtQ[kMaxM][kMaxM];   // dt * Q[m][j]
-  double dtS[kMaxM][kMaxM];   // dt * S[m][j], rows m = 0..M-2
+  double dtQ[kMaxM][kMaxM];   // dt * Q[m][j]; row 0 is zero for Gauss-Lobatto (tau_1 = 0)
   double dtm[kMaxM];          // dt_m = dt (tau_{m+1} - tau_m)
 };
 
@@ -239,22 +302,22 @@ __global__ void __launch_bounds__(kBX* kBY)
 }
 
 // Right-hand side of node m's implicit Euler system (Eq. 4, implicit unknown
-// moved to the left):
+// moved to the left), stored row-scaled as beta = b / d:
 //   b = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C_m,
 //   C_m = dt sum_j s_{m,j} f(u_j^k) - dt_m f^E(u_m^k) - dt_m f^I(u_{m+1}^k)
 // (C_m comes from the end of the previous sweep).  For m >= 1 the same pass
 // stores f_m = f(u_m^{k+1}), which the residual and the next sweep need.
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_rhs(int n, double nu_h2, int reaction, double dtm, const double* __restrict__ Um,
-          const double* __restrict__ Cm, double* __restrict__ b, double* __restrict__ Fm) {
+    k_rhs(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
+          const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
   const double up = Um[p];
   const double fe = reaction_term(reaction, up);
-  b[p] = up + dtm * fe + Cm[p];
+  beta[p] = (fma(dtm, fe, up) + Cm[p]) * inv_d;
   if (Fm) Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
 }
 
@@ -313,27 +376,30 @@ __global__ void __launch_bounds__(kBX* kBY)
       if (m < M - 1) f[m] = F[m * N + p];
       else if (m == M - 1) f[m] = flast;
     }
+    // dt sum_j q_{m,j} f_j for m >= 1 (row 0 of Q is zero); the node-to-node
+    // term dt sum_j s_{m,j} f_j of Eq. 2 is the difference of consecutive rows.
+#pragma unroll
+    for (int m = 1; m < kMaxM; ++m)
+      if (m < M) {
+        double acc = tb.dtQ[m][0] * f[0];
+#pragma unroll
+        for (int jj = 1; jj < kMaxM; ++jj)
+          if (jj < M) acc = fma(tb.dtQ[m][jj], f[jj], acc);
+        qf[m] = acc;
+      }
     double rmax = 0.0;
 #pragma unroll
-    for (int m = 0; m < kMaxM; ++m)
+    for (int m = 1; m < kMaxM; ++m)
       if (m < M) {
-        double acc = 0.0;
-#pragma unroll
-        for (int jj = 0; jj < kMaxM; ++jj)
-          if (jj < M) acc += tb.dtQ[m][jj] * f[jj];
-        qf[m] = acc;
-        const double r = fabs(u[0] + acc - u[m]);
+        const double r = fabs((u[0] - u[m]) + qf[m]);
         rmax = (r > rmax || r != r) ? r : rmax;
       }
 #pragma unroll
     for (int m = 0; m < kMaxM - 1; ++m)
       if (m < M - 1) {
-        double sf = 0.0;
-#pragma unroll
-        for (int jj = 0; jj < kMaxM; ++jj)
-          if (jj < M) sf += tb.dtS[m][jj] * f[jj];
+        const double sf = m == 0 ? qf[1] : qf[m + 1] - qf[m];
         // f^I(u_{m+1}) = f_{m+1} - f^E(u_{m+1})
-        C[m * N + p] = sf - tb.dtm[m] * (fe[m] + (f[m + 1] - fe[m + 1]));
+        C[m * N + p] = fma(-tb.dtm[m], fe[m] + (f[m + 1] - fe[m + 1]), sf);
       }
     rb = (unsigned long long)__double_as_longlong(rmax);
   }
@@ -343,14 +409,14 @@ __global__ void __launch_bounds__(kBX* kBY)
 // Max-norm of b - H x (classical SDC stopping test), FP64.
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_resnorm(int n, double c, double d, const double* __restrict__ x, const double* __restrict__ b,
+    k_resnorm(int n, double kappa, double d, const double* __restrict__ x, const double* __restrict__ beta,
               unsigned long long* __restrict__ out) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   unsigned long long rb = 0;
   if (i < n && j < n) {
     const int p = lin<DIM>(i, j, k, n);
-    const double r = fabs(b[p] - (d * x[p] - c * nbsum<double, DIM>(x, i, j, k, n, p)));
+    const double r = d * fabs(fma(kappa, nbsum<double, DIM>(x, i, j, k, n, p), beta[p]) - x[p]);
     rb = (unsigned long long)__double_as_longlong(r);
   }
   block_max_atomic(rb, out);
@@ -368,34 +434,32 @@ template <typename T>
 struct BottomParams {
   int nlev;
   int side[kMaxLevels];
-  T c[kMaxLevels], d[kMaxLevels];
+  T kappa[kMaxLevels];   // c/d per level
+  T rscale[kMaxLevels];  // restriction factor d_l / (2^(2 DIM) d_{l+1})
   int smoother, nu1, nu2;
   T omega;
-  const T* Ainv;  // dense inverse of H on the side-3 grid, row-major
+  const T* Ainv;  // d * H^{-1} on the side-3 grid (acts on the scaled rhs), row-major
 };
 
 template <typename T, int DIM>
 __device__ void bt_smooth(const BottomParams<T>& P, int l, T* x, const T* b, T* t) {
   const int n = P.side[l];
   const int Np = DIM == 2 ? n * n : n * n * n;
-  const T c = P.c[l], d = P.d[l];
+  const T kappa = P.kappa[l];
   if (P.smoother == 0) {
     for (int p = threadIdx.x; p < Np; p += blockDim.x) t[p] = x[p];
     __syncthreads();
-    const T wd = P.omega / d;
     for (int p = threadIdx.x; p < Np; p += blockDim.x) {
       const int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
-      const T r = b[p] - (d * t[p] - c * nbsum<T, DIM>(t, i, j, k, n, p));
-      x[p] = t[p] + wd * r;
+      x[p] = fma(P.omega, fma(kappa, nbsum<T, DIM>(t, i, j, k, n, p), b[p]) - t[p], t[p]);
     }
     __syncthreads();
   } else {
-    const T cd = c / d, id = T(1) / d;
     for (int colour = 0; colour < 2; ++colour) {
       for (int p = threadIdx.x; p < Np; p += blockDim.x) {
         const int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
         if (((i + j + k + DIM) & 1) != colour) continue;
-        x[p] = id * b[p] + cd * nbsum<T, DIM>(x, i, j, k, n, p);
+        x[p] = fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), b[p]);
       }
       __syncthreads();
     }
@@ -432,10 +496,10 @@ __global__ void __launch_bounds__(kBottomThreads)
     const int Np = DIM == 2 ? n * n : n * n * n;
     const int Nc = DIM == 2 ? nc * nc : nc * nc * nc;
     for (int s = 0; s < P.nu1; ++s) bt_smooth<T, DIM>(P, l, X[l], B[l], Tt[l]);
-    const T c = P.c[l], d = P.d[l];
+    const T kappa = P.kappa[l], rs = P.rscale[l];
     for (int p = threadIdx.x; p < Np; p += blockDim.x) {
       const int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
-      Tt[l][p] = B[l][p] - (d * X[l][p] - c * nbsum<T, DIM>(X[l], i, j, k, n, p));
+      Tt[l][p] = fma(kappa, nbsum<T, DIM>(X[l], i, j, k, n, p), B[l][p]) - X[l][p];
     }
     __syncthreads();
     for (int q = threadIdx.x; q < Nc; q += blockDim.x) {
@@ -448,7 +512,7 @@ __global__ void __launch_bounds__(kBottomThreads)
           const T* r = Tt[l] + (fi + n * (fj + dj));
           row[dj + 1] = (r[-1] + r[1]) + T(2) * r[0];
         }
-        acc = ((row[0] + row[2]) + T(2) * row[1]) * T(1.0 / 16.0);
+        acc = ((row[0] + row[2]) + T(2) * row[1]) * rs;
       } else {
         T pl[3];
         for (int dk = -1; dk <= 1; ++dk) {
@@ -459,7 +523,7 @@ __global__ void __launch_bounds__(kBottomThreads)
           }
           pl[dk + 1] = (row[0] + row[2]) + T(2) * row[1];
         }
-        acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * T(1.0 / 64.0);
+        acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * rs;
       }
       B[l + 1][q] = acc;
       X[l + 1][q] = T(0);

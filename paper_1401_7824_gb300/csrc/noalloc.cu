@@ -102,7 +102,7 @@ struct Layout {
   int nlev = 0, lb = 0;
   int side[kMaxLevels] = {};
   size_t npts[kMaxLevels] = {};
-  size_t ainv = 0, x[kMaxLevels] = {}, b[kMaxLevels] = {}, r[kMaxLevels] = {}, t[kMaxLevels] = {};
+  size_t ainv = 0, beta = 0, x[kMaxLevels] = {}, b[kMaxLevels] = {}, r[kMaxLevels] = {}, t[kMaxLevels] = {};
   size_t bytes = 0, bottom_smem = 0;
 };
 
@@ -128,6 +128,7 @@ void plan(int dim, int n, bool jacobi, Layout& L) {
     return o;
   };
   L.ainv = take(dim == 2 ? 81 : 729);
+  L.beta = take(L.npts[0]);
   for (int q = 0; q < L.nlev; ++q) {
     if (q < L.lb) {
       L.r[q] = take(L.npts[q]);
@@ -142,6 +143,17 @@ void plan(int dim, int n, bool jacobi, Layout& L) {
   size_t sm = 0;
   for (int q = L.lb; q < L.nlev; ++q) sm += 3 * L.npts[q] * sizeof(double);
   L.bottom_smem = sm;
+}
+
+struct Coef {
+  double d, kappa;
+};
+inline Coef coef(int dim, int s, double a) {
+  const double h = 1.0 / (s + 1), c = a / (h * h), d = 1.0 + 2.0 * dim * c;
+  return {d, c / d};
+}
+inline double restrict_scale(int dim, int s, int sc, double a) {
+  return coef(dim, s, a).d / (coef(dim, sc, a).d * (dim == 2 ? 16.0 : 64.0));
 }
 
 inline dim3 grid_pts(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
@@ -159,17 +171,17 @@ struct Solve {
 template <int DIM>
 isdc_status smooth(const Solve& S, int l, double*& x, double* home, const double* b, bool& zero, int sweeps) {
   const int s = S.L.side[l];
-  const double h = 1.0 / (s + 1), c = S.a / (h * h), d = 1.0 + 2.0 * DIM * c;
+  const double kappa = coef(DIM, s, S.a).kappa;
   const dim3 blk(kBX, kBY, 1);
   for (int it = 0; it < sweeps; ++it) {
     if (S.smoother == ISDC_SMOOTHER_JACOBI) {
       double* t = S.at(S.L.t[l]);
       double* out = (x == t) ? home : t;
-      k_jacobi<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, c, d, S.omega / d, x, b, out, zero ? 1 : 0);
+      k_jacobi<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, kappa, S.omega, x, b, out, zero ? 1 : 0);
       x = out;
     } else {
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, c / d, 1.0 / d, 0, x, b, zero ? 1 : 0);
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, c / d, 1.0 / d, 1, x, b, 0);
+      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 0, x, b, zero ? 1 : 0);
+      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 1, x, b, 0);
     }
     STATIC_TRY(cudaGetLastError());
     zero = false;
@@ -194,10 +206,10 @@ isdc_status one_vcycle(const Solve& S, double* x0, const double* b0) {
       zero = false;
     }
     if ((st = smooth<DIM>(S, l, x, home, b, zero, S.nu1)) != ISDC_OK) return st;
-    const double h = 1.0 / (s + 1), c = S.a / (h * h), d = 1.0 + 2.0 * DIM * c;
-    k_residual<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, c, d, x, b, S.at(L.r[l]));
-    k_restrict<double, DIM><<<grid_pts(DIM, L.side[l + 1]), blk, 0, S.stream>>>(L.side[l + 1], S.at(L.r[l]),
-                                                                                 S.at(L.b[l + 1]));
+    k_residual<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, coef(DIM, s, S.a).kappa, x, b,
+                                                                      S.at(L.r[l]));
+    k_restrict<double, DIM><<<grid_pts(DIM, L.side[l + 1]), blk, 0, S.stream>>>(
+        L.side[l + 1], restrict_scale(DIM, s, L.side[l + 1], S.a), S.at(L.r[l]), S.at(L.b[l + 1]));
     STATIC_TRY(cudaGetLastError());
     xcur[l] = x;
   }
@@ -206,10 +218,9 @@ isdc_status one_vcycle(const Solve& S, double* x0, const double* b0) {
     P.nlev = L.nlev - L.lb;
     for (int q = 0; q < P.nlev; ++q) {
       const int s = L.side[L.lb + q];
-      const double h = 1.0 / (s + 1), c = S.a / (h * h);
       P.side[q] = s;
-      P.c[q] = c;
-      P.d[q] = 1.0 + 2.0 * DIM * c;
+      P.kappa[q] = coef(DIM, s, S.a).kappa;
+      P.rscale[q] = q + 1 < P.nlev ? restrict_scale(DIM, s, L.side[L.lb + q + 1], S.a) : 0.0;
     }
     P.smoother = S.smoother;
     P.nu1 = S.nu1;
@@ -225,7 +236,8 @@ isdc_status one_vcycle(const Solve& S, double* x0, const double* b0) {
   for (int l = L.lb - 1; l >= 0; --l) {
     double* home = l == 0 ? x0 : S.at(L.x[l]);
     double* x = xcur[l];
-    k_prolong_add<double, DIM><<<grid_pts(DIM, L.side[l]), blk, 0, S.stream>>>(L.side[l + 1], xcur[l + 1], x);
+    k_prolong_add<double, DIM><<<grid_pts(DIM, L.side[l + 1] + 1), blk, 0, S.stream>>>(L.side[l + 1], xcur[l + 1],
+                                                                                        x);
     STATIC_TRY(cudaGetLastError());
     bool zero = false;
     if ((st = smooth<DIM>(S, l, x, home, l == 0 ? b0 : S.at(L.b[l]), zero, S.nu2)) != ISDC_OK) return st;
@@ -262,11 +274,17 @@ ISDC_API isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoo
   S.base = static_cast<unsigned char*>(addr);
   double inv[27 * 27];
   side3_inverse(ndim, a, inv);
+  const double d3 = 1.0 + 2.0 * ndim * a * 16.0;  // the inverse acts on beta = b / d (h = 1/4)
+  for (int q = 0; q < (ndim == 2 ? 81 : 729); ++q) inv[q] *= d3;
   // pageable source: the copy is staged before cudaMemcpyAsync returns
   STATIC_TRY(cudaMemcpyAsync(S.at(S.L.ainv), inv, (ndim == 2 ? 81 : 729) * sizeof(double), cudaMemcpyHostToDevice,
                              S.stream));
+  // the V-cycles act on the row-scaled system x - kappa * (neighbour sum) = b / d
+  double* beta = S.at(S.L.beta);
+  k_scale<double><<<4 * 152, 256, 0, S.stream>>>(S.L.npts[0], 1.0 / coef(ndim, int(n), a).d, b, beta);
+  STATIC_TRY(cudaGetLastError());
   for (int c = 0; c < n_cycles; ++c) {
-    st = ndim == 2 ? one_vcycle<2>(S, x, b) : one_vcycle<3>(S, x, b);
+    st = ndim == 2 ? one_vcycle<2>(S, x, beta) : one_vcycle<3>(S, x, beta);
     if (st != ISDC_OK) return st;
   }
   return ISDC_OK;

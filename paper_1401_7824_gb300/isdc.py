@@ -23,7 +23,7 @@ ISDC_ERR_NONFINITE = 6
 ISDC_ERR_SCRATCH_TOO_SMALL = 7
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "NOT_CONVERGED",
                 6: "NONFINITE", 7: "SCRATCH_TOO_SMALL"}
-ISDC_STATIC_SCRATCH_BYTES = 48 << 20
+ISDC_STATIC_SCRATCH_BYTES = 64 << 20
 
 ISDC_NODES_GAUSS_LOBATTO = 0
 ISDC_NODES_RADAU_RIGHT = 1
@@ -216,8 +216,23 @@ def isdc_vcycles_static(ndim, n, a: float, x, b, n_cycles: int, smoother=ISDC_SM
     return st
 
 
-def isdc_profile_enable(ctx, enable: bool):
-    _check(load().isdc_profile_enable(ctx, 1 if enable else 0), ctx)
+PROFILE_CLASSES = ["spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine",
+                   "prolong_fine", "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse",
+                   "bottom", "defect", "update", "resnorm"]
+
+
+def isdc_profile_enable(ctx, enable, classes=None):
+    """enable: False = off; True = time every class with events, or only the
+    named `classes` (counts, bytes and ops are kept for all)."""
+    if not enable:
+        mask = 0
+    elif classes is None:
+        mask = -1
+    else:
+        mask = 0
+        for c in classes:
+            mask |= 1 << PROFILE_CLASSES.index(c)
+    _check(load().isdc_profile_enable(ctx, mask), ctx)
 
 
 def isdc_profile_read(ctx):
@@ -293,8 +308,8 @@ class Isdc:
     def vcycles(self, a, x, b, n_cycles):
         isdc_vcycles(self.ctx, a, x, b, n_cycles)
 
-    def profile(self, on=True):
-        isdc_profile_enable(self.ctx, on)
+    def profile(self, on=True, classes=None):
+        isdc_profile_enable(self.ctx, on, classes)
 
     def profile_read(self):
         return isdc_profile_read(self.ctx)

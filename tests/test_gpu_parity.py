@@ -85,7 +85,8 @@ def test_steps_match_oracle_fp64(case):
         g.step(u, ref.sweeps[s], L)
         assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-12
         hist = g.history()
-        np.testing.assert_allclose(hist, ref.residuals[s], rtol=1e-6, atol=1e-14)
+        # the SDC residual is a difference of O(dt |f|) terms: ~1e-14 absolute rounding floor
+        np.testing.assert_allclose(hist, ref.residuals[s], rtol=1e-6, atol=1e-13)
 
 
 def test_workload_2d_127_ten_steps():
