@@ -101,37 +101,25 @@ __global__ void __launch_bounds__(kBX* kBY)
   r[p] = fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]) - x[p];
 }
 
-// Full weighting to the coarse grid (side nc, fine side 2nc+1): coarse point
-// I sits on fine point 2I+1 (0-based); weights (1/4, 1/2, 1/4) per axis.  The
-// input is the fine scaled residual r' = r/d_f and the output the coarse scaled
-// right-hand side beta_c = FW(r)/d_c, so the final factor is
-// wscale = d_f / (2^(2 DIM) d_c).
+// Full weighting at coarse point (I,J,K) (see k_restrict).
 // RED_ONLY: the residual vanishes at the black points (see k_residual); the
 // coarse point's own fine point and its edge neighbours are red, its face and
 // corner neighbours black, so full weighting keeps 5 (2D) or 13 (3D) terms.
-template <typename T, int DIM, bool RED_ONLY = false>
-__global__ void __launch_bounds__(kBX* kBY)
-    k_restrict(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
-  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I >= nc || J >= nc) return;
+template <typename T, int DIM, bool RED_ONLY>
+__device__ __forceinline__ T restrict_point(int nc, T wscale, const T* __restrict__ r, int I, int J, int K) {
   const int n = 2 * nc + 1;
   const int fi = 2 * I + 1, fj = 2 * J + 1;
-  T acc = T(0);
   if (RED_ONLY) {
     if (DIM == 2) {
       const T* q = r + (fi + n * fj);
-      acc = fma(T(4), q[0], (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1])) * wscale;
-    } else {
-      const int nn = n * n;
-      const T* q = r + (fi + n * (fj + n * (2 * K + 1)));
-      const T e_xy = (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1]);
-      const T e_xz = (q[-nn - 1] + q[-nn + 1]) + (q[nn - 1] + q[nn + 1]);
-      const T e_yz = (q[-nn - n] + q[-nn + n]) + (q[nn - n] + q[nn + n]);
-      acc = fma(T(2), (e_xy + e_xz) + e_yz, T(8) * q[0]) * wscale;
+      return fma(T(4), q[0], (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1])) * wscale;
     }
-    bc[lin<DIM>(I, J, K, nc)] = acc;
-    return;
+    const int nn = n * n;
+    const T* q = r + (fi + n * (fj + n * (2 * K + 1)));
+    const T e_xy = (q[-n - 1] + q[-n + 1]) + (q[n - 1] + q[n + 1]);
+    const T e_xz = (q[-nn - 1] + q[-nn + 1]) + (q[nn - 1] + q[nn + 1]);
+    const T e_yz = (q[-nn - n] + q[-nn + n]) + (q[nn - n] + q[nn + n]);
+    return fma(T(2), (e_xy + e_xz) + e_yz, T(8) * q[0]) * wscale;
   }
   if (DIM == 2) {
     T row[3];
@@ -140,40 +128,50 @@ __global__ void __launch_bounds__(kBX* kBY)
       const T* q = r + (fi + n * (fj + dj));
       row[dj + 1] = (q[-1] + q[1]) + T(2) * q[0];
     }
-    acc = ((row[0] + row[2]) + T(2) * row[1]) * wscale;
-  } else {
-    const int fk = 2 * K + 1;
-    T pl[3];
-#pragma unroll
-    for (int dk = -1; dk <= 1; ++dk) {
-      T row[3];
-#pragma unroll
-      for (int dj = -1; dj <= 1; ++dj) {
-        const T* q = r + (fi + n * ((fj + dj) + n * (fk + dk)));
-        row[dj + 1] = (q[-1] + q[1]) + T(2) * q[0];
-      }
-      pl[dk + 1] = (row[0] + row[2]) + T(2) * row[1];
-    }
-    acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * wscale;
+    return ((row[0] + row[2]) + T(2) * row[1]) * wscale;
   }
-  bc[lin<DIM>(I, J, K, nc)] = acc;
+  const int fk = 2 * K + 1;
+  T pl[3];
+#pragma unroll
+  for (int dk = -1; dk <= 1; ++dk) {
+    T row[3];
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const T* q = r + (fi + n * ((fj + dj) + n * (fk + dk)));
+      row[dj + 1] = (q[-1] + q[1]) + T(2) * q[0];
+    }
+    pl[dk + 1] = (row[0] + row[2]) + T(2) * row[1];
+  }
+  return ((pl[0] + pl[2]) + T(2) * pl[1]) * wscale;
 }
 
-// x += P e_c: (bi/tri)linear interpolation from the coarse grid (side nc) to
-// the fine grid (side n = 2nc+1); coarse ghosts are zero.  One thread per
-// coarse cell (I,J,K) in [0, nc]^DIM owns the fine points {2I, 2I+1} x
-// {2J, 2J+1} (x {2K, 2K+1}): the odd index coincides with coarse I, the even
-// one lies between coarse I-1 and I.  The interpolated values are built from
-// shared partial sums (2.5 operations per fine point in 3D).
+// Full weighting to the coarse grid (side nc, fine side 2nc+1): coarse point
+// I sits on fine point 2I+1 (0-based); weights (1/4, 1/2, 1/4) per axis.  The
+// input is the fine scaled residual r' = r/d_f and the output the coarse scaled
+// right-hand side beta_c = FW(r)/d_c, so the final factor is
+// wscale = d_f / (2^(2 DIM) d_c).
+template <typename T, int DIM, bool RED_ONLY = false>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_restrict(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
+  bc[lin<DIM>(I, J, K, nc)] = restrict_point<T, DIM, RED_ONLY>(nc, wscale, r, I, J, K);
+}
+
+// x += P e_c on the fine points of coarse cell (I,J,K): (bi/tri)linear
+// interpolation from the coarse grid (side nc) to the fine grid (side
+// n = 2nc+1); coarse ghosts are zero.  Cell (I,J,K) in [0, nc]^DIM owns the
+// fine points {2I, 2I+1} x {2J, 2J+1} (x {2K, 2K+1}): the odd index coincides
+// with coarse I, the even one lies between coarse I-1 and I.  The
+// interpolated values are built from shared partial sums (2.5 operations per
+// fine point in 3D).
 // BLACK_ONLY: the next operation on this level is a red half sweep, which
 // overwrites every red point without reading it, so only the black fine points
 // (1-based index sum odd) are corrected; the result is the same.
-template <typename T, int DIM, bool BLACK_ONLY = false>
-__global__ void __launch_bounds__(kBX* kBY)
-    k_prolong_add(int nc, const T* __restrict__ ec, T* __restrict__ x) {
-  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I > nc || J > nc) return;
+template <typename T, int DIM, bool BLACK_ONLY>
+__device__ __forceinline__ void prolong_cell(int nc, const T* __restrict__ ec, T* __restrict__ x, int I, int J,
+                                             int K) {
   const int n = 2 * nc + 1;
   const bool hi_i = I > 0, ok_i = I < nc, hi_j = J > 0, ok_j = J < nc;
   const int fi = 2 * I, fj = 2 * J;
@@ -224,6 +222,15 @@ __global__ void __launch_bounds__(kBX* kBY)
       }
     }
   }
+}
+
+template <typename T, int DIM, bool BLACK_ONLY = false>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_prolong_add(int nc, const T* __restrict__ ec, T* __restrict__ x) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I > nc || J > nc) return;
+  prolong_cell<T, DIM, BLACK_ONLY>(nc, ec, x, I, J, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,12 +394,14 @@ __global__ void __launch_bounds__(kBX* kBY)
           if (jj < M) acc = fma(tb.dtQ[m][jj], f[jj], acc);
         qf[m] = acc;
       }
-    double rmax = 0.0;
+    // max of |r| on the integer pipe: with the sign bit cleared, doubles order
+    // like their bit patterns (NaN above Inf), so no FP64 compares are needed
 #pragma unroll
     for (int m = 1; m < kMaxM; ++m)
       if (m < M) {
-        const double r = fabs((u[0] - u[m]) + qf[m]);
-        rmax = (r > rmax || r != r) ? r : rmax;
+        const unsigned long long rbits =
+            (unsigned long long)__double_as_longlong((u[0] - u[m]) + qf[m]) & 0x7fffffffffffffffull;
+        rb = rbits > rb ? rbits : rb;
       }
 #pragma unroll
     for (int m = 0; m < kMaxM - 1; ++m)
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(kBX* kBY)
         // f^I(u_{m+1}) = f_{m+1} - f^E(u_{m+1})
         C[m * N + p] = fma(-tb.dtm[m], fe[m] + (f[m + 1] - fe[m + 1]), sf);
       }
-    rb = (unsigned long long)__double_as_longlong(rmax);
+
   }
   block_max_atomic(rb, Rbits);
 }
@@ -416,8 +425,8 @@ __global__ void __launch_bounds__(kBX* kBY)
   unsigned long long rb = 0;
   if (i < n && j < n) {
     const int p = lin<DIM>(i, j, k, n);
-    const double r = d * fabs(fma(kappa, nbsum<double, DIM>(x, i, j, k, n, p), beta[p]) - x[p]);
-    rb = (unsigned long long)__double_as_longlong(r);
+    const double r = d * (fma(kappa, nbsum<double, DIM>(x, i, j, k, n, p), beta[p]) - x[p]);
+    rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
   }
   block_max_atomic(rb, out);
 }
@@ -497,35 +506,18 @@ __global__ void __launch_bounds__(kBottomThreads)
     const int Nc = DIM == 2 ? nc * nc : nc * nc * nc;
     for (int s = 0; s < P.nu1; ++s) bt_smooth<T, DIM>(P, l, X[l], B[l], Tt[l]);
     const T kappa = P.kappa[l], rs = P.rscale[l];
+    // after a complete red-black sweep only the red rows carry a residual
+    const bool red_only = P.smoother == 1 && P.nu1 >= 1;
     for (int p = threadIdx.x; p < Np; p += blockDim.x) {
       const int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
+      if (red_only && ((i + j + k + DIM) & 1)) continue;
       Tt[l][p] = fma(kappa, nbsum<T, DIM>(X[l], i, j, k, n, p), B[l][p]) - X[l][p];
     }
     __syncthreads();
     for (int q = threadIdx.x; q < Nc; q += blockDim.x) {
       const int I = q % nc, J = (q / nc) % nc, K = DIM == 3 ? q / (nc * nc) : 0;
-      const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
-      T acc;
-      if (DIM == 2) {
-        T row[3];
-        for (int dj = -1; dj <= 1; ++dj) {
-          const T* r = Tt[l] + (fi + n * (fj + dj));
-          row[dj + 1] = (r[-1] + r[1]) + T(2) * r[0];
-        }
-        acc = ((row[0] + row[2]) + T(2) * row[1]) * rs;
-      } else {
-        T pl[3];
-        for (int dk = -1; dk <= 1; ++dk) {
-          T row[3];
-          for (int dj = -1; dj <= 1; ++dj) {
-            const T* r = Tt[l] + (fi + n * ((fj + dj) + n * (fk + dk)));
-            row[dj + 1] = (r[-1] + r[1]) + T(2) * r[0];
-          }
-          pl[dk + 1] = (row[0] + row[2]) + T(2) * row[1];
-        }
-        acc = ((pl[0] + pl[2]) + T(2) * pl[1]) * rs;
-      }
-      B[l + 1][q] = acc;
+      B[l + 1][q] = red_only ? restrict_point<T, DIM, true>(nc, rs, Tt[l], I, J, K)
+                             : restrict_point<T, DIM, false>(nc, rs, Tt[l], I, J, K);
       X[l + 1][q] = T(0);
     }
     __syncthreads();
@@ -543,34 +535,14 @@ __global__ void __launch_bounds__(kBottomThreads)
   }
   // upward leg
   for (int l = last - 1; l >= 0; --l) {
-    const int n = P.side[l], nc = P.side[l + 1];
-    const int Np = DIM == 2 ? n * n : n * n * n;
-    for (int p = threadIdx.x; p < Np; p += blockDim.x) {
-      const int i = p % n, j = (p / n) % n, k = DIM == 3 ? p / (n * n) : 0;
-      int ci[2], cj[2], ck[2];
-      T wi[2], wj[2], wk[2];
-      int ni = 0, nj = 0, nk = 0;
-      auto axis = [nc](int f, int* cc, T* w, int* cnt) {
-        if (f & 1) {
-          cc[0] = (f - 1) >> 1; w[0] = T(1); *cnt = 1;
-        } else {
-          int m = 0;
-          if (f > 0) { cc[m] = (f - 2) >> 1; w[m] = T(0.5); ++m; }
-          if (f / 2 < nc) { cc[m] = f >> 1; w[m] = T(0.5); ++m; }
-          *cnt = m;
-        }
-      };
-      axis(i, ci, wi, &ni);
-      axis(j, cj, wj, &nj);
-      if (DIM == 3) axis(k, ck, wk, &nk); else { ck[0] = 0; wk[0] = T(1); nk = 1; }
-      T e = T(0);
-      for (int c3 = 0; c3 < nk; ++c3)
-        for (int c2 = 0; c2 < nj; ++c2) {
-          T line = T(0);
-          for (int c1 = 0; c1 < ni; ++c1) line += wi[c1] * X[l + 1][lin<DIM>(ci[c1], cj[c2], ck[c3], nc)];
-          e += (wj[c2] * wk[c3]) * line;
-        }
-      X[l][p] += e;
+    const int nc = P.side[l + 1];
+    // a red half sweep follows: correct the black points only
+    const bool black_only = P.smoother == 1 && P.nu2 >= 1;
+    const int cells = DIM == 2 ? (nc + 1) * (nc + 1) : (nc + 1) * (nc + 1) * (nc + 1);
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+      const int I = q % (nc + 1), J = (q / (nc + 1)) % (nc + 1), K = DIM == 3 ? q / ((nc + 1) * (nc + 1)) : 0;
+      if (black_only) prolong_cell<T, DIM, true>(nc, X[l + 1], X[l], I, J, K);
+      else prolong_cell<T, DIM, false>(nc, X[l + 1], X[l], I, J, K);
     }
     __syncthreads();
     for (int s = 0; s < P.nu2; ++s) bt_smooth<T, DIM>(P, l, X[l], B[l], Tt[l]);
