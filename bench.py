@@ -179,7 +179,7 @@ def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    w = workloads()[args.workload]
+    w = workloads().get(args.workload, W.workload_3d_255())
     n_sample = 127 if w.ndim == 3 and w.n > 127 else w.n
     for _ in range(args.warmup):
         oracle_sweep_rate(w, n_sample)
@@ -327,19 +327,130 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """256 independent 2D instances (sides 2^j - 1, j in 6..10; nu, dt, M drawn
+    from seed 4) in one batch engine: FP32 V-cycles, FP64 SDC state, damped
+    Jacobi V(1,1), L = 2.  One bench step = one tick = one SDC sweep of every
+    running instance (one CUDA graph launch).  Warm-up ticks include the
+    autotuner's trial ticks."""
+    import torch
+    import paper_1401_7824_gb300 as G
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    insts = W.batch_instances(256, seed=4)
+    stream = torch.cuda.Stream()
+    o = G.isdc_default_options()
+    o.smoother, o.nu1, o.nu2, o.vcycle_fp32, o.tol, o.max_sweeps = G.ISDC_SMOOTHER_JACOBI, 1, 1, 1, 1e-10, 150
+    import ctypes
+    o.stream = ctypes.c_void_p(stream.cuda_stream)
+    eng = G.isdc_batch_create(2, 1023, 5, 200 << 30, 2, o)
+    sides = {}
+    for q, w in enumerate(insts):
+        slot = G.isdc_batch_admit(eng, w.n, w.nu, w.M, w.dt, w.steps, W.initial_condition(2, w.n, w.seed))
+        assert slot is not None
+        sides[slot] = w.n
+    warm = max(args.warmup, 6)
+    for _ in range(warm):
+        G.isdc_batch_tick(eng)
+    info = G.isdc_batch_stats(eng)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(None)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dofs = 0.0
+    e0.record(stream)
+    for _ in range(args.steps):
+        live = [s for s in sides if G.isdc_batch_query(eng, s).state == G.ISDC_SLOT_RUNNING]
+        dofs += sum(float(sides[s] ** 2) for s in live)
+        G.isdc_batch_tick(eng)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    info = G.isdc_batch_stats(eng)
+    G.isdc_batch_destroy(eng)
+    line = {"metric": "DOF-sweeps/s", "value": dofs / elapsed, "unit": "DOF-sweeps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": warm, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 V-cycles)",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "batch_2d_256", "instances": len(insts),
+                       "dofs_total": int(sum(w.n ** 2 for w in insts)),
+                       "sides": "2^j - 1, j uniform in 6..10", "smoother": "wjacobi V(1,1)", "L_vcycles": 2,
+                       "vcycle_precision": "fp32", "tol": 1e-10,
+                       "l2": "inputs larger than L2 (all instances resident, tens of GB)",
+                       "launch_shape": {"threads_per_block": info.threads_per_block,
+                                        "blocks_per_sm": info.blocks_per_sm, "tuned": info.tuned}},
+            "clocks": clk}
+    if args.compare_fp64:
+        # the same instances one at a time through the FP64 single-instance path
+        tot_dofs, tot_t = 0.0, 0.0
+        for w in insts[:args.compare_fp64]:
+            g = G.Isdc(2, w.n, w.nu, w.M, w.dt, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+            u = torch.from_numpy(W.initial_condition(2, w.n, w.seed)).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(u, 0, 2)
+            torch.cuda.synchronize()
+            tot_t += time.perf_counter() - t0
+            tot_dofs += w.n ** 2 * g.stats()[0]
+            g.close()
+        line["fp64_single_instance"] = {"value": tot_dofs / tot_t, "unit": "DOF-sweeps/s",
+                                        "instances": args.compare_fp64,
+                                        "what": "first time step of each instance, FP64 V-cycles, one "
+                                                "instance at a time through isdc_step"}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson stream of ISDC requests (70 % 2D sides 127..1023, 30 % 3D sides
+    63..255, M in {3,5}, 10 steps, tol 1e-10) served by continuous batching."""
+    import torch
+    from paper_1401_7824_gb300.serve import Request, Server
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = W.request_stream(args.requests, rate=args.rate, seed=5)
+    reqs = [Request(q, t, w.ndim, w.n, w.nu, w.M, w.dt, w.steps, W.initial_condition(w.ndim, w.n, w.seed))
+            for q, (t, w) in enumerate(stream)]
+    srv = Server(hbm_budget_bytes=(60 << 30, 160 << 30), max_side=(1023, 255))
+    clocks = ClockSampler(None)
+    clocks.start()
+    rep = srv.run(reqs, realtime=True)
+    clk = clocks.stop()
+    srv.close()
+    s = rep.summary()
+    line = {"metric": "DOF-sweeps/s", "value": s["dof_sweeps_per_s"], "unit": "DOF-sweeps/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "ms_per_step": s["wall_s"] * 1e3 / max(1, args.requests),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 V-cycles)",
+            "data": "synthetic Poisson request stream (seed 5)",
+            "config": {"workload": "serve_poisson", "requests": args.requests, "rate_per_s": args.rate,
+                       "mix": "70% 2D n in 127..1023, 30% 3D n in 63..255, M in {3,5}, 10 steps, tol 1e-10"},
+            "latency": {"p50_s": s["p50_s"], "p99_s": s["p99_s"], "mean_s": s["mean_s"],
+                        "completed": s["completed"], "failed": s["failed"], "wall_s": s["wall_s"]},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="3d_n255_M5_fp64", choices=sorted(workloads()))
+    ap.add_argument("--workload", default="3d_n255_M5_fp64",
+                    choices=sorted(workloads()) + ["batch_2d_256", "serve_poisson"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-fp64", type=int, default=0, help="batch: also time N instances on the FP64 path")
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch_2d_256":
+        run_batch(args)
+    elif args.workload == "serve_poisson":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -204,6 +204,85 @@ isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, in
 isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoother, int nu1, int nu2, double omega,
                                 double *x, const double *b, int n_cycles, void *stream);
 
+/*
+ * Batched and continuously batched integration (not from the paper: the
+ * serving layer around it).  An engine holds up to 256 independent ISDC
+ * integrations of one dimension (each with its own side, nu, M, dt and number
+ * of time steps; the smoother, nu1/nu2, L, tol and max_sweeps are the
+ * engine's).  Every tick advances every running instance by one SDC sweep:
+ * each phase of the sweep is one grid-stride launch over all instances taking
+ * part, and the whole tick is one CUDA graph.  V-cycles run in FP32 in
+ * defect-correction form; node values, S F, node residuals and the SDC
+ * residual are FP64.  Instances are admitted and their results taken between
+ * ticks; device memory for an instance is taken with cudaMallocAsync on
+ * admission, within the engine's HBM budget, and returned by isdc_batch_take.
+ * An engine is not thread-safe.
+ */
+typedef struct isdc_batch isdc_batch;
+
+typedef struct {
+    int64_t n;     /* interior side, 2^j - 1, 7 <= n <= the engine's max_side */
+    double  nu;    /* diffusion coefficient */
+    int     M;     /* Gauss-Lobatto nodes, 2 <= M <= the engine's max_M */
+    double  dt;    /* time-step length */
+    int     steps; /* time steps to run */
+} isdc_problem;
+
+enum { ISDC_SLOT_FREE = 0, ISDC_SLOT_RUNNING = 1, ISDC_SLOT_FINISHED = 2, ISDC_SLOT_FAILED = 3 };
+
+typedef struct {
+    int     state;              /* ISDC_SLOT_* */
+    int     steps_done;
+    int     sweeps_in_step;     /* sweeps of the current step so far */
+    int     total_sweeps;
+    int     nonconverged_steps; /* steps that ended at max_sweeps without reaching tol */
+    double  last_residual;      /* SDC residual after the instance's last sweep */
+    size_t  device_bytes;       /* device memory held by the instance */
+} isdc_slot_info;
+
+typedef struct {
+    int64_t ticks;
+    size_t  bytes_in_use;
+    int     running;
+    int     tuned;              /* 1 once the autotuner has picked the launch shape */
+    int     threads_per_block;  /* launch shape in use (tile = one point per thread) */
+    int     blocks_per_sm;      /* persistent blocks per SM */
+} isdc_batch_info;
+
+/* ndim 2 or 3; max_side: the largest side that will be admitted (sets the
+ * number of multigrid phases); max_M <= 7; hbm_budget_bytes: device memory the
+ * instances may hold together; n_vcycles: L >= 1; opt as for isdc_create
+ * (nu1 >= 1 is required; vcycle_fp32 is implied; stream NULL = own stream).
+ * The first ticks try several launch shapes and keep the fastest (autotuner).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, size_t hbm_budget_bytes, int n_vcycles,
+                              const isdc_options *opt, isdc_batch **out);
+
+/* Admit one integration with initial value u0 (n^ndim float64; host memory if
+ * u0_on_host, else device).  *slot receives the instance's slot.  Returns
+ * ISDC_ERR_OOM (soft: retry after taking results) when the budget or the
+ * slots are exhausted.  Synchronises the engine's stream. */
+isdc_status isdc_batch_admit(isdc_batch *b, const isdc_problem *p, const double *u0, int u0_on_host, int *slot);
+
+/* One sweep for every running instance (one graph launch); synchronises.
+ * *running: instances still running afterwards; *finished: instances that
+ * finished (or failed) in this tick.  Either pointer may be NULL. */
+isdc_status isdc_batch_tick(isdc_batch *b, int *running, int *finished);
+
+isdc_status isdc_batch_query(const isdc_batch *b, int slot, isdc_slot_info *info);
+
+/* Copy a finished instance's solution (u after its last step; n^ndim float64,
+ * host memory if out_on_host, else device; u_out may be NULL to discard) and
+ * free its slot and device memory. */
+isdc_status isdc_batch_take(isdc_batch *b, int slot, double *u_out, int out_on_host);
+
+isdc_status isdc_batch_stats(const isdc_batch *b, isdc_batch_info *info);
+
+/* Message for the last failure of b, or of isdc_batch_create when b is NULL. */
+const char *isdc_batch_last_error(const isdc_batch *b);
+
+void isdc_batch_destroy(isdc_batch *b);
+
 /* Per-kernel-class timing (not from the paper: instrumentation for the
  * roofline).  While enabled, every launch of the context is bracketed by CUDA
  * events on its stream, and the algorithmic bytes and floating-point

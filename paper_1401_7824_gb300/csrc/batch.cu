@@ -1,0 +1,577 @@
+// batch.cu -- the batched / continuously batched ISDC engine (isdc_batch_*).
+//
+// An engine holds up to kMaxInst independent ISDC integrations of one spatial
+// dimension, each with its own side n, nu, M, dt and number of time steps.
+// A tick advances every running instance by one SDC sweep (Sec. 2, Eq. 4;
+// Sec. 3): instances that start a time step are spread first, then the node
+// solves run with L FP32 V-cycles in defect-correction form (FP64 node state,
+// quadrature term, node residual and SDC residual), then every instance's SDC
+// residual is read back.  Each phase of the tick is one persistent
+// grid-stride launch over the work list of all instances taking part, and the
+// whole tick is one CUDA graph, captured once: the work lists live in device
+// memory and are rewritten before each launch, so instances can be admitted
+// and retired between ticks without re-capture (continuous batching).  Device
+// memory for an instance is taken with cudaMallocAsync when it is admitted,
+// within an HBM budget, and returned when its result is taken.
+//
+// Autotuning: the first ticks run with different launch shapes (threads per
+// block = tile size, persistent blocks per SM); each tick's DOF-sweep rate is
+// measured with events and the fastest shape is kept for the engine's life.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/isdc.h"
+#include "batch_kernels.cuh"
+#include "host_util.h"
+
+#define ISDC_API extern "C" __attribute__((visibility("default")))
+
+using namespace isdc;
+using namespace isdc::batch;
+
+namespace {
+
+thread_local char g_batch_error[512] = "";
+
+enum ListKind { LK_FULL = 0, LK_HALF = 1, LK_CPTS = 2, LK_CELLS = 3 };
+
+struct Slot {
+  int state = ISDC_SLOT_FREE;
+  int n = 0, M = 0, nlev = 0, steps = 0, steps_done = 0, sweeps = 0, total_sweeps = 0, nonconverged = 0;
+  bool spread_next = false;
+  double last_res = 0.0;
+  size_t bytes = 0;
+  void* mem = nullptr;
+};
+
+struct Shape {
+  int threads, blocks_per_sm;
+};
+const Shape kShapes[] = {{256, 8}, {128, 16}, {512, 4}, {256, 16}, {512, 8}};
+constexpr int kNumShapes = int(sizeof(kShapes) / sizeof(kShapes[0]));
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct isdc_batch {
+  int dim = 0, L = 2, Mmax = 0, Lmax = 0, sms = 0, max_side = 0;
+  isdc_options opt{};
+  size_t budget = 0, used = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Inst* d_insts = nullptr;
+  Inst* h_insts = nullptr;  // pinned mirror
+  List* d_lists = nullptr;
+  List* h_lists = nullptr;  // pinned staging
+  int nlists = 0;
+  unsigned long long *d_rbits = nullptr, *d_dummy = nullptr, *h_rbits = nullptr;
+  Slot slots[kMaxInst];
+  // graph per launch shape
+  cudaGraphExec_t exec[kNumShapes] = {};
+  int shape = 0;         // shape in use
+  int tuned = 0;         // 1 once the autotuner has chosen
+  int tune_next = 0;     // next shape to try
+  double tune_rate[kNumShapes] = {};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long ticks = 0;
+  char err[512] = "";
+};
+
+namespace {
+
+isdc_status bfail(isdc_batch* b, isdc_status st, const char* fmt, ...) {
+  char* dst = b ? b->err : g_batch_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define B_TRY(b, call)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? ISDC_ERR_OOM : ISDC_ERR_CUDA, "%s: %s", #call, \
+                   cudaGetErrorString(e_));                                                         \
+  } while (0)
+
+int levels_of(int n) {
+  int l = 1;
+  while (n > 3) { n = (n - 1) / 2; ++l; }
+  return l;
+}
+
+size_t pts(int dim, int n) { return dim == 2 ? size_t(n) * n : size_t(n) * n * n; }
+
+int list_index(const isdc_batch* b, int m, int l, int kind) { return ((m * b->Lmax) + l) * 4 + kind; }
+int list_coarse(const isdc_batch* b, int m) { return (b->Mmax - 1) * b->Lmax * 4 + m; }
+int list_spread(const isdc_batch* b) { return (b->Mmax - 1) * b->Lmax * 4 + (b->Mmax - 1); }
+int list_sweep(const isdc_batch* b) { return list_spread(b) + 1; }
+
+// Bytes of device memory one instance needs (node state FP64, hierarchy FP32).
+size_t instance_bytes(const isdc_batch* b, int n, int M) {
+  const size_t N = pts(b->dim, n);
+  size_t s = 0;
+  s += align256(size_t(M) * N * 8);        // U
+  s += align256(size_t(M) * N * 8);        // F
+  s += align256(size_t(M - 1) * N * 8);    // C
+  s += align256(N * 8);                    // beta
+  const int nlev = levels_of(n);
+  int side = n;
+  const int per_level = b->opt.smoother == ISDC_SMOOTHER_JACOBI ? 4 : 3;
+  for (int l = 0; l < nlev; ++l) {
+    s += per_level * align256(pts(b->dim, side) * 4);
+    side = (side - 1) / 2;
+  }
+  s += align256(size_t(M - 1) * (b->dim == 2 ? 81 : 729) * 4);  // coarse inverses
+  return s;
+}
+
+// Rebuild every work list for the current running set and tile size.
+void build_lists(isdc_batch* b, int tile) {
+  for (int q = 0; q < b->nlists; ++q) {
+    b->h_lists[q].count = 0;
+    b->h_lists[q].total = 0;
+    b->h_lists[q].start[0] = 0;
+  }
+  auto add = [&](int li, int inst, size_t domain) {
+    List& L = b->h_lists[li];
+    const int tiles = int((domain + tile - 1) / tile);
+    L.inst[L.count] = inst;
+    L.start[L.count] = L.total;
+    L.total += tiles;
+    L.count += 1;
+    L.start[L.count] = L.total;
+  };
+  const int dim = b->dim;
+  for (int i = 0; i < kMaxInst; ++i) {
+    const Slot& S = b->slots[i];
+    if (S.state != ISDC_SLOT_RUNNING) continue;
+    const size_t N = pts(dim, S.n);
+    if (S.spread_next) add(list_spread(b), i, N);
+    add(list_sweep(b), i, N);
+    for (int m = 0; m < S.M - 1; ++m) {
+      add(list_coarse(b, m), i, dim == 2 ? 9 : 27);
+      int side = S.n;
+      for (int l = 0; l < S.nlev - 1; ++l) {
+        const int sc = (side - 1) / 2;
+        add(list_index(b, m, l, LK_FULL), i, pts(dim, side));
+        add(list_index(b, m, l, LK_HALF), i, size_t((side + 1) / 2) * (dim == 2 ? side : size_t(side) * side));
+        add(list_index(b, m, l, LK_CPTS), i, pts(dim, sc));
+        add(list_index(b, m, l, LK_CELLS), i, pts(dim, sc + 1));
+        side = sc;
+      }
+    }
+  }
+}
+
+// Record one tick's launches on the stream (inside a capture).
+template <int DIM>
+void record_tick(isdc_batch* b, const Shape& sh) {
+  const dim3 grid(sh.blocks_per_sm * b->sms), blk(sh.threads);
+  cudaStream_t st = b->stream;
+  const Inst* I = b->d_insts;
+  const List* Ls = b->d_lists;
+  const int reaction = b->opt.reaction;
+  const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
+  const int nu1 = b->opt.nu1, nu2 = b->opt.nu2;
+  const int par = (nu1 + nu2) & 1;  // Jacobi: a level's iterate ends in t after an odd sweep count
+  cudaMemsetAsync(b->d_rbits, 0, sizeof(unsigned long long) * kMaxInst, st);
+  kb_spread<DIM><<<grid, blk, 0, st>>>(I, Ls + list_spread(b), reaction);
+  kb_sweep_end<DIM><<<grid, blk, 0, st>>>(I, Ls + list_spread(b), reaction, b->d_dummy);
+  for (int m = 0; m < b->Mmax - 1; ++m) {
+    const List* full0 = Ls + list_index(b, m, 0, LK_FULL);
+    kb_rhs<DIM><<<grid, blk, 0, st>>>(I, full0, m, reaction);
+    kb_defect<DIM><<<grid, blk, 0, st>>>(I, full0, m);
+    int loc0 = 0;  // level-0 error: in x (0) or t (1)
+    for (int c = 0; c < b->L; ++c) {
+      for (int l = 0; l < b->Lmax - 1; ++l) {
+        const bool zero = l > 0 || c == 0;
+        int loc = l == 0 ? loc0 : 0;
+        for (int s = 0; s < nu1; ++s) {
+          if (jac) {
+            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, float(b->opt.omega),
+                                                 loc, zero && s == 0);
+            loc ^= 1;
+          } else {
+            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, zero && s == 0);
+            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+          }
+        }
+        if (!jac)
+          kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0);
+        else
+          kb_residual<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, loc);
+        if (!jac)
+          kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+        else
+          kb_restrict<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+      }
+      // every instance's coarsest grid; the result goes where a smoothed level's
+      // iterate would be (t after an odd Jacobi sweep count) so the prolongation
+      // reads one location for all instances
+      kb_coarse<DIM><<<grid, blk, 0, st>>>(I, Ls + list_coarse(b, m), m, jac ? par : 0);
+      for (int l = b->Lmax - 2; l >= 0; --l) {
+        int loc = jac ? ((l == 0 ? loc0 : 0) ^ (nu1 & 1)) : 0;
+        const List* cells = Ls + list_index(b, m, l, LK_CELLS);
+        if (jac)
+          kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, loc, par);
+        else if (nu2 >= 1)  // a red half sweep follows and overwrites the red points
+          kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+        else
+          kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+        for (int s = 0; s < nu2; ++s) {
+          if (jac) {
+            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, float(b->opt.omega),
+                                                 loc, 0);
+            loc ^= 1;
+          } else {
+            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, 0);
+            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+          }
+        }
+      }
+      if (jac) loc0 ^= par;
+    }
+    kb_update<DIM><<<grid, blk, 0, st>>>(I, full0, m, loc0);
+  }
+  kb_sweep_end<DIM><<<grid, blk, 0, st>>>(I, Ls + list_sweep(b), reaction, b->d_rbits);
+  cudaMemcpyAsync(b->h_rbits, b->d_rbits, sizeof(unsigned long long) * kMaxInst, cudaMemcpyDeviceToHost, st);
+}
+
+isdc_status capture(isdc_batch* b, int shape) {
+  if (b->exec[shape]) return ISDC_OK;
+  cudaGraph_t g = nullptr;
+  B_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  if (b->dim == 2) record_tick<2>(b, kShapes[shape]); else record_tick<3>(b, kShapes[shape]);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec[shape], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return ISDC_OK;
+}
+
+void fill_instance(isdc_batch* b, int slot, int n, double nu, int M, double dt, unsigned char* mem) {
+  Inst& I = b->h_insts[slot];
+  std::memset(&I, 0, sizeof I);
+  const int dim = b->dim;
+  const size_t N = pts(dim, n);
+  const double h = 1.0 / (n + 1);
+  I.n = n;
+  I.M = M;
+  I.nlev = levels_of(n);
+  I.nu_h2 = nu / (h * h);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = mem + off;
+    off += align256(bytes);
+    return p;
+  };
+  I.U = static_cast<double*>(take(size_t(M) * N * 8));
+  I.F = static_cast<double*>(take(size_t(M) * N * 8));
+  I.C = static_cast<double*>(take(size_t(M - 1) * N * 8));
+  I.beta = static_cast<double*>(take(N * 8));
+  const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
+  int side = n;
+  for (int l = 0; l < I.nlev; ++l) {
+    const size_t bytes = pts(dim, side) * 4;
+    I.lev[l].n = side;
+    I.lev[l].x = static_cast<float*>(take(bytes));
+    I.lev[l].b = static_cast<float*>(take(bytes));
+    I.lev[l].r = static_cast<float*>(take(bytes));
+    I.lev[l].t = jac ? static_cast<float*>(take(bytes)) : nullptr;
+    side = (side - 1) / 2;
+  }
+  I.ainv = static_cast<float*>(take(size_t(M - 1) * (dim == 2 ? 81 : 729) * 4));
+  double tau[kMaxM], Q[kMaxM * kMaxM];
+  host::lobatto_nodes(M, tau);
+  host::q_matrix(M, tau, Q);
+  for (int m = 0; m < M; ++m)
+    for (int j = 0; j < M; ++j) I.dtQ[m][j] = dt * Q[m * M + j];
+  for (int m = 0; m < M - 1; ++m) {
+    I.dtm[m] = dt * (tau[m + 1] - tau[m]);
+    const double a = I.dtm[m] * nu;
+    int s = n;
+    for (int l = 0; l < I.nlev; ++l) {
+      const double hl = 1.0 / (s + 1), c = a / (hl * hl), d = 1.0 + 2.0 * dim * c;
+      I.kappa[m][l] = float(c / d);
+      if (l == 0) {
+        I.kappa0[m] = c / d;
+        I.inv_d0[m] = 1.0 / d;
+      }
+      if (l + 1 < I.nlev) {
+        const int sc = (s - 1) / 2;
+        const double hc = 1.0 / (sc + 1), cc = a / (hc * hc), dc = 1.0 + 2.0 * dim * cc;
+        I.wscale[m][l] = float(d / (dc * (dim == 2 ? 16.0 : 64.0)));
+      }
+      s = (s - 1) / 2;
+    }
+  }
+}
+
+}  // namespace
+
+ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, size_t hbm_budget_bytes,
+                                       int n_vcycles, const isdc_options* opt, isdc_batch** out) {
+  if (!out) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "ndim must be 2 or 3");
+  if (max_side < 7 || ((max_side + 1) & max_side) != 0 || (ndim == 3 && max_side > 1289) || max_side > 46339)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_side must be 2^j - 1 >= 7 (got %lld)", (long long)max_side);
+  if (max_M < 2 || max_M > kMaxM) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_M must be in [2, %d]", kMaxM);
+  if (n_vcycles < 1 || n_vcycles > 16) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "n_vcycles must be in [1, 16]");
+  isdc_options o;
+  if (opt) o = *opt; else isdc_default_options(&o);
+  if (o.smoother != ISDC_SMOOTHER_JACOBI && o.smoother != ISDC_SMOOTHER_RBGS)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "unknown smoother");
+  if (o.nu1 < 1 || o.nu2 < 0 || o.nu1 > 8 || o.nu2 > 8)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "the batch engine needs 1 <= nu1 <= 8 and 0 <= nu2 <= 8");
+  if (o.max_sweeps < 1) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps must be >= 1");
+  isdc_batch* b = new isdc_batch();
+  b->dim = ndim;
+  b->L = n_vcycles;
+  b->Mmax = max_M;
+  b->max_side = int(max_side);
+  b->Lmax = levels_of(int(max_side));
+  b->opt = o;
+  b->opt.vcycle_fp32 = 1;
+  b->budget = hbm_budget_bytes;
+  b->nlists = (max_M - 1) * b->Lmax * 4 + (max_M - 1) + 2;
+  auto bail = [&](isdc_status st) {
+    snprintf(g_batch_error, sizeof g_batch_error, "%s", b->err);
+    isdc_batch_destroy(b);
+    return st;
+  };
+#define CB(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      bfail(b, e_ == cudaErrorMemoryAllocation ? ISDC_ERR_OOM : ISDC_ERR_CUDA, "%s: %s", #call, \
+            cudaGetErrorString(e_));                                                    \
+      return bail(e_ == cudaErrorMemoryAllocation ? ISDC_ERR_OOM : ISDC_ERR_CUDA);      \
+    }                                                                                   \
+  } while (0)
+  int dev = 0;
+  CB(cudaGetDevice(&dev));
+  CB(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+  if (o.stream) {
+    b->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    CB(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  CB(cudaMalloc(&b->d_insts, sizeof(Inst) * kMaxInst));
+  CB(cudaMemset(b->d_insts, 0, sizeof(Inst) * kMaxInst));
+  CB(cudaMallocHost(&b->h_insts, sizeof(Inst) * kMaxInst));
+  CB(cudaMalloc(&b->d_lists, sizeof(List) * b->nlists));
+  CB(cudaMallocHost(&b->h_lists, sizeof(List) * b->nlists));
+  std::memset(b->h_lists, 0, sizeof(List) * b->nlists);
+  CB(cudaMemset(b->d_lists, 0, sizeof(List) * b->nlists));
+  CB(cudaMalloc(&b->d_rbits, sizeof(unsigned long long) * kMaxInst));
+  CB(cudaMalloc(&b->d_dummy, sizeof(unsigned long long) * kMaxInst));
+  CB(cudaMallocHost(&b->h_rbits, sizeof(unsigned long long) * kMaxInst));
+  CB(cudaEventCreate(&b->ev0));
+  CB(cudaEventCreate(&b->ev1));
+#undef CB
+  *out = b;
+  return ISDC_OK;
+}
+
+ISDC_API void isdc_batch_destroy(isdc_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int i = 0; i < kMaxInst; ++i)
+    if (b->slots[i].mem) cudaFreeAsync(b->slots[i].mem, b->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int s = 0; s < kNumShapes; ++s)
+    if (b->exec[s]) cudaGraphExecDestroy(b->exec[s]);
+  cudaFree(b->d_insts);
+  cudaFreeHost(b->h_insts);
+  cudaFree(b->d_lists);
+  cudaFreeHost(b->h_lists);
+  cudaFree(b->d_rbits);
+  cudaFree(b->d_dummy);
+  cudaFreeHost(b->h_rbits);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+ISDC_API isdc_status isdc_batch_admit(isdc_batch* b, const isdc_problem* p, const double* u0, int u0_on_host,
+                                      int* slot_out) {
+  if (!b || !p || !u0 || !slot_out) return ISDC_ERR_INVALID_ARG;
+  *slot_out = -1;
+  const int64_t n = p->n;
+  if (n < 7 || n > b->max_side || ((n + 1) & n) != 0)
+    return bfail(b, ISDC_ERR_INVALID_ARG, "side must be 2^j - 1 in [7, %d] (got %lld)", b->max_side, (long long)n);
+  if (p->M < 2 || p->M > b->Mmax) return bfail(b, ISDC_ERR_INVALID_ARG, "M must be in [2, %d]", b->Mmax);
+  if (!(p->nu > 0) || !(p->dt > 0) || !std::isfinite(p->nu) || !std::isfinite(p->dt) || p->steps < 1)
+    return bfail(b, ISDC_ERR_INVALID_ARG, "need nu > 0, dt > 0, steps >= 1");
+  int slot = -1;
+  for (int i = 0; i < kMaxInst; ++i)
+    if (b->slots[i].state == ISDC_SLOT_FREE) { slot = i; break; }
+  if (slot < 0) return bfail(b, ISDC_ERR_OOM, "all %d slots are in use", kMaxInst);
+  const size_t bytes = instance_bytes(b, int(n), p->M);
+  if (b->used + bytes > b->budget)
+    return bfail(b, ISDC_ERR_OOM, "instance needs %zu bytes; %zu of %zu budget bytes in use", bytes, b->used,
+                 b->budget);
+  void* mem = nullptr;
+  B_TRY(b, cudaMallocAsync(&mem, bytes, b->stream));
+  fill_instance(b, slot, int(n), p->nu, p->M, p->dt, static_cast<unsigned char*>(mem));
+  Inst& I = b->h_insts[slot];
+  const size_t N = pts(b->dim, int(n));
+  // initial value goes to the last node: a step's spread starts from u_{M-1}
+  B_TRY(b, cudaMemcpyAsync(I.U + size_t(p->M - 1) * N, u0, N * 8,
+                           u0_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->stream));
+  std::vector<float> ainv(size_t(p->M - 1) * (b->dim == 2 ? 81 : 729));
+  for (int m = 0; m < p->M - 1; ++m) {
+    std::vector<double> inv;
+    const double a = I.dtm[m] * p->nu;
+    host::coarse_inverse(b->dim, a, inv);
+    const double d3 = 1.0 + 2.0 * b->dim * a * 16.0;
+    for (size_t q = 0; q < inv.size(); ++q) ainv[m * inv.size() + q] = float(d3 * inv[q]);
+  }
+  B_TRY(b, cudaMemcpyAsync(I.ainv, ainv.data(), ainv.size() * 4, cudaMemcpyHostToDevice, b->stream));
+  B_TRY(b, cudaMemcpyAsync(b->d_insts + slot, &b->h_insts[slot], sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
+  B_TRY(b, cudaStreamSynchronize(b->stream));  // the host staging (ainv, pinned descriptor) is reused
+  Slot& S = b->slots[slot];
+  S = Slot();
+  S.state = ISDC_SLOT_RUNNING;
+  S.n = int(n);
+  S.M = p->M;
+  S.nlev = levels_of(int(n));
+  S.steps = p->steps;
+  S.spread_next = true;
+  S.bytes = bytes;
+  S.mem = mem;
+  b->used += bytes;
+  *slot_out = slot;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_batch_tick(isdc_batch* b, int* running_out, int* finished_out) {
+  if (!b) return ISDC_ERR_INVALID_ARG;
+  int running = 0;
+  double dofs = 0.0;
+  for (int i = 0; i < kMaxInst; ++i)
+    if (b->slots[i].state == ISDC_SLOT_RUNNING) {
+      ++running;
+      dofs += double(pts(b->dim, b->slots[i].n));
+    }
+  int finished = 0;
+  if (running) {
+    const int shape = b->tuned ? b->shape : b->tune_next;
+    isdc_status st = capture(b, shape);
+    if (st != ISDC_OK) return st;
+    build_lists(b, kShapes[shape].threads);
+    B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice, b->stream));
+    B_TRY(b, cudaEventRecord(b->ev0, b->stream));
+    B_TRY(b, cudaGraphLaunch(b->exec[shape], b->stream));
+    B_TRY(b, cudaEventRecord(b->ev1, b->stream));
+    B_TRY(b, cudaStreamSynchronize(b->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    if (!b->tuned) {  // autotuner: one real tick per launch shape, keep the fastest
+      b->tune_rate[shape] = dofs / std::max(ms, 1e-3f);
+      if (++b->tune_next == kNumShapes) {
+        int best = 0;
+        for (int s = 1; s < kNumShapes; ++s)
+          if (b->tune_rate[s] > b->tune_rate[best]) best = s;
+        b->shape = best;
+        b->tuned = 1;
+      }
+    }
+    ++b->ticks;
+    for (int i = 0; i < kMaxInst; ++i) {
+      Slot& S = b->slots[i];
+      if (S.state != ISDC_SLOT_RUNNING) continue;
+      double R;
+      std::memcpy(&R, &b->h_rbits[i], sizeof R);
+      S.spread_next = false;
+      S.sweeps += 1;
+      S.total_sweeps += 1;
+      S.last_res = R;
+      if (!std::isfinite(R)) {
+        S.state = ISDC_SLOT_FAILED;
+        ++finished;
+        continue;
+      }
+      const bool conv = R < b->opt.tol;
+      if (conv || S.sweeps >= b->opt.max_sweeps) {
+        if (!conv) ++S.nonconverged;
+        S.steps_done += 1;
+        S.sweeps = 0;
+        if (S.steps_done >= S.steps) {
+          S.state = ISDC_SLOT_FINISHED;
+          ++finished;
+        } else {
+          S.spread_next = true;
+        }
+      }
+    }
+  }
+  if (running_out) {
+    int r = 0;
+    for (int i = 0; i < kMaxInst; ++i) r += b->slots[i].state == ISDC_SLOT_RUNNING;
+    *running_out = r;
+  }
+  if (finished_out) *finished_out = finished;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_batch_query(const isdc_batch* b, int slot, isdc_slot_info* info) {
+  if (!b || !info || slot < 0 || slot >= kMaxInst) return ISDC_ERR_INVALID_ARG;
+  const Slot& S = b->slots[slot];
+  info->state = S.state;
+  info->steps_done = S.steps_done;
+  info->sweeps_in_step = S.sweeps;
+  info->total_sweeps = S.total_sweeps;
+  info->nonconverged_steps = S.nonconverged;
+  info->last_residual = S.last_res;
+  info->device_bytes = S.bytes;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_batch_take(isdc_batch* b, int slot, double* u_out, int out_on_host) {
+  if (!b || slot < 0 || slot >= kMaxInst) return ISDC_ERR_INVALID_ARG;
+  Slot& S = b->slots[slot];
+  if (S.state == ISDC_SLOT_FREE) return bfail(b, ISDC_ERR_INVALID_ARG, "slot %d is free", slot);
+  if (S.state == ISDC_SLOT_RUNNING && u_out)
+    return bfail(b, ISDC_ERR_INVALID_ARG, "slot %d is still running", slot);
+  if (u_out) {
+    const Inst& I = b->h_insts[slot];
+    const size_t N = pts(b->dim, S.n);
+    B_TRY(b, cudaMemcpyAsync(u_out, I.U + size_t(S.M - 1) * N, N * 8,
+                             out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->stream));
+  }
+  B_TRY(b, cudaFreeAsync(S.mem, b->stream));
+  B_TRY(b, cudaStreamSynchronize(b->stream));
+  b->used -= S.bytes;
+  S = Slot();
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info) {
+  if (!b || !info) return ISDC_ERR_INVALID_ARG;
+  info->ticks = b->ticks;
+  info->bytes_in_use = b->used;
+  info->tuned = b->tuned;
+  info->threads_per_block = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].threads;
+  info->blocks_per_sm = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].blocks_per_sm;
+  int r = 0;
+  for (int i = 0; i < kMaxInst; ++i) r += b->slots[i].state == ISDC_SLOT_RUNNING;
+  info->running = r;
+  return ISDC_OK;
+}
+
+ISDC_API const char* isdc_batch_last_error(const isdc_batch* b) { return b ? b->err : g_batch_error; }

@@ -18,123 +18,17 @@
 #include <vector>
 
 #include "../../include/isdc.h"
+#include "host_util.h"
 #include "kernels.cuh"
 
 #define ISDC_API extern "C" __attribute__((visibility("default")))
 
 using namespace isdc;
+using namespace isdc::host;
 
 namespace {
 
 thread_local char g_create_error[512] = "";
-
-// ---------------------------------------------------------------------------
-// Collocation tables (Sec. 2, Eq. 2).
-// ---------------------------------------------------------------------------
-
-// Number of eigenvalues below x of the symmetric tridiagonal matrix with zero
-// diagonal and squared off-diagonals beta (Sturm sequence count).
-int sturm_count(const std::vector<double>& beta, int size, double x) {
-  int count = 0;
-  double q = -x;  // leading principal minor ratio
-  if (q < 0) ++count;
-  for (int k = 1; k < size; ++k) {
-    const double prev = (q == 0.0) ? 1e-300 : q;
-    q = -x - beta[k - 1] / prev;
-    if (q < 0) ++count;
-  }
-  return count;
-}
-
-// Gauss-Lobatto nodes on [0,1].  The interior nodes are the roots of
-// P'_{M-1}, i.e. of the Jacobi polynomial P^{(1,1)}_{M-2}: eigenvalues of its
-// Jacobi matrix (zero diagonal, squared off-diagonals k(k+2)/((2k+1)(2k+3))),
-// found by bisection on the Sturm count (Golub-Welsch).
-void lobatto_nodes(int M, double* tau) {
-  const int size = M - 2;
-  std::vector<double> beta(std::max(size, 1));
-  for (int k = 1; k < size; ++k) beta[k - 1] = double(k) * (k + 2) / ((2.0 * k + 1) * (2.0 * k + 3));
-  tau[0] = 0.0;
-  tau[M - 1] = 1.0;
-  for (int e = 0; e < size; ++e) {  // e-th smallest eigenvalue
-    double lo = -1.0, hi = 1.0;
-    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid == lo || mid == hi) break;
-      if (sturm_count(beta, size, mid) > e) hi = mid; else lo = mid;
-    }
-    tau[e + 1] = 0.5 * (0.5 * (lo + hi) + 1.0);
-  }
-}
-
-// Q[m][j] = int_0^{tau_m} l_j(s) ds, computed exactly: l_j expanded in powers
-// of x = 2s - 1 in [-1,1] and integrated term by term.
-void q_matrix(int M, const double* tau, double* Q) {
-  std::vector<double> x(M);
-  for (int i = 0; i < M; ++i) x[i] = 2.0 * tau[i] - 1.0;
-  for (int j = 0; j < M; ++j) {
-    std::vector<double> c(1, 1.0);  // coefficients, ascending powers
-    double denom = 1.0;
-    for (int i = 0; i < M; ++i) {
-      if (i == j) continue;
-      std::vector<double> nc(c.size() + 1, 0.0);
-      for (size_t k = 0; k < c.size(); ++k) {
-        nc[k + 1] += c[k];
-        nc[k] -= x[i] * c[k];
-      }
-      c.swap(nc);
-      denom *= (x[j] - x[i]);
-    }
-    auto antider = [&](double t) {
-      double acc = 0.0, pw = t;
-      for (size_t k = 0; k < c.size(); ++k) {
-        acc += c[k] * pw / double(k + 1);
-        pw *= t;
-      }
-      return acc;
-    };
-    const double base = antider(-1.0);
-    for (int m = 0; m < M; ++m) Q[m * M + j] = 0.5 * (antider(x[m]) - base) / denom;
-  }
-}
-
-// Inverse of the dense matrix of H = I - a L_h on a side-3 grid (Gauss-Jordan
-// with partial pivoting), row-major, Np x Np.
-void coarse_inverse(int dim, double a, std::vector<double>& inv) {
-  const int n = 3, Np = dim == 2 ? 9 : 27;
-  const double h = 1.0 / (n + 1), c = a / (h * h), d = 1.0 + 2.0 * dim * c;
-  std::vector<double> A(Np * Np, 0.0);
-  for (int p = 0; p < Np; ++p) {
-    const int i = p % n, j = (p / n) % n, k = dim == 3 ? p / (n * n) : 0;
-    A[p * Np + p] = d;
-    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
-    for (int q = 0; q < 2 * dim; ++q) {
-      const int ii = nb[q][0], jj = nb[q][1], kk = nb[q][2];
-      if (ii < 0 || ii >= n || jj < 0 || jj >= n || kk < 0 || kk >= (dim == 3 ? n : 1)) continue;
-      A[p * Np + (ii + n * (jj + n * kk))] = -c;
-    }
-  }
-  inv.assign(Np * Np, 0.0);
-  for (int p = 0; p < Np; ++p) inv[p * Np + p] = 1.0;
-  for (int col = 0; col < Np; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < Np; ++r)
-      if (std::fabs(A[r * Np + col]) > std::fabs(A[piv * Np + col])) piv = r;
-    if (piv != col)
-      for (int q = 0; q < Np; ++q) {
-        std::swap(A[col * Np + q], A[piv * Np + q]);
-        std::swap(inv[col * Np + q], inv[piv * Np + q]);
-      }
-    const double s = 1.0 / A[col * Np + col];
-    for (int q = 0; q < Np; ++q) { A[col * Np + q] *= s; inv[col * Np + q] *= s; }
-    for (int r = 0; r < Np; ++r) {
-      if (r == col) continue;
-      const double f = A[r * Np + col];
-      if (f == 0.0) continue;
-      for (int q = 0; q < Np; ++q) { A[r * Np + q] -= f * A[col * Np + q]; inv[r * Np + q] -= f * inv[col * Np + q]; }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Multigrid hierarchy in one precision.

@@ -46,6 +46,25 @@ class isdc_kernel_stat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("fp64_ops", ctypes.c_double), ("fp32_ops", ctypes.c_double)]
 
 
+class isdc_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nu", ctypes.c_double), ("M", ctypes.c_int), ("dt", ctypes.c_double),
+                ("steps", ctypes.c_int)]
+
+
+class isdc_slot_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("steps_done", ctypes.c_int), ("sweeps_in_step", ctypes.c_int),
+                ("total_sweeps", ctypes.c_int), ("nonconverged_steps", ctypes.c_int),
+                ("last_residual", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class isdc_batch_info(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t), ("running", ctypes.c_int),
+                ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+
+ISDC_SLOT_FREE, ISDC_SLOT_RUNNING, ISDC_SLOT_FINISHED, ISDC_SLOT_FAILED = 0, 1, 2, 3
+
+
 class IsdcError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -86,6 +105,15 @@ def load(build_if_missing: bool = True):
         "isdc_set_nodes": (I, [_ctx_p, V]),
         "isdc_vcycles": (I, [_ctx_p, D, V, V, I]),
         "isdc_vcycles_static": (I, [I, ctypes.c_int64, D, I, I, I, D, V, V, I, V]),
+        "isdc_batch_create": (I, [I, ctypes.c_int64, I, ctypes.c_size_t, I, ctypes.POINTER(isdc_options),
+                                  ctypes.POINTER(_ctx_p)]),
+        "isdc_batch_admit": (I, [_ctx_p, ctypes.POINTER(isdc_problem), V, I, ctypes.POINTER(I)]),
+        "isdc_batch_tick": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "isdc_batch_query": (I, [_ctx_p, I, ctypes.POINTER(isdc_slot_info)]),
+        "isdc_batch_take": (I, [_ctx_p, I, V, I]),
+        "isdc_batch_stats": (I, [_ctx_p, ctypes.POINTER(isdc_batch_info)]),
+        "isdc_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
+        "isdc_batch_destroy": (None, [_ctx_p]),
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
         "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
@@ -254,6 +282,120 @@ def isdc_last_error(ctx=None) -> str:
 def isdc_destroy(ctx):
     if ctx:
         load().isdc_destroy(ctx)
+
+
+# --- batched engine -----------------------------------------------------------------
+def _bcheck(st, b=None, soft=()):
+    if st != ISDC_OK and st not in soft:
+        raise IsdcError(st, load().isdc_batch_last_error(b).decode(errors="replace"))
+    return st
+
+
+def isdc_batch_create(ndim, max_side, max_M, hbm_budget_bytes, n_vcycles, options: isdc_options | None = None):
+    out = _ctx_p()
+    _bcheck(load().isdc_batch_create(ndim, max_side, max_M, hbm_budget_bytes, n_vcycles,
+                                     ctypes.byref(options) if options is not None else None, ctypes.byref(out)))
+    return out
+
+
+def isdc_batch_admit(b, n, nu, M, dt, steps, u0):
+    """u0: numpy float64 array (host) or float64 CUDA tensor (device).  Returns
+    the slot, or None when the budget or the slots are exhausted (soft)."""
+    import numpy as np
+    p = isdc_problem(n, nu, M, dt, steps)
+    if isinstance(u0, np.ndarray):
+        if u0.dtype != np.float64 or not u0.flags.c_contiguous:
+            raise TypeError("expected a contiguous float64 array")
+        ptr, host = ctypes.c_void_p(u0.ctypes.data), 1
+    else:
+        ptr, host = _dev_ptr(u0), 0
+    slot = ctypes.c_int(-1)
+    st = _bcheck(load().isdc_batch_admit(b, ctypes.byref(p), ptr, host, ctypes.byref(slot)), b,
+                 soft=(ISDC_ERR_OOM,))
+    return None if st == ISDC_ERR_OOM else slot.value
+
+
+def isdc_batch_tick(b):
+    r, f = ctypes.c_int(), ctypes.c_int()
+    _bcheck(load().isdc_batch_tick(b, ctypes.byref(r), ctypes.byref(f)), b)
+    return r.value, f.value
+
+
+def isdc_batch_query(b, slot):
+    info = isdc_slot_info()
+    _bcheck(load().isdc_batch_query(b, slot, ctypes.byref(info)), b)
+    return info
+
+
+def isdc_batch_take(b, slot, out=None):
+    """Copy the finished solution into `out` (numpy float64 array or float64 CUDA
+    tensor; None discards it) and free the slot."""
+    import numpy as np
+    if out is None:
+        ptr, host = None, 0
+    elif isinstance(out, np.ndarray):
+        ptr, host = ctypes.c_void_p(out.ctypes.data), 1
+    else:
+        ptr, host = _dev_ptr(out), 0
+    _bcheck(load().isdc_batch_take(b, slot, ptr, host), b)
+
+
+def isdc_batch_stats(b):
+    info = isdc_batch_info()
+    _bcheck(load().isdc_batch_stats(b, ctypes.byref(info)), b)
+    return info
+
+
+def isdc_batch_destroy(b):
+    if b:
+        load().isdc_batch_destroy(b)
+
+
+class Batch:
+    """An engine for many independent ISDC integrations of one dimension."""
+
+    def __init__(self, ndim, max_side, max_M=5, hbm_budget_bytes=64 << 30, n_vcycles=2, *,
+                 smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, omega=2.0 / 3.0, reaction=ISDC_REACTION_ALLEN_CAHN,
+                 tol=1e-10, max_sweeps=100):
+        o = isdc_default_options()
+        o.smoother, o.nu1, o.nu2, o.omega, o.reaction = smoother, nu1, nu2, omega, reaction
+        o.tol, o.max_sweeps, o.vcycle_fp32 = tol, max_sweeps, 1
+        self.ndim = ndim
+        self.b = isdc_batch_create(ndim, max_side, max_M, hbm_budget_bytes, n_vcycles, o)
+        self.sides = {}
+
+    def admit(self, n, nu, M, dt, steps, u0):
+        slot = isdc_batch_admit(self.b, n, nu, M, dt, steps, u0)
+        if slot is not None:
+            self.sides[slot] = n
+        return slot
+
+    def tick(self):
+        return isdc_batch_tick(self.b)
+
+    def query(self, slot):
+        return isdc_batch_query(self.b, slot)
+
+    def take(self, slot):
+        import numpy as np
+        out = np.empty((self.sides[slot],) * self.ndim)
+        isdc_batch_take(self.b, slot, out)
+        del self.sides[slot]
+        return out
+
+    def stats(self):
+        return isdc_batch_stats(self.b)
+
+    def close(self):
+        if self.b:
+            isdc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --- convenience wrapper ------------------------------------------------------

@@ -1,0 +1,122 @@
+"""Batched engine and continuous-batching server (isdc_batch_*): results
+against the FP64 oracle and against the same integration run alone.
+
+Tolerance: the engine runs FP32 V-cycles with FP64 node state, so results are
+compared with the FP64 oracle at relative L2 1e-9 once every step has reached
+SDC residual 1e-10.  Alone vs in the mix the per-point arithmetic is the same
+(the work lists only change which block computes a point), so the results
+must agree exactly."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import rel_l2, torch_cuda
+from isdc_inputs import initial_condition
+
+pytestmark = pytest.mark.gpu
+
+PROBS_2D = [  # n, nu, M, dt, steps
+    (63, 0.3, 3, 0.05, 2),
+    (127, 0.05, 5, 0.02, 2),
+    (31, 1.0, 5, 0.01, 3),
+    (63, 0.01, 3, 0.1, 2),
+]
+PROBS_3D = [
+    (31, 0.1, 5, 0.02, 2),
+    (15, 0.5, 3, 0.05, 2),
+]
+
+
+def _engine(ndim, budget=8 << 30):
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    if ndim == 2:
+        return G.Batch(2, 127, 5, budget, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+    return G.Batch(3, 31, 5, budget, 2, smoother=G.ISDC_SMOOTHER_RBGS, nu1=2, nu2=2, max_sweeps=150)
+
+
+def _run(eng, probs, ndim, seed0):
+    slots = []
+    for q, (n, nu, M, dt, steps) in enumerate(probs):
+        slots.append(eng.admit(n, nu, M, dt, steps, initial_condition(ndim, n, seed0 + q)))
+    assert all(s is not None for s in slots)
+    for _ in range(10000):
+        running, _ = eng.tick()
+        if running == 0:
+            break
+    out = []
+    for s in slots:
+        info = eng.query(s)
+        assert info.state == 2, info.state
+        out.append((eng.take(s), info.total_sweeps))
+    return out
+
+
+@pytest.mark.parametrize("ndim,probs", [(2, PROBS_2D), (3, PROBS_3D)])
+def test_batch_matches_fp64_oracle(ndim, probs):
+    eng = _engine(ndim)
+    got = _run(eng, probs, ndim, 40)
+    for q, (n, nu, M, dt, steps) in enumerate(probs):
+        sm = O.SMOOTHER_JACOBI if ndim == 2 else O.SMOOTHER_RBGS
+        nu1 = 1 if ndim == 2 else 2
+        p = O.Problem(ndim, n, nu, M, dt, smoother=sm, nu1=nu1, nu2=nu1, max_sweeps=150)
+        ref = O.integrate(p, initial_condition(ndim, n, 40 + q), steps, 0, 2)
+        assert all(s == 0 for s in ref.status)
+        assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
+    eng.close()
+
+
+def test_batch_alone_equals_in_the_mix():
+    mix = _engine(2)
+    together = _run(mix, PROBS_2D, 2, 70)
+    mix.close()
+    for q, prob in enumerate(PROBS_2D):
+        alone_eng = _engine(2)
+        alone = _run(alone_eng, [prob], 2, 70 + q)
+        alone_eng.close()
+        np.testing.assert_array_equal(alone[0][0], together[q][0])
+        assert alone[0][1] == together[q][1]
+
+
+def test_batch_budget_admission_is_soft():
+    import paper_1401_7824_gb300 as G
+    eng = _engine(2, budget=1)
+    assert eng.admit(63, 0.1, 3, 0.05, 1, initial_condition(2, 63, 1)) is None
+    eng.close()
+    u = initial_condition(2, 127, 2)
+    probe = _engine(2)
+    one = probe.query(probe.admit(127, 0.1, 5, 0.02, 1, u)).device_bytes
+    probe.close()
+    # room for exactly one 127^2, M = 5 instance: the second waits until the first is taken
+    eng = _engine(2, budget=int(1.5 * one))
+    s1 = eng.admit(127, 0.1, 5, 0.02, 1, u)
+    assert s1 is not None
+    assert eng.admit(127, 0.1, 5, 0.02, 1, u) is None
+    while eng.tick()[0]:
+        pass
+    eng.take(s1)
+    assert eng.admit(127, 0.1, 5, 0.02, 1, u) is not None
+    assert eng.stats().tuned in (0, 1)
+    with pytest.raises(G.IsdcError):
+        eng.admit(255, 0.1, 3, 0.02, 1, initial_condition(2, 255, 3))  # beyond max_side
+    eng.close()
+
+
+def test_server_continuous_batching_same_alone_and_in_mix():
+    from paper_1401_7824_gb300.serve import Request, Server
+    reqs = []
+    specs = [(2, 63, 0.3, 3, 0.05, 2), (3, 15, 0.5, 3, 0.05, 2), (2, 127, 0.05, 5, 0.02, 1),
+             (3, 31, 0.1, 5, 0.02, 1), (2, 31, 1.0, 5, 0.01, 2)]
+    for q, (d, n, nu, M, dt, steps) in enumerate(specs):
+        reqs.append(Request(q, 0.01 * q, d, n, nu, M, dt, steps, initial_condition(d, n, 90 + q)))
+    srv = Server(hbm_budget_bytes=(4 << 30, 4 << 30), max_side=(127, 31))
+    rep = srv.run(reqs, realtime=True)
+    srv.close()
+    s = rep.summary()
+    assert s["completed"] == len(specs) and s["failed"] == 0
+    assert s["p99_s"] >= s["p50_s"] > 0
+    for q, (d, n, nu, M, dt, steps) in enumerate(specs):
+        alone = Server(hbm_budget_bytes=(4 << 30, 4 << 30), max_side=(127, 31))
+        r1 = alone.run([Request(q, 0.0, d, n, nu, M, dt, steps, initial_condition(d, n, 90 + q))])
+        alone.close()
+        np.testing.assert_array_equal(r1.requests[0].result, reqs[q].result)
