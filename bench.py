@@ -200,6 +200,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(times, work, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's times
+    (max over ranks) and the work of all ranks (sum).  No data-path collective:
+    this is the only cross-rank exchange, after the timed region."""
+    if world <= 1:
+        return list(times), list(work)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor(work, dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t], [float(v) for v in w]
+
+
 def config_of(w):
     N = w.n ** w.ndim
     state_bytes = (3 * w.M + 2) * N * 8
@@ -287,15 +302,8 @@ def run_ours(args):
     e2e_t = time.perf_counter() - t0
     barrier()
 
-    if world > 1:
-        t = torch.tensor([elapsed, e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        work = torch.tensor([dof_sweeps, float(N * e2e_sweeps)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(work, op=dist.ReduceOp.SUM)
-        elapsed, e2e_t = float(t[0]), float(t[1])
-        dof_sweeps, e2e_work = float(work[0]), float(work[1])
-    else:
-        e2e_work = float(N * e2e_sweeps)
+    (elapsed, e2e_t), (dof_sweeps, e2e_work) = combine_ranks([elapsed, e2e_t], [dof_sweeps, float(N * e2e_sweeps)],
+                                                             world, "cuda")
 
     value = dof_sweeps / elapsed
     line = {

@@ -76,6 +76,9 @@ typedef struct {
     double mg_tol;        /* classical SDC (n_vcycles == 0): stop the node solve when the
                              max-norm residual of (I - dt_m A)x = b is <= mg_tol (default 1e-12) */
     int    mg_max_cycles; /* cap on V-cycles per node solve in that mode (default 50) */
+    int    vcycle_cap;    /* 0 (default): n_vcycles = L > 0 runs exactly L V-cycles.  1: L is a
+                             cap and a node solve stops early once its max-norm residual is
+                             <= mg_tol (one residual check, and host synchronisation, per cycle) */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream

@@ -56,7 +56,9 @@ typedef struct {
     int    nu1, nu2;    /* pre- and post-smoothing sweeps */
     double omega;       /* Jacobi damping */
     int    solver;      /* 0 ISDC: L V-cycles; 1 classical: MG until mg_tol;
-                           2 classical: exact sine-transform solve */
+                           2 classical: exact sine-transform solve;
+                           3 ISDC with L as a cap: at most L V-cycles, stopping
+                             early once the node residual is <= mg_tol */
     int    guess;       /* multigrid start: 0 u_{m+1}^k (Sec. 4.3), 1 zero,
                            2 u_m^{k+1} */
     double tol;         /* SDC residual tolerance */
@@ -619,6 +621,13 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
                 orc_solve_exact(d, n, a, rhs, x);
             } else if (P->solver == 1) {
                 for (int c = 0; c < P->mg_max_cycles; ++c) {
+                    orc_residual(d, n, a, x, rhs, tmp);
+                    if (max_abs(tmp, N) <= P->mg_tol) break;
+                    vcycle(P, &mg, 0, a, x, rhs);
+                    ++vcycles;
+                }
+            } else if (P->solver == 3) {
+                for (int c = 0; c < n_vcycles; ++c) {
                     orc_residual(d, n, a, x, rhs, tmp);
                     if (max_abs(tmp, N) <= P->mg_tol) break;
                     vcycle(P, &mg, 0, a, x, rhs);

@@ -28,6 +28,7 @@ SMOOTHER_RBGS = 1
 SOLVER_ISDC = 0       # L fixed V-cycles per node solve
 SOLVER_MG_TOL = 1     # classical SDC: V-cycles until the node residual < mg_tol
 SOLVER_EXACT = 2      # classical SDC: exact sine-transform solve
+SOLVER_ISDC_CAPPED = 3  # ISDC with L as a cap: stop a node solve early at mg_tol
 GUESS_PREVIOUS_SWEEP = 0  # u_{m+1}^k, the paper's choice (Sec. 4.3)
 GUESS_ZERO = 1
 GUESS_LEFT_NODE = 2       # u_m^{k+1}

@@ -513,11 +513,12 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
       LAUNCH_CHECK(ctx);
       double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
       const double a = dtm * ctx->nu;
-      if (n_vcycles > 0) {
+      if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
         if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, n_vcycles)) != ISDC_OK) return st;
         vcycles += n_vcycles;
-      } else {  // classical SDC: multigrid to a tolerance (Sec. 3)
-        for (int c = 0; c < ctx->opt.mg_max_cycles; ++c) {
+      } else {  // classical SDC: multigrid to a tolerance (Sec. 3); or L as a cap with that early exit
+        const int limit = n_vcycles > 0 ? n_vcycles : ctx->opt.mg_max_cycles;
+        for (int c = 0; c < limit; ++c) {
           double rn;
           if ((st = node_residual_norm<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
           if (!(rn > ctx->opt.mg_tol)) break;
@@ -572,6 +573,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->max_sweeps = 100;
   opt->mg_tol = 1e-12;
   opt->mg_max_cycles = 50;
+  opt->vcycle_cap = 0;
   opt->stream = nullptr;
   return ISDC_OK;
 }

@@ -1,0 +1,33 @@
+"""V-cycle accounting of classical SDC (node solves to a multigrid tolerance)
+and ISDC (L = 2 V-cycles as a cap) on the heat equation of Sec. 4.1
+(Table 1a setting, 5-point stencil): the CUDA path's sweep and V-cycle counts
+against the oracle's, and the paper's K <= K~ (Sec. 3)."""
+import pytest
+
+import oracle as O
+from gpu_util import make_gpu, to_dev
+from isdc_inputs import sine_mode
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("nu", [1, 10, 100])
+@pytest.mark.parametrize("M", [3, 5, 7])
+def test_sdc_and_isdc_counts_match_oracle(nu, M):
+    from oracle.table1 import heat_problem
+    u0 = sine_mode(2, 63)
+    ps = heat_problem(nu, M, O.SOLVER_MG_TOL)
+    pi = heat_problem(nu, M, O.SOLVER_ISDC_CAPPED)
+    sdc = O.isdc_step(ps, u0, 0, 0)
+    isdc = O.isdc_step(pi, u0, 0, 2)
+    g = make_gpu(ps)
+    u = to_dev(u0)
+    g.step(u, 0, 0)
+    gs = g.stats()
+    gi = make_gpu(pi, vcycle_cap=True)
+    v = to_dev(u0)
+    gi.step(v, 0, 2)
+    gis = gi.stats()
+    assert gs[0] == sdc.sweeps and abs(gs[1] - sdc.vcycles) <= 1
+    assert gis[0] == isdc.sweeps and abs(gis[1] - isdc.vcycles) <= 1
+    assert isdc.sweeps >= sdc.sweeps  # K <= K~
