@@ -85,6 +85,12 @@ struct isdc_ctx {
   double* u_dev = nullptr;  // device copy of u for isdc_step_host
   Hier<double> h64;
   Hier<float> h32;
+  // FP32 red-black mode: the fine level's error, defect and red residual in
+  // the colour-split layout (two colour arrays of hn = (n+1)/2 * n^(dim-1))
+  float* sp_x = nullptr;
+  float* sp_b = nullptr;
+  float* sp_r = nullptr;
+  size_t hn = 0;
   unsigned long long* d_scal = nullptr;  // [0] SDC residual bits, [1] node-residual bits
   unsigned long long* h_scal = nullptr;  // pinned mirror of d_scal
   unsigned long long* h_hist = nullptr;  // pinned residual bits per sweep
@@ -295,16 +301,18 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
   return ISDC_OK;
 }
 
+// V-cycle from level l0 (default the fine level) down and back; x0/b0 are
+// level l0's unknown and scaled right-hand side.
 template <typename T, int DIM>
-isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T* b0, bool zero0) {
+isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T* b0, bool zero0, int l0 = 0) {
   T* xcur[kMaxLevels];
   isdc_status st;
   // downward leg on the levels above the bottom block
-  for (int l = 0; l < H.lb; ++l) {
-    T* home = (l == 0) ? x0 : H.x[l];
+  for (int l = l0; l < H.lb; ++l) {
+    T* home = (l == l0) ? x0 : H.x[l];
     T* x = home;
-    const T* b = (l == 0) ? b0 : H.b[l];
-    bool zero = (l == 0) ? zero0 : true;
+    const T* b = (l == l0) ? b0 : H.b[l];
+    bool zero = (l == l0) ? zero0 : true;
     const int s = H.side[l];
     if (ctx->opt.nu1 == 0 && zero) {
       CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(T), ctx->stream));
@@ -317,7 +325,7 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     const bool red_only = ctx->opt.smoother == ISDC_SMOOTHER_RBGS && ctx->opt.nu1 >= 1;
     {
       const double f = red_only ? 0.5 : 1.0;
-      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * f * Np * sizeof(T),
+      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, (red_only ? 2.0 : 3.0) * Np * sizeof(T),
                    (nb_ops(DIM) + 2.0) * f * Np, sizeof(T) == 8);
       if (red_only)
         k_residual<T, DIM, true><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, T(lf.kappa), x, b, H.r[l]);
@@ -356,9 +364,9 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     P.nu2 = ctx->opt.nu2;
     P.omega = T(ctx->opt.omega);
     P.Ainv = H.Ainv + size_t(slot) * (DIM == 2 ? 81 : 729);
-    const T* bb = H.lb == 0 ? b0 : H.b[H.lb];
-    T* xb = H.lb == 0 ? x0 : H.x[H.lb];
-    const int load_x = (H.lb == 0 && !zero0) ? 1 : 0;
+    const T* bb = H.lb == l0 ? b0 : H.b[H.lb];
+    T* xb = H.lb == l0 ? x0 : H.x[H.lb];
+    const int load_x = (H.lb == l0 && !zero0) ? 1 : 0;
     {
       ProfScope ps(ctx, PC_BOTTOM, (2.0 + load_x) * double(H.npts[H.lb]) * sizeof(T), 0.0, sizeof(T) == 8);
       k_bottom<T, DIM><<<1, kBottomThreads, H.bottom_smem, ctx->stream>>>(P, bb, xb, load_x);
@@ -367,9 +375,9 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     xcur[H.lb] = xb;
   }
   // upward leg
-  for (int l = H.lb - 1; l >= 0; --l) {
+  for (int l = H.lb - 1; l >= l0; --l) {
     const int sc = H.side[l + 1], s = H.side[l];
-    T* home = (l == 0) ? x0 : H.x[l];
+    T* home = (l == l0) ? x0 : H.x[l];
     T* x = xcur[l];
     {
       // a red half sweep follows: it overwrites the red points, so correct the black ones only
@@ -384,12 +392,75 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     }
     LAUNCH_CHECK(ctx);
     bool zero = false;
-    if ((st = smooth_level<T, DIM>(ctx, H, l, a, x, home, l == 0 ? b0 : H.b[l], zero, ctx->opt.nu2)) != ISDC_OK)
+    if ((st = smooth_level<T, DIM>(ctx, H, l, a, x, home, l == l0 ? b0 : H.b[l], zero, ctx->opt.nu2)) != ISDC_OK)
       return st;
     xcur[l] = x;
   }
-  if (xcur[0] != x0)
-    CUDA_TRY(ctx, cudaMemcpyAsync(x0, xcur[0], H.npts[0] * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (xcur[l0] != x0)
+    CUDA_TRY(ctx, cudaMemcpyAsync(x0, xcur[l0], H.npts[l0] * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+  return ISDC_OK;
+}
+
+// FP32 V-cycles with red-black smoothing whose fine level is in the
+// colour-split layout (levels below it are natural): defect, n_cycles
+// V-cycles on the error equation, update.  Needs nu1, nu2 >= 1.
+template <int DIM>
+isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles) {
+  const int s = ctx->n, sc = ctx->h32.side[1];
+  Hier<float>& H = ctx->h32;
+  const size_t hn = ctx->hn;
+  float *x0 = ctx->sp_x, *x1 = ctx->sp_x + hn, *b0 = ctx->sp_b, *b1 = ctx->sp_b + hn;
+  const LevelCoef lf = level_coef(DIM, s, a);
+  const float kappa = float(lf.kappa);
+  const float ws = float(lf.d / (level_coef(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0)));
+  const double Np = double(ctx->N), Nc = double(H.npts[1]);
+  const dim3 g = rb_grid(DIM, s);
+  isdc_status st;
+  {
+    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
+    k_defect_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, lf.kappa, x, beta, b0, b1);
+  }
+  LAUNCH_CHECK(ctx);
+  auto sweep = [&](bool zero) -> isdc_status {
+    {
+      ProfScope ps(ctx, PC_SMOOTH0, (zero ? 1.0 : 1.5) * Np * 4, (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, false);
+      k_rbgs_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, x1, b0, zero ? 1 : 0);
+    }
+    LAUNCH_CHECK(ctx);
+    {
+      ProfScope ps(ctx, PC_SMOOTH0, 1.5 * Np * 4, (nb_ops(DIM) + 1.0) * 0.5 * Np, false);
+      k_rbgs_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, 1, x1, x0, b1, 0);
+    }
+    LAUNCH_CHECK(ctx);
+    return ISDC_OK;
+  };
+  for (int c = 0; c < n_cycles; ++c) {
+    for (int it = 0; it < ctx->opt.nu1; ++it)
+      if ((st = sweep(c == 0 && it == 0)) != ISDC_OK) return st;
+    {
+      ProfScope ps(ctx, PC_RESIDUAL0, 2.0 * Np * 4, (nb_ops(DIM) + 2.0) * 0.5 * Np, false);
+      k_residual_red_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, x0, x1, b0, ctx->sp_r);
+    }
+    LAUNCH_CHECK(ctx);
+    {
+      ProfScope ps(ctx, PC_RESTRICT0, (0.5 * Np + Nc) * 4, (DIM == 2 ? 6.0 : 15.0) * Nc, false);
+      k_restrict_red_split<DIM><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, ctx->sp_r, H.b[1]);
+    }
+    LAUNCH_CHECK(ctx);
+    if ((st = vcycle<float, DIM>(ctx, H, slot, a, H.x[1], H.b[1], true, 1)) != ISDC_OK) return st;
+    {
+      ProfScope ps(ctx, PC_PROLONG0, (Np + Nc) * 4, (DIM == 2 ? 1.25 : 1.75) * Np, false);
+      k_prolong_black_split<DIM><<<pt_grid(DIM, sc + 1), kBlock, 0, ctx->stream>>>(sc, H.x[1], x0, x1);
+    }
+    LAUNCH_CHECK(ctx);
+    for (int it = 0; it < ctx->opt.nu2; ++it)
+      if ((st = sweep(false)) != ISDC_OK) return st;
+  }
+  {
+    ProfScope ps(ctx, PC_UPDATE, 20.0 * Np, 1.0 * Np, true);
+    k_update_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, x, x0, x1);
+  }
+  LAUNCH_CHECK(ctx);
   return ISDC_OK;
 }
 
@@ -407,6 +478,7 @@ isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const doubl
     return ISDC_OK;
   }
   if (n_cycles <= 0) return ISDC_OK;
+  if (ctx->sp_x) return node_solve_split<DIM>(ctx, slot, a, x, beta, n_cycles);
   const int s = ctx->n;
   Hier<float>& H = ctx->h32;
   const double Np = double(ctx->N);
@@ -605,6 +677,9 @@ ISDC_API void isdc_destroy(isdc_ctx* ctx) {
   cudaFree(ctx->u_dev);
   free_hier(ctx->h64, false);
   free_hier(ctx->h32, true);
+  cudaFree(ctx->sp_x);
+  cudaFree(ctx->sp_b);
+  cudaFree(ctx->sp_r);
   cudaFree(ctx->d_scal);
   cudaFreeHost(ctx->h_scal);
   cudaFreeHost(ctx->h_hist);
@@ -700,6 +775,16 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   CREATE_TRY(cudaMallocHost(&ctx->h_hist, size_t(ctx->hist_cap) * sizeof(unsigned long long)));
   if (o.vcycle_fp32) {
     if ((st = alloc_hier(ctx, ctx->h32, true)) != ISDC_OK) return bail(st);
+    if (o.smoother == ISDC_SMOOTHER_RBGS && o.nu1 >= 1 && o.nu2 >= 1 && ctx->h32.lb > 0) {
+      ctx->hn = size_t((n + 1) / 2) * (ndim == 2 ? size_t(n) : size_t(n) * size_t(n));
+      CREATE_TRY(cudaMalloc(&ctx->sp_x, 2 * ctx->hn * sizeof(float)));
+      CREATE_TRY(cudaMalloc(&ctx->sp_b, 2 * ctx->hn * sizeof(float)));
+      CREATE_TRY(cudaMalloc(&ctx->sp_r, ctx->hn * sizeof(float)));
+      // padding slots (past the last point of a row) are never written: keep them zero
+      CREATE_TRY(cudaMemset(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float)));
+      CREATE_TRY(cudaMemset(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float)));
+      CREATE_TRY(cudaMemset(ctx->sp_r, 0, ctx->hn * sizeof(float)));
+    }
     if (ndim == 2) configure_bottom<float, 2>(ctx->h32); else configure_bottom<float, 3>(ctx->h32);
     for (int m = 0; m < M - 1; ++m)
       if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);

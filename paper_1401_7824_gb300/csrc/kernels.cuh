@@ -266,6 +266,171 @@ __global__ void __launch_bounds__(kBX* kBY)
 }
 
 // ---------------------------------------------------------------------------
+// Colour-split layout of the fine level (FP32 V-cycles with red-black
+// smoothing).  Each colour c has its own array with H = (n+1)/2 slots per
+// row: point (i,j,k) of colour c = (i+j+k+DIM) & 1 (0-based, red = 0) sits in
+// slot (i >> 1) + H * (j + n*k) of array c; in row (j,k) colour c starts at
+// i0 = (c + j + k + DIM) & 1.  The x-neighbours of a slot-h point are slots
+// h-1+i0 and h+i0 of the other colour in the same row, its y/z-neighbours
+// slot h of the other colour in rows j+-1 / k+-1, so a colour pass reads only
+// the other colour and its own rhs, all of it coalesced.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ int split_row(int j, int k, int n) {
+  return DIM == 2 ? j : j + n * k;
+}
+
+// Neighbour sum of the colour-c point in slot h of row (j,k) (x index i = 2h + i0)
+// from the other colour's array o; zero outside the interior.
+template <int DIM>
+__device__ __forceinline__ float split_nbsum(const float* __restrict__ o, int h, int i, int i0, int j, int k, int n,
+                                             int H) {
+  const size_t r = size_t(H) * split_row<DIM>(j, k, n);
+  const float* row = o + r;
+  const float sx = (i > 0 ? row[h - 1 + i0] : 0.f) + (i < n - 1 ? row[h + i0] : 0.f);
+  const float sy = (j > 0 ? row[h - H] : 0.f) + (j < n - 1 ? row[h + H] : 0.f);
+  if (DIM == 2) return sx + sy;
+  const size_t hz = size_t(H) * n;
+  const float sz = (k > 0 ? row[h - hz] : 0.f) + (k < n - 1 ? row[h + hz] : 0.f);
+  return (sx + sy) + sz;
+}
+
+// FP64 defect of the node equation into the split FP32 arrays: one thread per
+// slot pair (points 2h and 2h+1 of a row, one of each colour).
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_defect_split(int n, double kappa, const double* __restrict__ x, const double* __restrict__ beta,
+                   float* __restrict__ r0, float* __restrict__ r1) {
+  const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int H = (n + 1) >> 1;
+  if (h >= H || j >= n) return;
+  const int c0 = (j + (DIM == 3 ? k : 0) + DIM) & 1;  // colour of the even point 2h
+  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+  float* even = c0 ? r1 : r0;
+  float* odd = c0 ? r0 : r1;
+  const int i = 2 * h;
+  int p = lin<DIM>(i, j, k, n);
+  even[slot] = float(fma(kappa, nbsum<double, DIM>(x, i, j, k, n, p), beta[p]) - x[p]);
+  if (i + 1 < n) {
+    ++p;
+    odd[slot] = float(fma(kappa, nbsum<double, DIM>(x, i + 1, j, k, n, p), beta[p]) - x[p]);
+  }
+}
+
+// u += e from the split arrays, in FP64.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_update_split(int n, double* __restrict__ x, const float* __restrict__ e0, const float* __restrict__ e1) {
+  const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int H = (n + 1) >> 1;
+  if (h >= H || j >= n) return;
+  const int c0 = (j + (DIM == 3 ? k : 0) + DIM) & 1;
+  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+  const int p = lin<DIM>(2 * h, j, k, n);
+  x[p] += double((c0 ? e1 : e0)[slot]);
+  if (2 * h + 1 < n) x[p + 1] += double((c0 ? e0 : e1)[slot]);
+}
+
+// Red-black half sweep on the split layout: x_c = beta_c + kappa * (sum of the
+// other colour's neighbours); zero_guess: x_c = beta_c.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rbgs_split(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
+                 const float* __restrict__ bc, int zero_guess) {
+  const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int H = (n + 1) >> 1;
+  const int i0 = (colour + j + (DIM == 3 ? k : 0) + DIM) & 1;
+  const int i = 2 * h + i0;
+  if (i >= n || j >= n) return;
+  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+  xc[slot] = zero_guess ? bc[slot] : fmaf(kappa, split_nbsum<DIM>(xo, h, i, i0, j, k, n, H), bc[slot]);
+}
+
+// Scaled residual at the red points after a complete red-black sweep (the
+// black rows are satisfied), stored in a red-only array with the red slots.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_residual_red_split(int n, float kappa, const float* __restrict__ xr, const float* __restrict__ xb,
+                         const float* __restrict__ br, float* __restrict__ rr) {
+  const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int H = (n + 1) >> 1;
+  const int i0 = (j + (DIM == 3 ? k : 0) + DIM) & 1;
+  const int i = 2 * h + i0;
+  if (i >= n || j >= n) return;
+  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+  rr[slot] = fmaf(kappa, split_nbsum<DIM>(xb, h, i, i0, j, k, n, H), br[slot]) - xr[slot];
+}
+
+// Full weighting from the red-only residual (the 13 / 5 red terms of
+// restrict_point<RED_ONLY>) to the natural-layout coarse rhs.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_restrict_red_split(int nc, float wscale, const float* __restrict__ rr, float* __restrict__ bc) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
+  const int n = 2 * nc + 1, H = (n + 1) >> 1;
+  const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
+  auto red = [&](int i, int j, int k) { return rr[size_t(i >> 1) + size_t(H) * split_row<DIM>(j, k, n)]; };
+  float acc;
+  if (DIM == 2) {
+    acc = fmaf(4.f, red(fi, fj, 0), (red(fi - 1, fj - 1, 0) + red(fi + 1, fj - 1, 0)) +
+                                        (red(fi - 1, fj + 1, 0) + red(fi + 1, fj + 1, 0))) * wscale;
+  } else {
+    const float e_xy = (red(fi - 1, fj - 1, fk) + red(fi + 1, fj - 1, fk)) + (red(fi - 1, fj + 1, fk) + red(fi + 1, fj + 1, fk));
+    const float e_xz = (red(fi - 1, fj, fk - 1) + red(fi + 1, fj, fk - 1)) + (red(fi - 1, fj, fk + 1) + red(fi + 1, fj, fk + 1));
+    const float e_yz = (red(fi, fj - 1, fk - 1) + red(fi, fj + 1, fk - 1)) + (red(fi, fj - 1, fk + 1) + red(fi, fj + 1, fk + 1));
+    acc = fmaf(2.f, (e_xy + e_xz) + e_yz, 8.f * red(fi, fj, fk)) * wscale;
+  }
+  bc[lin<DIM>(I, J, K, nc)] = acc;
+}
+
+// Prolongation of the natural-layout coarse error onto the black points of the
+// split fine level (a red half sweep follows and overwrites the red ones).
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_prolong_black_split(int nc, const float* __restrict__ ec, float* __restrict__ x0, float* __restrict__ x1) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I > nc || J > nc) return;
+  const int n = 2 * nc + 1, H = (n + 1) >> 1;
+  const bool hi_i = I > 0, ok_i = I < nc, hi_j = J > 0, ok_j = J < nc;
+  const int fi = 2 * I, fj = 2 * J;
+  // the black fine point at (fi + ex, fj + ey, fk + ez) sits in slot I of its row
+  auto add = [&](int ex, int ey, int ez, float v) {
+    const int j = fj + ey, k = DIM == 3 ? 2 * K + ez : 0;
+    const int c = (fi + ex + j + k + DIM) & 1;
+    float* a = c ? x1 : x0;
+    a[size_t(I) + size_t(H) * split_row<DIM>(j, k, n)] += v;
+  };
+  if (DIM == 2) {
+    const float c01 = (ok_i && hi_j) ? ec[I + nc * (J - 1)] : 0.f;
+    const float c10 = (hi_i && ok_j) ? ec[(I - 1) + nc * J] : 0.f;
+    const float c11 = (ok_i && ok_j) ? ec[I + nc * J] : 0.f;
+    if (ok_i) add(1, 0, 0, 0.5f * (c01 + c11));
+    if (ok_j) add(0, 1, 0, 0.5f * (c10 + c11));
+  } else {
+    const bool hi_k = K > 0, ok_k = K < nc;
+    auto cv = [&](bool ok, int i, int j, int k) { return ok ? ec[i + nc * (j + nc * k)] : 0.f; };
+    const float c000 = cv(hi_i && hi_j && hi_k, I - 1, J - 1, K - 1), c001 = cv(ok_i && hi_j && hi_k, I, J - 1, K - 1);
+    const float c010 = cv(hi_i && ok_j && hi_k, I - 1, J, K - 1), c011 = cv(ok_i && ok_j && hi_k, I, J, K - 1);
+    const float c100 = cv(hi_i && hi_j && ok_k, I - 1, J - 1, K), c101 = cv(ok_i && hi_j && ok_k, I, J - 1, K);
+    const float c110 = cv(hi_i && ok_j && ok_k, I - 1, J, K), c111 = cv(ok_i && ok_j && ok_k, I, J, K);
+    const float sx00 = c000 + c001, sx01 = c010 + c011, sx10 = c100 + c101, sx11 = c110 + c111;
+    const float sy1 = c101 + c111, sz = c011 + c111;
+    // black points of the cell: ex+ey+ez even
+    add(0, 0, 0, 0.125f * ((sx00 + sx01) + (sx10 + sx11)));
+    if (ok_i && ok_j) add(1, 1, 0, 0.5f * sz);
+    if (ok_i && ok_k) add(1, 0, 1, 0.5f * sy1);
+    if (ok_j && ok_k) add(0, 1, 1, 0.5f * sx11);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // SDC kernels (FP64).
 // ---------------------------------------------------------------------------
 constexpr int kMaxM = 7;
