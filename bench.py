@@ -269,7 +269,8 @@ def run_ours(args):
         gpu_id = None
     clocks = ClockSampler(gpu_id)
     clocks.start()
-    g.profile(True, classes=[dominant])
+    if not args.no_profile:
+        g.profile(True, classes=[dominant])
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -284,7 +285,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    prof = g.profile_read()
+    prof = g.profile_read() if not args.no_profile else full_prof
     g.profile(False)
     elapsed = e0.elapsed_time(e1) / 1e3
     residual = g.residual()
@@ -447,6 +448,9 @@ def main():
     ap.add_argument("--workload", default="3d_n255_M5_fp64",
                     choices=sorted(workloads()) + ["batch_2d_256", "serve_poisson"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="no per-launch events in the timed region (sweeps replay CUDA graphs); the roofline then "
+                         "comes from the untimed fully profiled step")
     ap.add_argument("--compare-fp64", type=int, default=0, help="batch: also time N instances on the FP64 path")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")

@@ -79,6 +79,10 @@ typedef struct {
     int    vcycle_cap;    /* 0 (default): n_vcycles = L > 0 runs exactly L V-cycles.  1: L is a
                              cap and a node solve stops early once its max-norm residual is
                              <= mg_tol (one residual check, and host synchronisation, per cycle) */
+    int    use_graphs;    /* 1 (default): a sweep with a fixed V-cycle count is captured once as a
+                             CUDA graph and replayed (same kernels, same order); 0: launch one by
+                             one.  With the profiler on, the graph carries its event nodes and the
+                             stream is synchronised after every replay to read them. */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream

@@ -65,6 +65,14 @@ struct Profiler {
   size_t used = 0;
   double ms[PC_COUNT] = {}, bytes[PC_COUNT] = {}, dp_ops[PC_COUNT] = {}, sp_ops[PC_COUNT] = {};
   long long launches[PC_COUNT] = {};
+  // While a sweep graph is captured, events go to gpool (they become event
+  // nodes of the graph and are re-recorded on every replay) and the counts to
+  // the per-sweep deltas, which are added once per replay.
+  bool capturing = false;
+  std::vector<Rec> gpool;
+  size_t gused = 0;
+  double d_bytes[PC_COUNT] = {}, d_dp[PC_COUNT] = {}, d_sp[PC_COUNT] = {};
+  long long d_launches[PC_COUNT] = {};
 };
 
 }  // namespace
@@ -101,6 +109,11 @@ struct isdc_ctx {
   int nodes_pending = 0;
   int spare_slot = 0;  // Ainv slot for isdc_vcycles
   Profiler prof;
+  // one SDC sweep (fixed V-cycle count) captured as a CUDA graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t sweep_graph = nullptr;
+  int graph_vcycles = 0;
+  unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
   char err[512] = "";
 };
 
@@ -136,16 +149,34 @@ void prof_flush(isdc_ctx* ctx) {
   for (size_t q = 0; q < P.used; ++q) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, P.pool[q].e0, P.pool[q].e1) == cudaSuccess) P.ms[P.pool[q].cls] += t;
+    else cudaGetLastError();
   }
   P.used = 0;
 }
 
 struct ProfScope {
   isdc_ctx* ctx;
-  int idx = -1;
+  int idx = -1, gidx = -1;
   ProfScope(isdc_ctx* c, int cls, double bytes, double ops, bool fp64) : ctx(c) {
     Profiler& P = ctx->prof;
     if (!P.on) return;
+    if (P.capturing) {
+      P.d_launches[cls] += 1;
+      P.d_bytes[cls] += bytes;
+      (fp64 ? P.d_dp[cls] : P.d_sp[cls]) += ops;
+      if (!(P.event_mask & (1u << cls))) return;
+      if (P.gused == P.gpool.size()) {
+        Profiler::Rec r{};
+        if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+        if (cudaEventCreate(&r.e1) != cudaSuccess) { cudaEventDestroy(r.e0); return; }
+        P.gpool.push_back(r);
+      }
+      gidx = int(P.gused++);
+      P.gpool[gidx].cls = cls;
+      // an external record inside a capture becomes an event-record node
+      cudaEventRecordWithFlags(P.gpool[gidx].e0, ctx->stream, cudaEventRecordExternal);
+      return;
+    }
     P.launches[cls] += 1;
     P.bytes[cls] += bytes;
     (fp64 ? P.dp_ops[cls] : P.sp_ops[cls]) += ops;
@@ -166,8 +197,26 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (idx >= 0) cudaEventRecord(ctx->prof.pool[idx].e1, ctx->stream);
+    if (gidx >= 0) cudaEventRecordWithFlags(ctx->prof.gpool[gidx].e1, ctx->stream, cudaEventRecordExternal);
   }
 };
+
+// After a replay of a profiled sweep graph has completed: add its event times
+// and its per-sweep counts.
+void prof_graph_replayed(isdc_ctx* ctx) {
+  Profiler& P = ctx->prof;
+  for (size_t q = 0; q < P.gused; ++q) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, P.gpool[q].e0, P.gpool[q].e1) == cudaSuccess) P.ms[P.gpool[q].cls] += t;
+    else cudaGetLastError();  // a timing failure must not surface as a later launch error
+  }
+  for (int c = 0; c < PC_COUNT; ++c) {
+    P.launches[c] += P.d_launches[c];
+    P.bytes[c] += P.d_bytes[c];
+    P.dp_ops[c] += P.d_dp[c];
+    P.sp_ops[c] += P.d_sp[c];
+  }
+}
 
 inline double nb_ops(int dim) { return dim == 2 ? 3.0 : 5.0; }
 
@@ -538,6 +587,93 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   return ISDC_OK;
 }
 
+// One SDC sweep (Sec. 2, Eq. 4): the M-1 node solves and the sweep end
+// (f_{M-1}, SDC residual, next C_m).  *vcycles accumulates the V-cycles spent.
+template <int DIM>
+isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
+  const int n = ctx->n, M = ctx->M;
+  const size_t N = ctx->N;
+  const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
+  isdc_status st;
+  for (int m = 0; m < M - 1; ++m) {
+    const double dtm = ctx->tables.dtm[m];
+    const double inv_d0 = 1.0 / level_coef(DIM, n, dtm * ctx->nu).d;
+    {
+      ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
+                   (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
+      k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
+                                                              ctx->U + m * N,
+                                                              ctx->C + m * N, ctx->b,
+                                                              m >= 1 ? ctx->F + m * N : nullptr);
+    }
+    LAUNCH_CHECK(ctx);
+    double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
+    const double a = dtm * ctx->nu;
+    if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
+      if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, n_vcycles)) != ISDC_OK) return st;
+      *vcycles += n_vcycles;
+    } else {  // classical SDC: multigrid to a tolerance (Sec. 3); or L as a cap with that early exit
+      const int limit = n_vcycles > 0 ? n_vcycles : ctx->opt.mg_max_cycles;
+      for (int c = 0; c < limit; ++c) {
+        double rn;
+        if ((st = node_residual_norm<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
+        if (!(rn > ctx->opt.mg_tol)) break;
+        if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, 1)) != ISDC_OK) return st;
+        ++*vcycles;
+      }
+    }
+  }
+  return sweep_end<DIM>(ctx);
+}
+
+// Capture one sweep as a CUDA graph (on a private stream, so that the caller
+// may run on the legacy default stream); the graph also copies the residual
+// bits to the pinned host scalar.
+template <int DIM>
+isdc_status capture_sweep(isdc_ctx* ctx, int n_vcycles) {
+  Profiler& P = ctx->prof;
+  const unsigned mask = P.on ? P.event_mask : 0u;
+  if (ctx->sweep_graph && ctx->graph_vcycles == n_vcycles && ctx->graph_mask == mask && (mask || !P.on)) {
+    return ISDC_OK;
+  }
+  if (ctx->sweep_graph) {
+    cudaGraphExecDestroy(ctx->sweep_graph);
+    ctx->sweep_graph = nullptr;
+  }
+  if (!ctx->cap_stream) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  P.capturing = P.on;
+  P.gused = 0;
+  for (int c = 0; c < PC_COUNT; ++c) {
+    P.d_launches[c] = 0;
+    P.d_bytes[c] = P.d_dp[c] = P.d_sp[c] = 0.0;
+  }
+  long long dummy = 0;
+  isdc_status st = sweep_once<DIM>(ctx, n_vcycles, &dummy);
+  P.capturing = false;
+  if (st == ISDC_OK) {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e != cudaSuccess) st = fail(ctx, ISDC_ERR_CUDA, "capture copy: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->stream = user;
+  if (st != ISDC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(ctx, ISDC_ERR_CUDA, "sweep capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->sweep_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, ISDC_ERR_CUDA, "sweep graph: %s", cudaGetErrorString(e));
+  ctx->graph_vcycles = n_vcycles;
+  ctx->graph_mask = mask;
+  return ISDC_OK;
+}
+
 template <int DIM>
 isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   const int n = ctx->n, M = ctx->M;
@@ -570,38 +706,24 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   int k = 0;
   isdc_status result = ISDC_OK;
   ctx->hist_count = 0;
+  // sweeps with a fixed V-cycle count replay one captured graph (unless the
+  // profiler or a per-sweep history copy needs the launches one by one)
+  const bool graph = ctx->opt.use_graphs && n_vcycles > 0 && !ctx->opt.vcycle_cap &&
+                     (until_tol || !ctx->record_history);
+  if (graph && (st = capture_sweep<DIM>(ctx, n_vcycles)) != ISDC_OK) return st;
   for (;;) {
-    for (int m = 0; m < M - 1; ++m) {
-      const double dtm = ctx->tables.dtm[m];
-      const double inv_d0 = 1.0 / level_coef(DIM, n, dtm * ctx->nu).d;
-      {
-        ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
-                     (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
-        k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
-                                                                ctx->U + m * N,
-                                                                ctx->C + m * N, ctx->b,
-                                                                m >= 1 ? ctx->F + m * N : nullptr);
+    if (graph) {
+      CUDA_TRY(ctx, cudaGraphLaunch(ctx->sweep_graph, ctx->stream));
+      vcycles += (long long)n_vcycles * (M - 1);
+      if (ctx->prof.on) {  // read the replay's event nodes before the next replay re-records them
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        prof_graph_replayed(ctx);
       }
-      LAUNCH_CHECK(ctx);
-      double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
-      const double a = dtm * ctx->nu;
-      if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
-        if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, n_vcycles)) != ISDC_OK) return st;
-        vcycles += n_vcycles;
-      } else {  // classical SDC: multigrid to a tolerance (Sec. 3); or L as a cap with that early exit
-        const int limit = n_vcycles > 0 ? n_vcycles : ctx->opt.mg_max_cycles;
-        for (int c = 0; c < limit; ++c) {
-          double rn;
-          if ((st = node_residual_norm<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
-          if (!(rn > ctx->opt.mg_tol)) break;
-          if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, 1)) != ISDC_OK) return st;
-          ++vcycles;
-        }
-      }
+    } else if ((st = sweep_once<DIM>(ctx, n_vcycles, &vcycles)) != ISDC_OK) {
+      return st;
     }
     ++k;
-    if ((st = sweep_end<DIM>(ctx)) != ISDC_OK) return st;
-    if (until_tol || ctx->record_history) {
+    if (!graph && (until_tol || ctx->record_history)) {
       if (k - 1 < ctx->hist_cap)
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_hist + (k - 1), ctx->d_scal, sizeof(unsigned long long),
                                       cudaMemcpyDeviceToHost, ctx->stream));
@@ -609,6 +731,10 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
     }
     if (until_tol) {
       CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (graph) {
+        if (k - 1 < ctx->hist_cap) ctx->h_hist[k - 1] = ctx->h_scal[0];
+        ctx->hist_count = std::min(k, ctx->hist_cap);
+      }
       const double R = bits_to_double(ctx->h_hist[k - 1]);
       if (!std::isfinite(R)) { result = fail(ctx, ISDC_ERR_NONFINITE, "SDC residual is %g after sweep %d", R, k); break; }
       if (R < ctx->opt.tol) break;
@@ -646,6 +772,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->mg_tol = 1e-12;
   opt->mg_max_cycles = 50;
   opt->vcycle_cap = 0;
+  opt->use_graphs = 1;
   opt->stream = nullptr;
   return ISDC_OK;
 }
@@ -683,6 +810,12 @@ ISDC_API void isdc_destroy(isdc_ctx* ctx) {
   cudaFree(ctx->d_scal);
   cudaFreeHost(ctx->h_scal);
   cudaFreeHost(ctx->h_hist);
+  if (ctx->sweep_graph) cudaGraphExecDestroy(ctx->sweep_graph);
+  for (auto& r : ctx->prof.gpool) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto& r : ctx->prof.pool) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);

@@ -236,3 +236,21 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(G.IsdcError) as e:
         G.isdc_create(3, 31, -1.0, 3, 0.05)
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_sweep_graph_replay_is_bitwise_identical(fp32):
+    """A sweep replayed from its captured CUDA graph runs the same kernels in
+    the same order as launching them one by one."""
+    p = O.Problem(3, 31, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, 31, seed=21)
+    outs = []
+    for graphs in (True, False):
+        g = make_gpu(p, vcycle_fp32=fp32, use_graphs=graphs)
+        u = to_dev(u0)
+        for _ in range(2):
+            g.step(u, 0, 2)
+        outs.append((u.cpu().numpy(), g.stats(), g.history()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    assert outs[0][2] == outs[1][2]
