@@ -319,6 +319,7 @@ def run_ours(args):
         "converged": all(s == 0 for s in statuses),
         "gpu_launches": int(sum(v["launches"] for v in prof.values())),
         "roofline": roofline(prof, dominant, w.name, shares),
+        "autotune": g.tuning(),
         "clocks": clk,
         "e2e": {"value": e2e_work / e2e_t, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": N * 8,
                 "d2h_bytes_per_step": N * 8},

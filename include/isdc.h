@@ -317,6 +317,12 @@ isdc_status isdc_profile_enable(isdc_ctx *ctx, int enable);
  * to out; *count receives the number of such classes. */
 isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int *count);
 
+/* Launch shape chosen by the context's autotuner (not from the paper): z-planes
+ * per thread of the fine-level red-black smoother in FP64 and in FP32 (3D
+ * red-black contexts time 1, 2, 4 and 8 on their own arrays in isdc_create;
+ * otherwise 1). */
+isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32);
+
 /* Message for the last failure of ctx, or of isdc_create when ctx is NULL. */
 const char *isdc_last_error(const isdc_ctx *ctx);
 

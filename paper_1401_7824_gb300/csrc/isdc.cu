@@ -114,6 +114,8 @@ struct isdc_ctx {
   cudaGraphExec_t sweep_graph = nullptr;
   int graph_vcycles = 0;
   unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
+  // z-planes per thread of the fine-level red-black smoothers (autotuned)
+  int zb64 = 1, zb32 = 1;
   char err[512] = "";
 };
 
@@ -231,12 +233,17 @@ inline LevelCoef level_coef(int dim, int s, double a) {
 }
 
 inline dim3 pt_grid(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
-inline dim3 rb_grid(int dim, int s) { return dim3(((s + 1) / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
+inline dim3 rb_grid(int dim, int s, int zb = 1) {
+  return dim3(((s + 1) / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? (s + zb - 1) / zb : 1);
+}
 const dim3 kBlock(kBX, kBY, 1);
 
 inline size_t pow_dim(int dim, size_t s) { return dim == 2 ? s * s : s * s * s; }
 
-int bottom_threshold(int dim) { return dim == 2 ? 63 : 15; }
+// Largest side handled by the single-block bottom kernel.  One block runs on
+// one SM, whose FP64 pipe issues 2 operations per clock on GB300, so FP64
+// hierarchies hand only the smallest grids to it; FP32 ones go deeper.
+int bottom_threshold(int dim, bool fp64) { return dim == 2 ? (fp64 ? 31 : 63) : (fp64 ? 7 : 15); }
 
 template <typename T>
 isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
@@ -250,7 +257,7 @@ isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   }
   H.nlev = l;
   H.lb = 0;
-  while (H.side[H.lb] > bottom_threshold(ctx->dim)) ++H.lb;
+  while (H.side[H.lb] > bottom_threshold(ctx->dim, sizeof(T) == 8)) ++H.lb;
   for (int q = 0; q < H.nlev; ++q) {
     const size_t bytes = H.npts[q] * sizeof(T);
     const bool global_level = q < H.lb;
@@ -318,6 +325,7 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
   // ping-pongs between home and H.t[l]).
   const int s = H.side[l];
   const T kappa = T(level_coef(DIM, s, a).kappa);
+  const int zb = l == 0 ? (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) : 1;
   for (int it = 0; it < sweeps; ++it) {
     if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) {
       T* out = (x == H.t[l]) ? home : H.t[l];
@@ -335,13 +343,13 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
       {
         ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 1.0 : 1.5) * Np * sizeof(T),
                      (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, 0, x, b, zero ? 1 : 0);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s, zb), kBlock, 0, ctx->stream>>>(s, kappa, 0, x, b, zero ? 1 : 0, zb);
       }
       LAUNCH_CHECK(ctx);
       {
         ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), (nb_ops(DIM) + 1.0) * 0.5 * Np,
                      sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, 1, x, b, 0);
+        k_rbgs<T, DIM><<<rb_grid(DIM, s, zb), kBlock, 0, ctx->stream>>>(s, kappa, 1, x, b, 0, zb);
       }
       LAUNCH_CHECK(ctx);
     }
@@ -463,7 +471,7 @@ isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const
   const float kappa = float(lf.kappa);
   const float ws = float(lf.d / (level_coef(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0)));
   const double Np = double(ctx->N), Nc = double(H.npts[1]);
-  const dim3 g = rb_grid(DIM, s);
+  const dim3 g = rb_grid(DIM, s), gz = rb_grid(DIM, s, ctx->zb32);
   isdc_status st;
   {
     ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
@@ -473,12 +481,12 @@ isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const
   auto sweep = [&](bool zero) -> isdc_status {
     {
       ProfScope ps(ctx, PC_SMOOTH0, (zero ? 1.0 : 1.5) * Np * 4, (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, false);
-      k_rbgs_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, x1, b0, zero ? 1 : 0);
+      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, x1, b0, zero ? 1 : 0, ctx->zb32);
     }
     LAUNCH_CHECK(ctx);
     {
       ProfScope ps(ctx, PC_SMOOTH0, 1.5 * Np * 4, (nb_ops(DIM) + 1.0) * 0.5 * Np, false);
-      k_rbgs_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, 1, x1, x0, b1, 0);
+      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 1, x1, x0, b1, 0, ctx->zb32);
     }
     LAUNCH_CHECK(ctx);
     return ISDC_OK;
@@ -754,6 +762,61 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   return result;
 }
 
+// Autotuner for the fine-level red-black smoother (3D): time one red and one
+// black pass with 1, 2, 4 and 8 z-planes per thread on the context's own fine
+// arrays (zeroed first; the values do not change the timing) and keep the
+// fastest.  Runs once, in isdc_create.
+isdc_status tune_smoother(isdc_ctx* ctx) {
+  if (ctx->dim != 3 || ctx->opt.smoother != ISDC_SMOOTHER_RBGS) return ISDC_OK;
+  const int s = ctx->n, cand[4] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_zb = 1;
+  const bool split = ctx->sp_x != nullptr;
+  double* x64 = ctx->U;
+  if (split) {
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+  } else if (!ctx->opt.vcycle_fp32) {
+    CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, ctx->N * sizeof(double), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->b, 0, ctx->N * sizeof(double), ctx->stream));
+  } else {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ISDC_OK;
+  }
+  for (int rep = 0; rep < 2; ++rep)  // the first round warms up
+    for (int c = 0; c < 4; ++c) {
+      const int zb = cand[c];
+      const dim3 g = rb_grid(3, s, zb);
+      CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+      for (int colour = 0; colour < 2; ++colour) {
+        if (split) {
+          float* xc = ctx->sp_x + colour * ctx->hn;
+          float* xo = ctx->sp_x + (1 - colour) * ctx->hn;
+          k_rbgs_split<3><<<g, kBlock, 0, ctx->stream>>>(s, 0.1f, colour, xc, xo, ctx->sp_b + colour * ctx->hn, 0, zb);
+        } else {
+          k_rbgs<double, 3><<<g, kBlock, 0, ctx->stream>>>(s, 0.1, colour, x64, ctx->b, 0, zb);
+        }
+      }
+      CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
+      CUDA_TRY(ctx, cudaEventSynchronize(e1));
+      LAUNCH_CHECK(ctx);
+      float ms = 0.f;
+      CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < best) {
+        best = ms;
+        best_zb = zb;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (split) ctx->zb32 = best_zb; else ctx->zb64 = best_zb;
+  return ISDC_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -928,6 +991,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       if ((st = upload_ainv(ctx, ctx->h64, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   }
   ctx->spare_slot = M - 1;
+  if ((st = tune_smoother(ctx)) != ISDC_OK) return bail(st);
   CREATE_TRY(cudaGetLastError());
 #undef CREATE_TRY
   *out = ctx;
@@ -1054,6 +1118,13 @@ ISDC_API isdc_status isdc_profile_read(isdc_ctx* ctx, isdc_kernel_stat* out, int
     ++c;
   }
   if (count) *count = c;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_tuning(const isdc_ctx* ctx, int* zb_fp64, int* zb_fp32) {
+  if (!ctx) return ISDC_ERR_INVALID_ARG;
+  if (zb_fp64) *zb_fp64 = ctx->zb64;
+  if (zb_fp32) *zb_fp32 = ctx->zb32;
   return ISDC_OK;
 }
 

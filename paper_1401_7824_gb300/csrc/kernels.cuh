@@ -70,20 +70,23 @@ __global__ void __launch_bounds__(kBX* kBY)
 // interior indices.  Each thread owns one point of the colour and solves its
 // row: x_p = beta_p + kappa * (sum of neighbours).  zero_guess (red pass from
 // x == 0): the neighbours are zero.
+// zb: z-planes per thread (3D; blockIdx.z covers planes [zb*blockIdx.z, +zb)),
+// picked by the context's autotuner.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_rbgs(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+    k_rbgs(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess, int zb) {
   const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  const int k = blockIdx.z;
-  // (i+1)+(j+1)+(k+1) parity == colour  <=>  i parity == (colour + j + k + DIM) & 1
-  const int i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0) + DIM) & 1);
-  if (i >= n || j >= n) return;
-  const int p = lin<DIM>(i, j, k, n);
-  if (zero_guess) {
-    x[p] = beta[p];
-    return;
+  if (j >= n) return;
+  const int nz = DIM == 3 ? zb : 1;
+  for (int kk = 0; kk < nz; ++kk) {
+    const int k = DIM == 3 ? blockIdx.z * zb + kk : 0;
+    if (k >= (DIM == 3 ? n : 1)) return;
+    // (i+1)+(j+1)+(k+1) parity == colour  <=>  i parity == (colour + j + k + DIM) & 1
+    const int i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0) + DIM) & 1);
+    if (i >= n) continue;
+    const int p = lin<DIM>(i, j, k, n);
+    x[p] = zero_guess ? beta[p] : fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]);
   }
-  x[p] = fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]);
 }
 
 // Scaled residual r' = beta - x + kappa * sum = (b - H x)/d.
@@ -338,15 +341,20 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs_split(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
-                 const float* __restrict__ bc, int zero_guess) {
+                 const float* __restrict__ bc, int zero_guess, int zb) {
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
-  const int i0 = (colour + j + (DIM == 3 ? k : 0) + DIM) & 1;
-  const int i = 2 * h + i0;
-  if (i >= n || j >= n) return;
-  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
-  xc[slot] = zero_guess ? bc[slot] : fmaf(kappa, split_nbsum<DIM>(xo, h, i, i0, j, k, n, H), bc[slot]);
+  if (j >= n) return;
+  const int nz = DIM == 3 ? zb : 1;
+  for (int kk = 0; kk < nz; ++kk) {
+    const int k = DIM == 3 ? blockIdx.z * zb + kk : 0;
+    if (k >= (DIM == 3 ? n : 1)) return;
+    const int i0 = (colour + j + (DIM == 3 ? k : 0) + DIM) & 1;
+    const int i = 2 * h + i0;
+    if (i >= n) continue;
+    const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+    xc[slot] = zero_guess ? bc[slot] : fmaf(kappa, split_nbsum<DIM>(xo, h, i, i0, j, k, n, H), bc[slot]);
+  }
 }
 
 // Scaled residual at the red points after a complete red-black sweep (the

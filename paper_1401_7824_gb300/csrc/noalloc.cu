@@ -180,8 +180,8 @@ isdc_status smooth(const Solve& S, int l, double*& x, double* home, const double
       k_jacobi<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, kappa, S.omega, x, b, out, zero ? 1 : 0);
       x = out;
     } else {
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 0, x, b, zero ? 1 : 0);
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 1, x, b, 0);
+      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 0, x, b, zero ? 1 : 0, 1);
+      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 1, x, b, 0, 1);
     }
     STATIC_TRY(cudaGetLastError());
     zero = false;

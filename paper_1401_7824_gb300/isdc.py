@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
         "isdc_batch_destroy": (None, [_ctx_p]),
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
+        "isdc_tuning": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
         "isdc_destroy": (None, [_ctx_p]),
     }
@@ -274,6 +275,12 @@ def isdc_profile_read(ctx):
         out[r.name.decode()] = dict(launches=r.launches, total_ms=r.total_ms, bytes=r.bytes,
                                     fp64_ops=r.fp64_ops, fp32_ops=r.fp32_ops)
     return out
+
+
+def isdc_tuning(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().isdc_tuning(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return {"zb_fp64": a.value, "zb_fp32": b.value}
 
 
 def isdc_last_error(ctx=None) -> str:
@@ -451,6 +458,9 @@ class Isdc:
 
     def vcycles(self, a, x, b, n_cycles):
         isdc_vcycles(self.ctx, a, x, b, n_cycles)
+
+    def tuning(self):
+        return isdc_tuning(self.ctx)
 
     def profile(self, on=True, classes=None):
         isdc_profile_enable(self.ctx, on, classes)
