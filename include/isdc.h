@@ -44,7 +44,7 @@ typedef struct isdc_ctx isdc_ctx;
 typedef enum {
     ISDC_OK = 0,
     ISDC_ERR_INVALID_ARG = 1,   /* bad size, parameter or NULL pointer            */
-    ISDC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement   */
+    ISDC_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement   */
     ISDC_ERR_OOM = 3,           /* device allocation failed                       */
     ISDC_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed    */
     ISDC_ERR_NOT_CONVERGED = 5, /* soft: max_sweeps reached; u holds the last sweep */
