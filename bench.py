@@ -363,6 +363,7 @@ def run_batch(args):
     for _ in range(warm):
         G.isdc_batch_tick(eng)
     info = G.isdc_batch_stats(eng)
+    launches0 = info.kernel_launches
     torch.cuda.synchronize()
     clocks = ClockSampler(None)
     clocks.start()
@@ -378,6 +379,7 @@ def run_batch(args):
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
     info = G.isdc_batch_stats(eng)
+    launches = info.kernel_launches - launches0
     G.isdc_batch_destroy(eng)
     line = {"metric": "DOF-sweeps/s", "value": dofs / elapsed, "unit": "DOF-sweeps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": warm, "ms_per_step": elapsed / args.steps * 1e3,
@@ -390,6 +392,7 @@ def run_batch(args):
                        "l2": "inputs larger than L2 (all instances resident, tens of GB)",
                        "launch_shape": {"threads_per_block": info.threads_per_block,
                                         "blocks_per_sm": info.blocks_per_sm, "tuned": info.tuned}},
+            "gpu_launches": int(launches),
             "clocks": clk}
     if args.compare_fp64:
         # the same instances one at a time through the FP64 single-instance path

@@ -249,6 +249,7 @@ typedef struct {
 
 typedef struct {
     int64_t ticks;
+    int64_t kernel_launches;    /* kernels executed by all ticks (kernel nodes of the tick graphs) */
     size_t  bytes_in_use;
     int     running;
     int     tuned;              /* 1 once the autotuner has picked the launch shape */

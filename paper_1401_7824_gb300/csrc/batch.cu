@@ -81,6 +81,8 @@ struct isdc_batch {
   double tune_rate[kNumShapes] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   long long ticks = 0;
+  long long kernel_launches = 0;   // kernel nodes executed by all ticks
+  int kernel_nodes[kNumShapes] = {};  // kernel nodes per tick graph
   char err[512] = "";
 };
 
@@ -254,6 +256,16 @@ isdc_status capture(isdc_batch* b, int shape) {
   if (b->dim == 2) record_tick<2>(b, kShapes[shape]); else record_tick<3>(b, kShapes[shape]);
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t q = 0; q < nn; ++q) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+          ++b->kernel_nodes[shape];
+      }
+  }
   e = cudaGraphInstantiate(&b->exec[shape], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -477,6 +489,7 @@ ISDC_API isdc_status isdc_batch_tick(isdc_batch* b, int* running_out, int* finis
     B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice, b->stream));
     B_TRY(b, cudaEventRecord(b->ev0, b->stream));
     B_TRY(b, cudaGraphLaunch(b->exec[shape], b->stream));
+    b->kernel_launches += b->kernel_nodes[shape];
     B_TRY(b, cudaEventRecord(b->ev1, b->stream));
     B_TRY(b, cudaStreamSynchronize(b->stream));
     float ms = 0.f;
@@ -564,6 +577,7 @@ ISDC_API isdc_status isdc_batch_take(isdc_batch* b, int slot, double* u_out, int
 ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info) {
   if (!b || !info) return ISDC_ERR_INVALID_ARG;
   info->ticks = b->ticks;
+  info->kernel_launches = b->kernel_launches;
   info->bytes_in_use = b->used;
   info->tuned = b->tuned;
   info->threads_per_block = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].threads;

@@ -59,7 +59,8 @@ class isdc_slot_info(ctypes.Structure):
 
 
 class isdc_batch_info(ctypes.Structure):
-    _fields_ = [("ticks", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t), ("running", ctypes.c_int),
+    _fields_ = [("ticks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("running", ctypes.c_int),
                 ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
 
 

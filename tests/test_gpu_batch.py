@@ -120,3 +120,27 @@ def test_server_continuous_batching_same_alone_and_in_mix():
         r1 = alone.run([Request(q, 0.0, d, n, nu, M, dt, steps, initial_condition(d, n, 90 + q))])
         alone.close()
         np.testing.assert_array_equal(r1.requests[0].result, reqs[q].result)
+
+
+def test_server_queues_requests_under_memory_pressure():
+    """With room for one instance at a time, requests wait for memory, every
+    request still completes, and results equal the runs alone."""
+    from paper_1401_7824_gb300.serve import Request, Server
+    probe = _engine(2)
+    one = probe.query(probe.admit(63, 0.1, 5, 0.02, 1, initial_condition(2, 63, 1))).device_bytes
+    probe.close()
+    specs = [(63, 0.3, 5, 0.05, 1), (63, 0.05, 5, 0.02, 1), (63, 1.0, 3, 0.01, 2)]
+    reqs = [Request(q, 0.0, 2, n, nu, M, dt, steps, initial_condition(2, n, 130 + q))
+            for q, (n, nu, M, dt, steps) in enumerate(specs)]
+    srv = Server(hbm_budget_bytes=(int(1.2 * one), 1 << 30), max_side=(63, 15))
+    rep = srv.run(reqs, realtime=False)
+    srv.close()
+    assert rep.summary()["completed"] == 3
+    admitted = sorted(r.admitted for r in reqs)
+    done = sorted(r.done for r in reqs)
+    assert admitted[1] >= done[0] and admitted[2] >= done[1]   # one at a time
+    for q, (n, nu, M, dt, steps) in enumerate(specs):
+        alone = Server(hbm_budget_bytes=(4 << 30, 1 << 30), max_side=(63, 15))
+        r1 = alone.run([Request(q, 0.0, 2, n, nu, M, dt, steps, initial_condition(2, n, 130 + q))])
+        alone.close()
+        np.testing.assert_array_equal(r1.requests[0].result, reqs[q].result)

@@ -254,3 +254,32 @@ def test_sweep_graph_replay_is_bitwise_identical(fp32):
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
     assert outs[0][2] == outs[1][2]
+
+
+def test_fp32_red_black_2d_split_layout_converges_to_oracle():
+    """2D red-black smoothing with FP32 V-cycles uses the colour-split fine level."""
+    p = O.Problem(2, 255, 0.2, 5, 0.02, smoother=RB, nu1=2, nu2=2, max_sweeps=150)
+    u0 = initial_condition(2, 255, seed=17)
+    ref = O.integrate(p, u0, 2, 0, 2)
+    g = make_gpu(p, vcycle_fp32=True)
+    u = to_dev(u0)
+    for s in range(2):
+        assert g.step(u, 0, 2) == 0
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-9
+
+
+def test_largest_grid_allocates_and_a_second_reports_oom():
+    """The largest grid (3D side 1023, M = 7: ~200 GB of node state and
+    hierarchy) allocates; a second one does not fit beside it and fails cleanly
+    with ISDC_ERR_OOM (an allocation failure; nothing is launched)."""
+    import paper_1401_7824_gb300 as G
+    big = G.isdc_create(3, 1023, 0.1, 7, 0.01)
+    try:
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_create(3, 1023, 0.1, 7, 0.01)
+        assert e.value.status == G.ISDC_ERR_OOM
+    finally:
+        G.isdc_destroy(big)
+    g = make_gpu(O.Problem(2, 63, 0.1, 3, 0.05))  # the device is still usable afterwards
+    u = to_dev(initial_condition(2, 63, seed=1))
+    assert g.step(u, 2, 2) == 0
