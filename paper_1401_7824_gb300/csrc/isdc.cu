@@ -116,6 +116,7 @@ struct isdc_ctx {
   unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
   // z-planes per thread of the fine-level red-black smoothers (autotuned)
   int zb64 = 1, zb32 = 1;
+  int zbl[kMaxLevels] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // per grid-wide level (natural layout)
   char err[512] = "";
 };
 
@@ -325,7 +326,7 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
   // ping-pongs between home and H.t[l]).
   const int s = H.side[l];
   const T kappa = T(level_coef(DIM, s, a).kappa);
-  const int zb = l == 0 ? (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) : 1;
+  const int zb = ctx->zbl[l];
   for (int it = 0; it < sweeps; ++it) {
     if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) {
       T* out = (x == H.t[l]) ? home : H.t[l];
@@ -762,59 +763,78 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   return result;
 }
 
-// Autotuner for the fine-level red-black smoother (3D): time one red and one
-// black pass with 1, 2, 4 and 8 z-planes per thread on the context's own fine
-// arrays (zeroed first; the values do not change the timing) and keep the
-// fastest.  Runs once, in isdc_create.
+// Autotuner for the red-black smoothers (3D): on every grid-wide level with
+// side >= 31, time one red and one black pass with 1, 2, 4 and 8 z-planes per
+// thread on the context's own arrays of that level (zeroed first; the values
+// do not change the timing) and keep the fastest.  Runs once, in isdc_create.
+template <typename T>
+float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0, float* bs0, size_t hn,
+                     cudaEvent_t e0, cudaEvent_t e1, isdc_status* st) {
+  *st = ISDC_OK;
+  if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { *st = ISDC_ERR_CUDA; return 0.f; }
+  for (int colour = 0; colour < 2; ++colour) {
+    if (xs0) {
+      k_rbgs_split<3><<<rb_grid(3, s, zb), kBlock, 0, ctx->stream>>>(s, 0.1f, colour, xs0 + colour * hn,
+                                                                     xs0 + (1 - colour) * hn, bs0 + colour * hn, 0,
+                                                                     zb);
+    } else {
+      k_rbgs<T, 3><<<rb_grid(3, s, zb), kBlock, 0, ctx->stream>>>(s, T(0.1), colour, x, b, 0, zb);
+    }
+  }
+  float ms = 0.f;
+  if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaGetLastError() != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+    *st = fail(ctx, ISDC_ERR_CUDA, "smoother autotuning failed");
+  return ms;
+}
+
+template <typename T>
+isdc_status tune_levels(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cudaEvent_t e0, cudaEvent_t e1) {
+  const int cand[4] = {1, 2, 4, 8};
+  for (int l = 0; l < H.lb; ++l) {
+    const int s = H.side[l];
+    if (s < 31) break;
+    T* x = l == 0 ? x0 : H.x[l];
+    T* b = l == 0 ? b0 : H.b[l];
+    const bool split = l == 0 && split0;
+    if (split) {
+      CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+      CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+    } else {
+      CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(T), ctx->stream));
+      CUDA_TRY(ctx, cudaMemsetAsync(b, 0, H.npts[l] * sizeof(T), ctx->stream));
+    }
+    float best = 1e30f;
+    int best_zb = 1;
+    for (int rep = 0; rep < 2; ++rep)  // the first round warms up
+      for (int c = 0; c < 4; ++c) {
+        isdc_status st;
+        const float ms = time_rbgs_pass<T>(ctx, s, cand[c], x, b, split ? ctx->sp_x : nullptr,
+                                           split ? ctx->sp_b : nullptr, ctx->hn, e0, e1, &st);
+        if (st != ISDC_OK) return st;
+        if (rep == 1 && ms < best) {
+          best = ms;
+          best_zb = cand[c];
+        }
+      }
+    if (split) ctx->zb32 = best_zb;
+    else ctx->zbl[l] = best_zb;
+    if (l == 0 && !split) (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) = best_zb;
+  }
+  return ISDC_OK;
+}
+
 isdc_status tune_smoother(isdc_ctx* ctx) {
   if (ctx->dim != 3 || ctx->opt.smoother != ISDC_SMOOTHER_RBGS) return ISDC_OK;
-  const int s = ctx->n, cand[4] = {1, 2, 4, 8};
   cudaEvent_t e0, e1;
   CUDA_TRY(ctx, cudaEventCreate(&e0));
   CUDA_TRY(ctx, cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_zb = 1;
-  const bool split = ctx->sp_x != nullptr;
-  double* x64 = ctx->U;
-  if (split) {
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
-  } else if (!ctx->opt.vcycle_fp32) {
-    CUDA_TRY(ctx, cudaMemsetAsync(x64, 0, ctx->N * sizeof(double), ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->b, 0, ctx->N * sizeof(double), ctx->stream));
-  } else {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return ISDC_OK;
-  }
-  for (int rep = 0; rep < 2; ++rep)  // the first round warms up
-    for (int c = 0; c < 4; ++c) {
-      const int zb = cand[c];
-      const dim3 g = rb_grid(3, s, zb);
-      CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
-      for (int colour = 0; colour < 2; ++colour) {
-        if (split) {
-          float* xc = ctx->sp_x + colour * ctx->hn;
-          float* xo = ctx->sp_x + (1 - colour) * ctx->hn;
-          k_rbgs_split<3><<<g, kBlock, 0, ctx->stream>>>(s, 0.1f, colour, xc, xo, ctx->sp_b + colour * ctx->hn, 0, zb);
-        } else {
-          k_rbgs<double, 3><<<g, kBlock, 0, ctx->stream>>>(s, 0.1, colour, x64, ctx->b, 0, zb);
-        }
-      }
-      CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
-      CUDA_TRY(ctx, cudaEventSynchronize(e1));
-      LAUNCH_CHECK(ctx);
-      float ms = 0.f;
-      CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
-      if (rep == 1 && ms < best) {
-        best = ms;
-        best_zb = zb;
-      }
-    }
+  isdc_status st = ctx->opt.vcycle_fp32
+                       ? tune_levels<float>(ctx, ctx->h32, ctx->h32.x[0], ctx->h32.b[0], ctx->sp_x != nullptr, e0, e1)
+                       : tune_levels<double>(ctx, ctx->h64, ctx->U, ctx->b, false, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (split) ctx->zb32 = best_zb; else ctx->zb64 = best_zb;
-  return ISDC_OK;
+  return st;
 }
 
 }  // namespace

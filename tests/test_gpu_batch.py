@@ -144,3 +144,36 @@ def test_server_queues_requests_under_memory_pressure():
         r1 = alone.run([Request(q, 0.0, 2, n, nu, M, dt, steps, initial_condition(2, n, 130 + q))])
         alone.close()
         np.testing.assert_array_equal(r1.requests[0].result, reqs[q].result)
+
+
+def test_full_256_instance_batch_matches_single_instance_runs():
+    """The 256-instance batch at full size (one step each): sampled instances
+    (smallest, median and largest side) against independent single-instance
+    runs with FP32 V-cycles, both at SDC residual < 1e-10."""
+    import paper_1401_7824_gb300 as G
+    from gpu_util import make_gpu, to_dev
+    from isdc_inputs import batch_instances
+    insts = batch_instances(256, seed=4)
+    eng = G.Batch(2, 1023, 5, 200 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+    slots = [eng.admit(w.n, w.nu, w.M, w.dt, 1, initial_condition(2, w.n, w.seed)) for w in insts]
+    assert all(s is not None for s in slots)
+    while eng.tick()[0]:
+        pass
+    order = sorted(range(len(insts)), key=lambda q: insts[q].n)
+    sample = {order[0], order[len(order) // 2], order[-1]}
+    results = {}
+    for q, s in enumerate(slots):
+        info = eng.query(s)
+        assert info.state == G.ISDC_SLOT_FINISHED and info.nonconverged_steps == 0
+        out = eng.take(s)
+        if q in sample:
+            results[q] = out
+    eng.close()
+    for q in sample:
+        w = insts[q]
+        p = O.Problem(2, w.n, w.nu, w.M, w.dt, smoother=O.SMOOTHER_JACOBI, max_sweeps=150)
+        g = make_gpu(p, vcycle_fp32=True)
+        u = to_dev(initial_condition(2, w.n, w.seed))
+        assert g.step(u, 0, 2) == 0
+        assert rel_l2(results[q], u.cpu().numpy()) <= 1e-9
+        g.close()

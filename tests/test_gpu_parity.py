@@ -283,3 +283,42 @@ def test_largest_grid_allocates_and_a_second_reports_oom():
     g = make_gpu(O.Problem(2, 63, 0.1, 3, 0.05))  # the device is still usable afterwards
     u = to_dev(initial_condition(2, 63, seed=1))
     assert g.step(u, 2, 2) == 0
+
+
+def test_mid_step_checkpoint_resumes_bitwise():
+    """Checkpoint / resume: node values saved after 3 sweeps and restored in a
+    fresh context continue exactly like an uninterrupted 5-sweep step (a sweep
+    depends only on the node values and f of the previous one)."""
+    p = O.Problem(3, 31, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, 31, seed=23)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    g.step(u, 5, 2)
+    g2 = make_gpu(p)
+    v = to_dev(u0)
+    g2.step(v, 3, 2)
+    ckpt = g2.nodes().clone()
+    g3 = make_gpu(p)
+    g3.set_nodes(ckpt)
+    w = to_dev(u0)
+    g3.step(w, 2, 2)
+    np.testing.assert_array_equal(w.cpu().numpy(), u.cpu().numpy())
+    np.testing.assert_array_equal(g3.nodes().cpu().numpy(), g.nodes().cpu().numpy())
+
+
+def test_workload_3d_511_fp32_vcycles_full_size_residual():
+    """The 511^3 FP32-V-cycle workload at full size: one step to residual 1e-10;
+    the oracle recomputes the FP64 SDC residual of the GPU's node values."""
+    from isdc_inputs import workload_3d_511_mixed
+    w = workload_3d_511_mixed()
+    p = O.Problem(3, w.n, w.nu, w.M, w.dt, smoother=RB, nu1=2, nu2=2, max_sweeps=200)
+    u0 = initial_condition(3, w.n, w.seed)
+    g = make_gpu(p, vcycle_fp32=True)
+    u = to_dev(u0)
+    assert g.step(u, 0, w.n_vcycles) == 0
+    R = g.residual()
+    assert R < 1e-10
+    nodes = g.nodes().cpu().numpy()
+    g.close()
+    R_oracle = O.sdc_residual(p, nodes)
+    assert R_oracle < 1e-10 and abs(R_oracle - R) <= 1e-13, (R, R_oracle)
