@@ -9,9 +9,11 @@
  * this file shares no code, header, table or helper with it.
  *
  * What it computes, step by step in the paper's order and notation:
- *   - Gauss-Lobatto collocation nodes tau_1=0 < ... < tau_M=1 on [0,1] and the
- *     integration matrices Q (Q[m][j] = int_0^{tau_m} l_j) and
- *     S (node-to-node, S_m^{m+1} = Q_{m+1} - Q_m)            -- Sec. 2, Eq. 2
+ *   - collocation nodes tau_1 < ... < tau_M in [0,1] (Sec. 2 names
+ *     Gauss-Lobatto and Gauss-Legendre; Gauss-Radau with tau_M = 1 as well):
+ *     t_0 = T_n <= t_1 < ... < t_M <= T_{n+1}, and the integration matrices
+ *     Q (Q[m][j] = int_0^{tau_m} l_j) and S (point-to-point,
+ *     S_m^{m+1} = Q_{m+1} - Q_m, with the row of t_0 zero)    -- Sec. 2, Eq. 2
  *   - the semi-implicit SDC sweep                             -- Sec. 2, Eq. 4
  *       u_{m+1}^{k+1} = u_m^{k+1} + dt_m[f^I(u_{m+1}^{k+1}) - f^I(u_{m+1}^k)]
  *                     + dt_m[f^E(u_m^{k+1}) - f^E(u_m^k)] + S_m^{m+1}F(u^k)
@@ -65,6 +67,8 @@ typedef struct {
     int    max_sweeps;  /* cap for the until-tolerance mode */
     double mg_tol;      /* classical SDC: max-norm residual of the node solve */
     int    mg_max_cycles;
+    int    nodes;       /* 0 Gauss-Lobatto, 1 Gauss-Radau (right, tau_M = 1),
+                           2 Gauss-Legendre */
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -136,6 +140,64 @@ int orc_lobatto_nodes(int M, double *tau)
     return 0;
 }
 
+/*
+ * Right Gauss-Radau nodes on [0,1]: the M roots of P_M - P_{M-1} on [-1,1]
+ * (x = 1 is one of them), mapped to [0,1].  The roots are bracketed by sign
+ * changes on a fine uniform grid of [-1,1) and refined by bisection.
+ */
+int orc_radau_right_nodes(int M, double *tau)
+{
+    if (M < 2 || M > ORC_MAX_M) return 1;
+    const int samples = 4000 * M;
+    int found = 0;
+    double a = -1.0, pa, pb, dp;
+    legendre(M, a, &pa, &dp);
+    legendre(M - 1, a, &pb, &dp);
+    double ga = pa - pb;
+    for (int s = 1; s < samples && found < M - 1; ++s) {
+        double b = -1.0 + 2.0 * s / samples;
+        legendre(M, b, &pa, &dp);
+        legendre(M - 1, b, &pb, &dp);
+        double gb = pa - pb;
+        if ((ga < 0.0) != (gb < 0.0)) {
+            double lo = a, hi = b, glo = ga;
+            for (int it = 0; it < 200 && hi - lo > 1e-17; ++it) {
+                double mid = 0.5 * (lo + hi), pm, pm1;
+                legendre(M, mid, &pm, &dp);
+                legendre(M - 1, mid, &pm1, &dp);
+                double gm = pm - pm1;
+                if ((gm < 0.0) == (glo < 0.0)) { lo = mid; glo = gm; } else hi = mid;
+            }
+            tau[found++] = 0.5 * (0.5 * (lo + hi) + 1.0);
+        }
+        a = b;
+        ga = gb;
+    }
+    if (found != M - 1) return 2;
+    tau[M - 1] = 1.0;
+    return 0;
+}
+
+/* Gauss-Legendre nodes on [0,1]: the roots of P_M mapped from [-1,1], ascending. */
+int orc_legendre_nodes(int M, double *tau)
+{
+    if (M < 1 || M > ORC_MAX_M) return 1;
+    double x[ORC_MAX_M], w[ORC_MAX_M];
+    gauss_legendre(M, x, w);
+    /* gauss_legendre returns them in descending order (cosine start values) */
+    for (int i = 0; i < M; ++i) tau[i] = 0.5 * (x[M - 1 - i] + 1.0);
+    return 0;
+}
+
+/* Nodes of the given family (0 Lobatto, 1 Radau right, 2 Legendre). */
+int orc_nodes(int kind, int M, double *tau)
+{
+    if (kind == 0) return orc_lobatto_nodes(M, tau);
+    if (kind == 1) return orc_radau_right_nodes(M, tau);
+    if (kind == 2) return orc_legendre_nodes(M, tau);
+    return 1;
+}
+
 /* Lagrange basis polynomial l_j over the nodes tau, evaluated at s. */
 static double lagrange(int M, const double *tau, int j, double s)
 {
@@ -162,6 +224,21 @@ int orc_q_matrix(int M, const double *tau, double *Q)
                 acc += gw[g] * lagrange(M, tau, j, half * (gx[g] + 1.0));
             Q[m * M + j] = half * acc;
         }
+    }
+    return 0;
+}
+
+/* Full-interval weights w_j = int_0^1 l_j(s) ds (the end-point quadrature of
+ * the collocation rule; with tau_M = 1 they are the last row of Q). */
+int orc_end_weights(int M, const double *tau, double *w)
+{
+    if (M < 1 || M > ORC_MAX_M) return 1;
+    double gx[ORC_MAX_M], gw[ORC_MAX_M];
+    gauss_legendre(M, gx, gw);
+    for (int j = 0; j < M; ++j) {
+        double acc = 0.0;
+        for (int g = 0; g < M; ++g) acc += gw[g] * lagrange(M, tau, j, 0.5 * (gx[g] + 1.0));
+        w[j] = 0.5 * acc;
     }
     return 0;
 }
@@ -541,13 +618,20 @@ static void eval_f(const orc_problem *P, const double *u, double *fE, double *fI
 /*
  * Advance u (N values, in place) by one time step of length dt.
  *
+ * The sweep runs over the points t_0 = T_n and the nodes t_1..t_M of Sec. 2.
+ * Gauss-Lobatto has tau_1 = 0, so t_0 is node 1 and a sweep makes M-1 node
+ * solves; Gauss-Radau and Gauss-Legendre start at t_0 < t_1 and make M.
+ * With Gauss-Legendre (tau_M < 1) the step ends with the collocation
+ * end-point quadrature u_{n+1} = u_0 + dt sum_j w_j f(u_j); otherwise
+ * u_{n+1} is the last node value.
+ *
  * n_sweeps > 0: exactly that many sweeps; n_sweeps == 0: sweep until the SDC
  * residual drops below tol, at most max_sweeps.  n_vcycles is L for solver 0.
  * Outputs: *sweeps_out, *vcycles_out (V-cycles spent on node solves),
  * res_hist[k-1] = residual after sweep k (room for max(n_sweeps, max_sweeps)),
  * nodes_out (optional, M*N): the node values U_1..U_M after the last sweep.
- * nodes_in (optional, M*N): initial node values instead of spreading u; its
- * first node must equal u (Lobatto: tau_1 = 0).
+ * nodes_in (optional, M*N): initial node values instead of spreading u (for
+ * Gauss-Lobatto its first node must equal u).
  * Returns 0 on success (converged or fixed count), 1 when the cap is hit
  * without convergence, 2 on a non-finite residual, 3 on a bad argument.
  */
@@ -557,19 +641,33 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
 {
     const int d = P->ndim, n = P->n, M = P->M;
     if ((d != 2 && d != 3) || n < 1 || M < 2 || M > ORC_MAX_M) return 3;
+    if (P->nodes < 0 || P->nodes > 2) return 3;
     const long N = npoints(d, n);
-    double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M], S[ORC_MAX_M * ORC_MAX_M];
-    orc_lobatto_nodes(M, tau);
+    /* points: t_0 and the nodes; node j (0-based) is point j + off */
+    const int off = P->nodes == 0 ? 0 : 1, NP = M + off;
+    double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M], w[ORC_MAX_M];
+    double tpt[ORC_MAX_M + 1], Qpt[(ORC_MAX_M + 1) * ORC_MAX_M], Spt[ORC_MAX_M * ORC_MAX_M];
+    if (orc_nodes(P->nodes, M, tau) != 0) return 3;
     orc_q_matrix(M, tau, Q);
-    orc_s_matrix(M, Q, S);
+    orc_end_weights(M, tau, w);
+    /* Qpt[p][j] = int_0^{t_p} l_j: zero for t_0, the rows of Q for the nodes */
+    tpt[0] = 0.0;
+    for (int j = 0; j < M; ++j) Qpt[j] = 0.0;
+    for (int m = 0; m < M; ++m) {
+        tpt[m + off] = tau[m];
+        for (int j = 0; j < M; ++j) Qpt[(m + off) * M + j] = Q[m * M + j];
+    }
+    /* point-to-point integrals S_m^{m+1} = Qpt_{m+1} - Qpt_m (Eq. 2) */
+    for (int m = 0; m < NP - 1; ++m)
+        for (int j = 0; j < M; ++j) Spt[m * M + j] = Qpt[(m + 1) * M + j] - Qpt[m * M + j];
 
-    /* node values U_m (m = 0..M-1 here, 0-based), old iterate, f^E and f^I */
-    double *U = (double *)malloc(sizeof(double) * M * N);
-    double *Uold = (double *)malloc(sizeof(double) * M * N);
-    double *FE = (double *)malloc(sizeof(double) * M * N);
-    double *FI = (double *)malloc(sizeof(double) * M * N);
-    double *FEold = (double *)malloc(sizeof(double) * M * N);
-    double *FIold = (double *)malloc(sizeof(double) * M * N);
+    /* values at the NP points, old iterate, f^E and f^I */
+    double *U = (double *)malloc(sizeof(double) * NP * N);
+    double *Uold = (double *)malloc(sizeof(double) * NP * N);
+    double *FE = (double *)malloc(sizeof(double) * NP * N);
+    double *FI = (double *)malloc(sizeof(double) * NP * N);
+    double *FEold = (double *)malloc(sizeof(double) * NP * N);
+    double *FIold = (double *)malloc(sizeof(double) * NP * N);
     double *u0 = (double *)malloc(sizeof(double) * N);
     double *rhs = (double *)malloc(sizeof(double) * N);
     double *x = (double *)malloc(sizeof(double) * N);
@@ -581,34 +679,35 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
 
     /* Initial iterate: u_0 spread to every node (the paper does not state it). */
     memcpy(u0, u, sizeof(double) * N);
-    for (int m = 0; m < M; ++m) {
-        memcpy(U + m * N, nodes_in ? nodes_in + m * N : u0, sizeof(double) * N);
-        eval_f(P, U + m * N, FE + m * N, FI + m * N);
-    }
+    memcpy(U, u0, sizeof(double) * N); /* point t_0 */
+    for (int m = 0; m < M; ++m)
+        if (m + off > 0) memcpy(U + (m + off) * N, nodes_in ? nodes_in + m * N : u0, sizeof(double) * N);
+    for (int p = 0; p < NP; ++p) eval_f(P, U + p * N, FE + p * N, FI + p * N);
 
     int k = 0, status = 0;
     long vcycles = 0;
     int cap = n_sweeps > 0 ? n_sweeps : P->max_sweeps;
     for (;;) {
         /* keep u^k and F(u^k) for the whole sweep */
-        memcpy(Uold, U, sizeof(double) * M * N);
-        memcpy(FEold, FE, sizeof(double) * M * N);
-        memcpy(FIold, FI, sizeof(double) * M * N);
+        memcpy(Uold, U, sizeof(double) * NP * N);
+        memcpy(FEold, FE, sizeof(double) * NP * N);
+        memcpy(FIold, FI, sizeof(double) * NP * N);
 
-        /* node 0 is t_0 = T_n (Lobatto): u_0^{k+1} = u_0, nothing to solve */
-        for (int m = 0; m < M - 1; ++m) {
-            double dtm = P->dt * (tau[m + 1] - tau[m]);
+        /* point 0 is t_0: u_0^{k+1} = u_0, nothing to solve */
+        for (int m = 0; m < NP - 1; ++m) {
+            double dtm = P->dt * (tpt[m + 1] - tpt[m]);
             double a = dtm * P->nu; /* (I - dt_m A) with A = nu L_h */
             const double *Um_new = U + m * N;
             for (long p = 0; p < N; ++p) fe_new[p] = f_explicit(P, Um_new[p]);
             /* Eq. 4 with the implicit unknown moved left:
              * (I - dt_m A) u_{m+1}^{k+1} = u_m^{k+1}
              *     + dt_m [f^E(u_m^{k+1}) - f^E(u_m^k)] - dt_m f^I(u_{m+1}^k)
-             *     + S_m^{m+1} F(u^k),   S_m^{m+1}F = dt sum_j s_{m,j} f(u_j^k) */
+             *     + S_m^{m+1} F(u^k),   S_m^{m+1}F = dt sum_j s_{m,j} f(u_j^k)
+             * (the sum runs over the nodes j, which are points j + off) */
             for (long p = 0; p < N; ++p) {
                 double sf = 0.0;
                 for (int j = 0; j < M; ++j)
-                    sf += S[m * M + j] * (FEold[j * N + p] + FIold[j * N + p]);
+                    sf += Spt[m * M + j] * (FEold[(j + off) * N + p] + FIold[(j + off) * N + p]);
                 rhs[p] = Um_new[p] + dtm * (fe_new[p] - FEold[m * N + p])
                        - dtm * FIold[(m + 1) * N + p] + P->dt * sf;
             }
@@ -645,13 +744,14 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
 
         /* F(u^{k+1}) and the SDC residual
          * max_m max_x | u_0 + dt sum_j q_{m,j} f(u_j^{k+1}) - u_m^{k+1} |   (Sec. 3) */
-        for (int m = 0; m < M; ++m) eval_f(P, U + m * N, FE + m * N, FI + m * N);
+        for (int p = 0; p < NP; ++p) eval_f(P, U + p * N, FE + p * N, FI + p * N);
         double R = 0.0;
         for (int m = 0; m < M; ++m)
             for (long p = 0; p < N; ++p) {
                 double qf = 0.0;
-                for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
-                double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
+                for (int j = 0; j < M; ++j)
+                    qf += Q[m * M + j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
+                double r = fabs(u0[p] + P->dt * qf - U[(m + off) * N + p]);
                 if (r > R || r != r) R = r;
             }
         if (res_hist) res_hist[k - 1] = R;
@@ -664,8 +764,17 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
         }
     }
 
-    memcpy(u, U + (M - 1) * N, sizeof(double) * N); /* Lobatto: tau_M = 1 */
-    if (nodes_out) memcpy(nodes_out, U, sizeof(double) * M * N);
+    if (P->nodes == 2) {
+        /* Gauss-Legendre: tau_M < 1, end-point quadrature of the collocation rule */
+        for (long p = 0; p < N; ++p) {
+            double wf = 0.0;
+            for (int j = 0; j < M; ++j) wf += w[j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
+            u[p] = u0[p] + P->dt * wf;
+        }
+    } else {
+        memcpy(u, U + (NP - 1) * N, sizeof(double) * N); /* tau_M = 1 */
+    }
+    if (nodes_out) memcpy(nodes_out, U + off * N, sizeof(double) * M * N);
     if (sweeps_out) *sweeps_out = k;
     if (vcycles_out) *vcycles_out = vcycles;
     free(U); free(Uold); free(FE); free(FI); free(FEold); free(FIold);
@@ -676,16 +785,18 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
 
 /*
  * SDC residual of given node values (Sec. 3): with f_j = f(U_j),
- *   R = max_m max_x | u_0 + dt sum_j q_{m,j} f_j - U_m |,   u_0 = U_1.
- * U: M*N node values.  Used to check a result at sizes where running the
- * whole step on the CPU is too slow.
+ *   R = max_m max_x | u_0 + dt sum_j q_{m,j} f_j - U_m |.
+ * U: M*N node values.  u0: the step's initial value, or NULL for
+ * Gauss-Lobatto (u_0 = U_1).  Used to check a result at sizes where running
+ * the whole step on the CPU is too slow.
  */
-double orc_sdc_residual(const orc_problem *P, const double *U)
+double orc_sdc_residual(const orc_problem *P, const double *u0, const double *U)
 {
     const int M = P->M;
     const long N = npoints(P->ndim, P->n);
     double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M];
-    orc_lobatto_nodes(M, tau);
+    if (orc_nodes(P->nodes, M, tau) != 0 || (!u0 && P->nodes != 0)) return -1.0;
+    if (!u0) u0 = U;
     orc_q_matrix(M, tau, Q);
     double *FE = (double *)malloc(sizeof(double) * M * N);
     double *FI = (double *)malloc(sizeof(double) * M * N);
@@ -695,7 +806,7 @@ double orc_sdc_residual(const orc_problem *P, const double *U)
         for (long p = 0; p < N; ++p) {
             double qf = 0.0;
             for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
-            double r = fabs(U[p] + P->dt * qf - U[m * N + p]);
+            double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
             if (r > R || r != r) R = r;
         }
     free(FE); free(FI);

@@ -35,6 +35,9 @@ GUESS_LEFT_NODE = 2       # u_m^{k+1}
 REACTION_NONE = 0
 REACTION_ALLEN_CAHN = 1   # f^E(u) = u - u^3
 REACTION_LINEAR = 2       # f^E(u) = lambda_e * u
+NODES_LOBATTO = 0         # Gauss-Lobatto, tau_1 = 0, tau_M = 1 (M - 1 solves per sweep)
+NODES_RADAU_RIGHT = 1     # Gauss-Radau, tau_M = 1 (M solves per sweep)
+NODES_LEGENDRE = 2        # Gauss-Legendre, interior nodes (M solves, end-point quadrature)
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +58,7 @@ class _Problem(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("solver", ctypes.c_int), ("guess", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
-                ("mg_max_cycles", ctypes.c_int)]
+                ("mg_max_cycles", ctypes.c_int), ("nodes", ctypes.c_int)]
 
 
 @dataclass
@@ -78,11 +81,12 @@ class Problem:
     max_sweeps: int = 50
     mg_tol: float = 1e-12
     mg_max_cycles: int = 100
+    nodes: int = NODES_LOBATTO
 
     def _c(self) -> _Problem:
         return _Problem(self.ndim, self.n, self.nu, self.M, self.dt, self.reaction, self.lambda_e,
                         self.smoother, self.nu1, self.nu2, self.omega, self.solver, self.guess,
-                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles)
+                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles, self.nodes)
 
     @property
     def shape(self):
@@ -100,6 +104,8 @@ def _L():
         dp = ctypes.POINTER(ctypes.c_double)
         I, D = ctypes.c_int, ctypes.c_double
         lib.orc_lobatto_nodes.argtypes = [I, dp]
+        lib.orc_nodes.argtypes = [I, I, dp]
+        lib.orc_end_weights.argtypes = [I, dp, dp]
         lib.orc_q_matrix.argtypes = [I, dp, dp]
         lib.orc_s_matrix.argtypes = [I, dp, dp]
         lib.orc_laplacian.argtypes = [I, I, dp, dp]
@@ -113,9 +119,10 @@ def _L():
         lib.orc_vcycle.argtypes = [ctypes.POINTER(_Problem), D, dp, dp]
         lib.orc_isdc_step.argtypes = [ctypes.POINTER(_Problem), dp, I, I, ctypes.POINTER(I),
                                       ctypes.POINTER(ctypes.c_long), dp, dp, dp]
-        lib.orc_sdc_residual.argtypes = [ctypes.POINTER(_Problem), dp]
+        lib.orc_sdc_residual.argtypes = [ctypes.POINTER(_Problem), dp, dp]
         lib.orc_sdc_residual.restype = D
-        for f in ("orc_lobatto_nodes", "orc_q_matrix", "orc_s_matrix", "orc_vcycle", "orc_isdc_step"):
+        for f in ("orc_lobatto_nodes", "orc_nodes", "orc_end_weights", "orc_q_matrix", "orc_s_matrix",
+                  "orc_vcycle", "orc_isdc_step"):
             getattr(lib, f).restype = I
         _lib = lib
     return _lib
@@ -138,11 +145,28 @@ def lobatto_nodes(M: int) -> np.ndarray:
     return tau
 
 
-def q_matrix(M: int) -> np.ndarray:
-    tau = lobatto_nodes(M)
+def nodes(M: int, kind: int = NODES_LOBATTO) -> np.ndarray:
+    """Collocation nodes tau_1 < ... < tau_M on [0, 1] of the given family (Sec. 2)."""
+    tau = np.zeros(M)
+    if _L().orc_nodes(kind, M, _p(tau)):
+        raise ValueError("bad M or node family")
+    return tau
+
+
+def q_matrix(M: int, kind: int = NODES_LOBATTO) -> np.ndarray:
+    """Q[m, j] = int_0^{tau_m} l_j (Eq. 2)."""
+    tau = nodes(M, kind)
     Q = np.zeros((M, M))
     _L().orc_q_matrix(M, _p(tau), _p(Q))
     return Q
+
+
+def end_weights(M: int, kind: int = NODES_LOBATTO) -> np.ndarray:
+    """w_j = int_0^1 l_j: the collocation rule's weights over the whole step."""
+    tau = nodes(M, kind)
+    w = np.zeros(M)
+    _L().orc_end_weights(M, _p(tau), _p(w))
+    return w
 
 
 def s_matrix(M: int) -> np.ndarray:
@@ -265,12 +289,21 @@ def isdc_step(problem: Problem, u, n_sweeps: int = 0, n_vcycles: int = 2,
     return StepResult(u, sweeps.value, vcyc.value, hist[:sweeps.value].copy(), st, nodes)
 
 
-def sdc_residual(problem: Problem, nodes) -> float:
-    """Max-norm SDC residual (Sec. 3) of node values (shape (M,) + grid)."""
-    nodes = _f64(nodes)
-    assert nodes.shape == (problem.M,) + problem.shape
+def sdc_residual(problem: Problem, node_values, u0=None) -> float:
+    """Max-norm SDC residual (Sec. 3) of node values (shape (M,) + grid); u0 is
+    the step's initial value (for Gauss-Lobatto it defaults to the first node)."""
+    node_values = _f64(node_values)
+    assert node_values.shape == (problem.M,) + problem.shape
+    u0p = None
+    if u0 is not None:
+        u0 = _f64(u0)
+        assert u0.shape == problem.shape
+        u0p = _p(u0)
     pc = problem._c()
-    return float(_L().orc_sdc_residual(ctypes.byref(pc), _p(nodes)))
+    R = float(_L().orc_sdc_residual(ctypes.byref(pc), u0p, _p(node_values)))
+    if R < 0:
+        raise ValueError("invalid problem (u0 is required for this node family)")
+    return R
 
 
 @dataclass

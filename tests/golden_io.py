@@ -37,3 +37,37 @@ def pade_numerators():
         m, coeffs = [p.strip() for p in line.split("|")]
         out[int(m)] = [float(Fraction(c.strip())) for c in coeffs.split(",")]
     return out
+
+
+def _family_lines(name):
+    for line in _lines(name):
+        head, rest = line.split("|", 1)
+        fam, m = head.split()
+        yield fam, int(m), rest
+
+
+def radau_legendre_rules():
+    """{(family, M): (nodes, weights)} from radau_legendre_rules.txt."""
+    out = {}
+    for fam, m, rest in _family_lines("radau_legendre_rules.txt"):
+        nodes, weights = [p.strip() for p in rest.split("|")]
+        out[(fam, m)] = ([_eval(e) for e in nodes.split(",")], [_eval(e) for e in weights.split(",")])
+    return out
+
+
+def collocation_tableaus():
+    """{(family, M): A} from collocation_tableaus.txt."""
+    out = {}
+    for fam, m, rest in _family_lines("collocation_tableaus.txt"):
+        out[(fam, m)] = [[_eval(e) for e in row.split(",")] for row in rest.split(";")]
+    return out
+
+
+def pade_radau_gauss():
+    """{(family, M): (numerator, denominator)} coefficient lists, ascending powers."""
+    out = {}
+    for fam, m, rest in _family_lines("pade_radau_gauss.txt"):
+        num, den = [p.strip() for p in rest.split("|")]
+        out[(fam, m)] = ([float(Fraction(c.strip())) for c in num.split(",")],
+                         [float(Fraction(c.strip())) for c in den.split(",")])
+    return out

@@ -46,3 +46,38 @@ def test_s_matrix_is_node_to_node(M):
     # S integrates tau^p over [tau_m, tau_{m+1}] exactly for p <= M-1
     for p in range(M):
         np.testing.assert_allclose(S @ tau ** p, np.diff(tau ** (p + 1)) / (p + 1), atol=1e-14)
+
+
+# --- Gauss-Radau (right) and Gauss-Legendre nodes ------------------------------
+FAMILIES = {"radau": O.NODES_RADAU_RIGHT, "legendre": O.NODES_LEGENDRE}
+
+
+@pytest.mark.parametrize("fam,M", [("radau", 2), ("radau", 3), ("legendre", 2), ("legendre", 3)])
+def test_radau_legendre_rules_match_closed_form(fam, M):
+    from golden_io import collocation_tableaus, radau_legendre_rules
+    nodes, weights = radau_legendre_rules()[(fam, M)]
+    np.testing.assert_allclose(O.nodes(M, FAMILIES[fam]), nodes, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.end_weights(M, FAMILIES[fam]), weights, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.q_matrix(M, FAMILIES[fam]), collocation_tableaus()[(fam, M)], rtol=0, atol=2e-15)
+
+
+@pytest.mark.parametrize("fam", ["radau", "legendre"])
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 6, 7])
+def test_radau_legendre_exactness(fam, M):
+    """Q rows integrate degree <= M-1 exactly on [0, tau_m]; the full-step
+    weights integrate up to degree 2M-2 (Radau) / 2M-1 (Gauss) and no further."""
+    kind = FAMILIES[fam]
+    tau, Q, w = O.nodes(M, kind), O.q_matrix(M, kind), O.end_weights(M, kind)
+    assert np.all(np.diff(tau) > 0) and tau[0] > 0
+    if fam == "radau":
+        assert tau[-1] == 1.0
+        np.testing.assert_allclose(Q[-1], w, rtol=0, atol=1e-15)
+    else:
+        assert tau[-1] < 1.0
+        np.testing.assert_allclose(tau + tau[::-1], 1.0, rtol=0, atol=1e-15)  # symmetric
+    for p in range(M):
+        np.testing.assert_allclose(Q @ tau ** p, tau ** (p + 1) / (p + 1), rtol=0, atol=1e-14)
+    top = 2 * M - 2 if fam == "radau" else 2 * M - 1
+    for p in range(top + 1):
+        assert abs(w @ tau ** p - 1.0 / (p + 1)) < 1e-14
+    assert abs(w @ tau ** (top + 1) - 1.0 / (top + 2)) > 1e-9

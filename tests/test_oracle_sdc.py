@@ -17,7 +17,7 @@ def _collocation_solution(p: O.Problem, u0, reaction_fn=None):
     """Solve U = 1 (x) u0 + dt (Q (x) I) F(U) directly (the M*N collocation system
     whose solution converged SDC reproduces, Sec. 1-2).  F(U_j) = nu L U_j + f^E(U_j)."""
     N, M = p.N, p.M
-    Q = O.q_matrix(M)
+    Q = O.q_matrix(M, p.nodes)
     A = p.nu * D.laplacian(p.ndim, p.n)
     u0v = u0.reshape(-1)
     if p.reaction in (O.REACTION_NONE, O.REACTION_LINEAR):
@@ -205,3 +205,116 @@ def test_sdc_residual_of_nodes_matches_step_history():
     p0 = O.Problem(2, 15, 1e-300, 5, 0.02, reaction=O.REACTION_NONE)
     nodes = np.stack([u0] + [u0 + 0.1 * m for m in range(1, 5)])
     assert abs(O.sdc_residual(p0, nodes) - 0.4) < 1e-12
+
+
+# --- Gauss-Radau (right) and Gauss-Legendre nodes (Sec. 2) ----------------------
+def _full_step_weights(tau):
+    """w with sum_j w_j tau_j^p = 1/(p+1), p < M: the interpolatory rule on the
+    nodes, from a Vandermonde solve (independent of the oracle's quadrature)."""
+    M = len(tau)
+    V = np.vander(tau, M, increasing=True).T
+    return np.linalg.solve(V, 1.0 / np.arange(1, M + 1))
+
+
+def _collocation_end(p, u0, U):
+    """End value of the collocation step: the last node when tau_M = 1, else
+    u0 + dt sum_j w_j f(U_j) (Gauss-Legendre)."""
+    if p.nodes != O.NODES_LEGENDRE:
+        return U[-1]
+    A = p.nu * D.laplacian(p.ndim, p.n)
+    w = _full_step_weights(O.nodes(p.M, p.nodes))
+    F = [A @ U[j].reshape(-1) + (U[j] - U[j] ** 3).reshape(-1) if p.reaction == O.REACTION_ALLEN_CAHN
+         else A @ U[j].reshape(-1) + (p.lambda_e * U[j].reshape(-1) if p.reaction == O.REACTION_LINEAR else 0.0)
+         for j in range(p.M)]
+    return u0 + p.dt * sum(w[j] * F[j] for j in range(p.M)).reshape(p.shape)
+
+
+NODE_CASES = [
+    # ndim, n, nu, M, dt, reaction, smoother, nodes
+    (2, 7, 1.0, 3, 0.01, O.REACTION_NONE, O.SMOOTHER_JACOBI, O.NODES_RADAU_RIGHT),
+    (2, 7, 0.5, 2, 0.02, O.REACTION_ALLEN_CAHN, O.SMOOTHER_RBGS, O.NODES_RADAU_RIGHT),
+    (3, 3, 0.3, 5, 0.05, O.REACTION_ALLEN_CAHN, O.SMOOTHER_RBGS, O.NODES_LEGENDRE),
+    (2, 7, 0.2, 3, 0.05, O.REACTION_LINEAR, O.SMOOTHER_JACOBI, O.NODES_LEGENDRE),
+]
+
+
+@pytest.mark.parametrize("case", NODE_CASES)
+@pytest.mark.parametrize("solver", [O.SOLVER_EXACT, O.SOLVER_ISDC])
+def test_radau_legendre_sweeps_reproduce_collocation_solution(case, solver):
+    d, n, nu, M, dt, reaction, smoother, kind = case
+    nu1 = 1 if smoother == O.SMOOTHER_JACOBI else 2
+    p = O.Problem(d, n, nu, M, dt, reaction=reaction, lambda_e=-0.7, smoother=smoother, nu1=nu1, nu2=nu1,
+                  solver=solver, tol=1e-14, max_sweeps=200, nodes=kind)
+    u0 = initial_condition(d, n, seed=12, noise_std=0.05)
+    ref = _collocation_solution(p, u0)
+    r = O.isdc_step(p, u0, 0, 2, want_nodes=True)
+    assert r.status == 0
+    np.testing.assert_allclose(r.nodes, ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r.u, _collocation_end(p, u0, ref), rtol=0, atol=1e-12)
+    assert O.sdc_residual(p, r.nodes, u0) < 1e-13
+    # M node solves per sweep (t_0 is not a node)
+    if solver == O.SOLVER_ISDC:
+        assert r.vcycles == r.sweeps * M * 2
+
+
+@pytest.mark.parametrize("kind,M,ks,conv", [(O.NODES_RADAU_RIGHT, 3, [1, 2, 3, 4], 5),
+                                            (O.NODES_LEGENDRE, 2, [1, 2, 3], 4),
+                                            (O.NODES_LEGENDRE, 3, [1, 2, 3, 4], 6)])
+def test_radau_legendre_order_per_sweep(kind, M, ks, conv):
+    """Dahlquist problem as above: each sweep gains one order at the nodes, up
+    to the collocation order (2M-1 Radau IIA, 2M Gauss).  The Gauss step ends
+    with the full-step quadrature of f at the nodes, one order above them."""
+    n = 3
+    h = 1.0 / (n + 1)
+    lam_h = -8.0 / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    nu, lam_e, T = 1.5 / -lam_h, 0.5, 1.0
+    v = sine_mode(2, n)
+    for k in ks + [40]:
+        errs = []
+        for steps in (4, 8, 16):
+            p = O.Problem(2, n, nu, M, T / steps, reaction=O.REACTION_LINEAR, lambda_e=lam_e,
+                          solver=O.SOLVER_EXACT, nodes=kind)
+            u = v.copy()
+            for _ in range(steps):
+                u = O.isdc_step(p, u, k, 0).u
+            errs.append(np.abs(u - np.exp(-1.0 * T) * v).max())
+        order = np.log2(errs[1] / errs[2])
+        expect = min(k + (1 if kind == O.NODES_LEGENDRE else 0), conv)
+        assert abs(order - expect) < 0.35, (k, errs, order)
+
+
+@pytest.mark.parametrize("fam,kind,M", [("radau", O.NODES_RADAU_RIGHT, 2), ("radau", O.NODES_RADAU_RIGHT, 3),
+                                        ("legendre", O.NODES_LEGENDRE, 2), ("legendre", O.NODES_LEGENDRE, 3)])
+@pytest.mark.parametrize("solver", [O.SOLVER_EXACT, O.SOLVER_ISDC])
+def test_sine_mode_decays_by_radau_gauss_pade_factor(fam, kind, M, solver):
+    """Pure diffusion on a sine mode: converged SDC is the Radau IIA / Gauss
+    collocation step, whose stability function is the (M-1, M) / (M, M) Pade
+    approximant of exp."""
+    from golden_io import pade_radau_gauss
+    d, n, nu, dt = 2, 15, 1.0, 0.002
+    p_mode = (2, 1, 1)
+    h = 1.0 / (n + 1)
+    lam = -4.0 / h ** 2 * sum(np.sin(p_mode[a] * np.pi * h / 2) ** 2 for a in range(d))
+    z = dt * nu * lam
+    num, den = pade_radau_gauss()[(fam, M)]
+    R = np.polyval(num[::-1], z) / np.polyval(den[::-1], z)
+    p = O.Problem(d, n, nu, M, dt, reaction=O.REACTION_NONE, solver=solver, tol=1e-15, max_sweeps=300,
+                  nodes=kind)
+    u = sine_mode(d, n, p_mode)
+    v = u.copy()
+    for _ in range(3):
+        u = O.isdc_step(p, u, 0, 2).u
+    np.testing.assert_allclose(u, R ** 3 * v, rtol=0, atol=1e-13)
+
+
+def test_radau_legendre_resume_and_residual_need_u0():
+    p = O.Problem(2, 15, 0.2, 3, 0.02, nodes=O.NODES_LEGENDRE)
+    u0 = initial_condition(2, 15, seed=13)
+    full = O.isdc_step(p, u0, 5, 2, want_nodes=True)
+    part = O.isdc_step(p, u0, 3, 2, want_nodes=True)
+    rest = O.isdc_step(p, u0, 2, 2, want_nodes=True, nodes_in=part.nodes)
+    np.testing.assert_array_equal(rest.nodes, full.nodes)
+    np.testing.assert_array_equal(rest.u, full.u)
+    assert abs(O.sdc_residual(p, full.nodes, u0) - full.residuals[-1]) <= 1e-15
+    with pytest.raises(ValueError):
+        O.sdc_residual(p, full.nodes)
