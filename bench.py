@@ -247,7 +247,7 @@ def run_ours(args):
     N = w.n ** w.ndim
     u0 = W.initial_condition(w.ndim, w.n, w.seed)
     g = G.Isdc(w.ndim, w.n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
-               vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200)
+               vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200, temporal_blocking=args.temporal_blocking)
     stream = torch.cuda.current_stream()
     u = torch.from_numpy(u0).cuda()
     for _ in range(args.warmup):
@@ -458,6 +458,9 @@ def main():
     ap.add_argument("--compare-fp64", type=int, default=0, help="batch: also time N instances on the FP64 path")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--temporal-blocking", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="3D FP32 red-black fine level: -1 autotuned, 0 one pass per colour, "
+                         "1/2 red-black sweeps per blocked pass")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

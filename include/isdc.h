@@ -53,7 +53,11 @@ typedef enum {
                                       fit in its static scratch array                  */
 } isdc_status;
 
-/* Collocation node families (Sec. 2).  Gauss-Lobatto is implemented. */
+/* Collocation node families (Sec. 2: t_0 = T_n <= t_1 < ... < t_M <= T_{n+1}).
+ * Gauss-Lobatto: tau_1 = 0, tau_M = 1, t_0 is node 1, M-1 node solves per sweep.
+ * Gauss-Radau (right): tau_M = 1, M node solves per sweep from t_0.
+ * Gauss-Legendre: interior nodes, M node solves per sweep, and the step ends
+ * with the full-step quadrature u_{n+1} = u_0 + dt sum_j w_j f(u_j). */
 typedef enum {
     ISDC_NODES_GAUSS_LOBATTO = 0,
     ISDC_NODES_RADAU_RIGHT = 1,
@@ -83,6 +87,12 @@ typedef struct {
                              CUDA graph and replayed (same kernels, same order); 0: launch one by
                              one.  With the profiler on, the graph carries its event nodes and the
                              stream is synchronised after every replay to read them. */
+    int    temporal_blocking; /* 3D, FP32 V-cycles, red-black: smoothing of the fine level.
+                             -1 (default): chosen by the autotuner in isdc_create.  0: one pass
+                             over the grid per colour.  1 or 2: that many complete red-black
+                             sweeps per pass over HBM (temporal blocking; the same FP32
+                             operations in the same order, so the same result bit for bit).
+                             Other configurations ignore it. */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream
@@ -94,23 +104,26 @@ isdc_status isdc_default_options(isdc_options *opt);
 
 /*
  * Collocation tables of Sec. 2 (Eq. 2) on the unit interval, host only (no
- * GPU needed): nodes tau[M] (tau_1 = 0, tau_M = 1 for Gauss-Lobatto), the
- * integration matrix Q[M*M] (Q[m*M+j] = integral from 0 to tau_m of the
- * Lagrange basis polynomial l_j) and, if S is not NULL, the node-to-node matrix
- * S[(M-1)*M] = Q_{m+1} - Q_m.  The S_m^{m+1} F(u) of Eq. 2 is
- * dt * sum_j S[m*M+j] f(u_j).  Errors: UNSUPPORTED (node type), INVALID_ARG.
+ * GPU needed): nodes tau[M] (ascending; tau_1 = 0, tau_M = 1 for
+ * Gauss-Lobatto), the integration matrix Q[M*M] (Q[m*M+j] = integral from 0 to
+ * tau_m of the Lagrange basis polynomial l_j over the nodes) and, if S is not
+ * NULL, the matrix of the sweep's steps between consecutive points
+ * t_0 <= t_1 < ... : S[R*M] with R = M-1 rows (Gauss-Lobatto, S_m = Q_{m+1} -
+ * Q_m) or R = M rows (Radau, Legendre: S_0 = Q_1, S_m = Q_{m+1} - Q_m).  The
+ * S_m^{m+1} F(u) of Eq. 2 is dt * sum_j S[m*M+j] f(u_j).
+ * Errors: INVALID_ARG (node type, M outside [2, 7], NULL tau or Q).
  */
 isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double *tau, double *Q, double *S);
 
 /*
  * Create a context for one problem: the collocation tables (Sec. 2, Eq. 2:
- * nodes tau_m, Q, S_m^{m+1}, dt_m = dt (tau_{m+1} - tau_m)), the device node
- * state (u_m, f(u_m) for every node) and the multigrid hierarchy (sides
+ * nodes tau_m, Q, S_m^{m+1}, dt_m = t_{m+1} - t_m), the device node state
+ * (u and f(u) at t_0 and every node) and the multigrid hierarchy (sides
  * n, (n-1)/2, ... down to 3).
  *   ndim   2 or 3
  *   dims   ndim interior sides; all equal, each 2^j - 1 with j >= 2
  *   nu     diffusion coefficient (> 0)
- *   nodes  ISDC_NODES_GAUSS_LOBATTO (others: ISDC_ERR_UNSUPPORTED)
+ *   nodes  isdc_node_type (Gauss-Lobatto, Gauss-Radau right or Gauss-Legendre)
  *   M      number of nodes, 2..7
  *   dt     time-step length (> 0)
  *   opt    options, or NULL for the defaults
@@ -124,7 +137,8 @@ isdc_status isdc_create(int ndim, const int64_t *dims, double nu, isdc_node_type
 /*
  * Advance u by one time step (Sec. 2, Eq. 4; Sec. 3).
  *   u          device pointer, N = n^ndim float64 values; on entry u(T_n), on
- *              return u(T_n + dt) = u_M (Gauss-Lobatto: tau_M = 1)
+ *              return u(T_n + dt): u_M (Gauss-Lobatto, Radau: tau_M = 1) or
+ *              u_0 + dt sum_j w_j f(u_j) (Gauss-Legendre)
  *   n_sweeps   > 0: exactly that many sweeps (no host synchronisation);
  *              0: sweep until the SDC residual < opt.tol, at most opt.max_sweeps
  *   n_vcycles  L > 0: L V-cycles per node solve (ISDC);
@@ -166,8 +180,9 @@ isdc_status isdc_set_record_history(isdc_ctx *ctx, int record);
 isdc_status isdc_get_nodes(const isdc_ctx *ctx, double *dst);
 
 /* Use the M*N node values in the device buffer src as the initial iterate of
- * the NEXT isdc_step instead of spreading u (resume from a checkpoint).  The
- * first node must equal that step's u.  Applies to one step only. */
+ * the NEXT isdc_step instead of spreading u (resume from a checkpoint).  With
+ * Gauss-Lobatto nodes the first node must equal that step's u; with the other
+ * families t_0 is not a node and takes that step's u.  Applies to one step only. */
 isdc_status isdc_set_nodes(isdc_ctx *ctx, const double *src);
 
 /*
@@ -321,8 +336,10 @@ isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int
 /* Launch shape chosen by the context's autotuner (not from the paper): z-planes
  * per thread of the fine-level red-black smoother in FP64 and in FP32 (3D
  * red-black contexts time 1, 2, 4 and 8 on their own arrays in isdc_create;
- * otherwise 1). */
-isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32);
+ * otherwise 1); for the FP32 fine level also the temporal-blocking depth
+ * (red-black sweeps per pass, 0 = one pass per colour) and the z-planes per
+ * block of the blocked pass.  Any output pointer may be NULL. */
+isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32, int *tb_depth, int *tb_planes);
 
 /* Message for the last failure of ctx, or of isdc_create when ctx is NULL. */
 const char *isdc_last_error(const isdc_ctx *ctx);

@@ -125,7 +125,6 @@ size_t instance_bytes(const isdc_batch* b, int n, int M) {
   s += align256(size_t(M) * N * 8);        // U
   s += align256(size_t(M) * N * 8);        // F
   s += align256(size_t(M - 1) * N * 8);    // C
-  s += align256(N * 8);                    // beta
   const int nlev = levels_of(n);
   int side = n;
   const int per_level = b->opt.smoother == ISDC_SMOOTHER_JACOBI ? 4 : 3;
@@ -192,7 +191,6 @@ void record_tick(isdc_batch* b, const Shape& sh) {
   for (int m = 0; m < b->Mmax - 1; ++m) {
     const List* full0 = Ls + list_index(b, m, 0, LK_FULL);
     kb_rhs<DIM><<<grid, blk, 0, st>>>(I, full0, m, reaction);
-    kb_defect<DIM><<<grid, blk, 0, st>>>(I, full0, m);
     int loc0 = 0;  // level-0 error: in x (0) or t (1)
     for (int c = 0; c < b->L; ++c) {
       for (int l = 0; l < b->Lmax - 1; ++l) {
@@ -291,7 +289,6 @@ void fill_instance(isdc_batch* b, int slot, int n, double nu, int M, double dt, 
   I.U = static_cast<double*>(take(size_t(M) * N * 8));
   I.F = static_cast<double*>(take(size_t(M) * N * 8));
   I.C = static_cast<double*>(take(size_t(M - 1) * N * 8));
-  I.beta = static_cast<double*>(take(N * 8));
   const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
   int side = n;
   for (int l = 0; l < I.nlev; ++l) {
@@ -316,10 +313,7 @@ void fill_instance(isdc_batch* b, int slot, int n, double nu, int M, double dt, 
     for (int l = 0; l < I.nlev; ++l) {
       const double hl = 1.0 / (s + 1), c = a / (hl * hl), d = 1.0 + 2.0 * dim * c;
       I.kappa[m][l] = float(c / d);
-      if (l == 0) {
-        I.kappa0[m] = c / d;
-        I.inv_d0[m] = 1.0 / d;
-      }
+      if (l == 0) I.inv_d0[m] = 1.0 / d;
       if (l + 1 < I.nlev) {
         const int sc = (s - 1) / 2;
         const double hc = 1.0 / (sc + 1), cc = a / (hc * hc), dc = 1.0 + 2.0 * dim * cc;

@@ -27,12 +27,11 @@ struct Inst {
   double nu_h2;                       // nu / h^2 on the fine grid
   double* U;                          // M node arrays (node-major)
   double* F;                          // f(u_m), M arrays
-  double* C;                          // sweep constants, M-1 arrays
-  double* beta;                       // scaled node right-hand side
+  double* C;                          // sweep constants C'_m (defect form), M-1 arrays
   Level lev[kMaxLevels];
   double dtm[kMaxM];                  // dt (tau_{m+1} - tau_m)
   double dtQ[kMaxM][kMaxM];           // dt * Q
-  double kappa0[kMaxM], inv_d0[kMaxM];  // fine-grid row scaling per node solve
+  double inv_d0[kMaxM];               // fine-grid row scaling 1/d per node solve
   float kappa[kMaxM][kMaxLevels];     // per node solve and level
   float wscale[kMaxM][kMaxLevels];    // restriction factor level l -> l+1
   float* ainv;                        // per node solve: d * H^{-1} on the side-3 grid
@@ -111,7 +110,11 @@ __global__ void kb_spread(const Inst* __restrict__ insts, const List* __restrict
   BATCH_END
 }
 
-// beta = (u_m + dt_m f^E(u_m) + C_m) / d, and f_m = f(u_m) for m >= 1 (Eq. 4).
+// FP64 defect of node m+1's equation at its initial guess u_{m+1}^k, scaled
+// by 1/d and stored in FP32 on level 0, and f_m = f(u_m) for m >= 1 (Eq. 4).
+// With C'_m = dt sum_j s_{m,j} f(u_j^k) - dt_m f^E(u_m^k) - u_{m+1}^k the
+// implicit terms of b and of (I - a L_h) u_{m+1}^k cancel:
+//   r = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C'_m.
 template <int DIM>
 __global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int reaction) {
   const List& L = *list;
@@ -124,23 +127,9 @@ __global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ 
     const double* Um = I.U + m * N;
     const double up = Um[q];
     const double fe = reaction_term(reaction, up);
-    I.beta[q] = (fma(I.dtm[m], fe, up) + I.C[m * N + q]) * I.inv_d0[m];
+    I.lev[0].b[q] = float((fma(I.dtm[m], fe, up) + I.C[m * N + q]) * I.inv_d0[m]);
     if (m >= 1)
       I.F[m * N + q] = fma(I.nu_h2, fma(-double(2 * DIM), up, nbsum<double, DIM>(Um, i, j, k, n, q)), fe);
-  BATCH_END
-}
-
-// FP64 defect of node m+1's equation, stored in FP32 on level 0.
-template <int DIM>
-__global__ void kb_defect(const Inst* __restrict__ insts, const List* __restrict__ list, int m) {
-  const List& L = *list;
-  BATCH_LOOP(L)
-    const int n = I.n;
-    if (q >= npts<DIM>(n)) continue;
-    int i, j, k;
-    decode<DIM>(q, n, i, j, k);
-    const double* x = I.U + (m + 1) * size_t(npts<DIM>(n));
-    I.lev[0].b[q] = float(fma(I.kappa0[m], nbsum<double, DIM>(x, i, j, k, n, q), I.beta[q]) - x[q]);
   BATCH_END
 }
 
@@ -157,7 +146,7 @@ __global__ void kb_update(const Inst* __restrict__ insts, const List* __restrict
 }
 
 // End of a sweep: f_{M-1}, the max-norm SDC residual (Sec. 3) into
-// rbits[instance] and the next sweep's C_m.
+// rbits[instance] and the next sweep's C'_m.
 template <int DIM>
 __global__ void kb_sweep_end(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction,
                              unsigned long long* __restrict__ rbits) {
@@ -201,7 +190,7 @@ __global__ void kb_sweep_end(const Inst* __restrict__ insts, const List* __restr
       for (int mm = 0; mm < kMaxM - 1; ++mm)
         if (mm < M - 1) {
           const double sf = mm == 0 ? qf[1] : qf[mm + 1] - qf[mm];
-          I.C[mm * N + q] = fma(-I.dtm[mm], fe[mm] + (f[mm + 1] - fe[mm + 1]), sf);
+          I.C[mm * N + q] = fma(-I.dtm[mm], fe[mm], sf) - u[mm + 1];
         }
     }
     // all threads of the block work on the same instance: block max, one atomic

@@ -1,6 +1,7 @@
 // host_util.h -- host-side tables shared by the single-instance context and
-// the batched engine: Gauss-Lobatto collocation tables (Sec. 2, Eq. 2) and the
-// dense inverse of the side-3 multigrid operator.
+// the batched engine: collocation tables (Sec. 2, Eq. 2: Gauss-Lobatto,
+// Gauss-Radau and Gauss-Legendre nodes, Q, full-step weights) and the dense
+// inverse of the side-3 multigrid operator.
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -13,44 +14,82 @@ namespace host {
 // Collocation tables (Sec. 2, Eq. 2).
 // ---------------------------------------------------------------------------
 
-// Number of eigenvalues below x of the symmetric tridiagonal matrix with zero
-// diagonal and squared off-diagonals beta (Sturm sequence count).
-inline int sturm_count(const std::vector<double>& beta, int size, double x) {
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal alpha and squared off-diagonals beta (Sturm sequence count).
+inline int sturm_count(const std::vector<double>& alpha, const std::vector<double>& beta, int size, double x) {
   int count = 0;
-  double q = -x;  // leading principal minor ratio
+  double q = alpha[0] - x;  // leading principal minor ratio
   if (q < 0) ++count;
   for (int k = 1; k < size; ++k) {
     const double prev = (q == 0.0) ? 1e-300 : q;
-    q = -x - beta[k - 1] / prev;
+    q = alpha[k] - x - beta[k - 1] / prev;
     if (q < 0) ++count;
   }
   return count;
 }
 
-// Gauss-Lobatto nodes on [0,1].  The interior nodes are the roots of
-// P'_{M-1}, i.e. of the Jacobi polynomial P^{(1,1)}_{M-2}: eigenvalues of its
-// Jacobi matrix (zero diagonal, squared off-diagonals k(k+2)/((2k+1)(2k+3))),
-// found by bisection on the Sturm count (Golub-Welsch).
-inline void lobatto_nodes(int M, double* tau) {
-  const int size = M - 2;
-  std::vector<double> beta(std::max(size, 1));
-  for (int k = 1; k < size; ++k) beta[k - 1] = double(k) * (k + 2) / ((2.0 * k + 1) * (2.0 * k + 3));
-  tau[0] = 0.0;
-  tau[M - 1] = 1.0;
+// Eigenvalues (ascending) of that matrix, all inside (-1, 1), by bisection on
+// the Sturm count: the Golub-Welsch nodes of the orthogonal polynomial whose
+// recurrence coefficients alpha, beta are given.
+inline void jacobi_matrix_eigs(const std::vector<double>& alpha, const std::vector<double>& beta, int size,
+                               double* out) {
   for (int e = 0; e < size; ++e) {  // e-th smallest eigenvalue
     double lo = -1.0, hi = 1.0;
     for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
       const double mid = 0.5 * (lo + hi);
       if (mid == lo || mid == hi) break;
-      if (sturm_count(beta, size, mid) > e) hi = mid; else lo = mid;
+      if (sturm_count(alpha, beta, size, mid) > e) hi = mid; else lo = mid;
     }
-    tau[e + 1] = 0.5 * (0.5 * (lo + hi) + 1.0);
+    out[e] = 0.5 * (lo + hi);
   }
 }
 
-// Q[m][j] = int_0^{tau_m} l_j(s) ds, computed exactly: l_j expanded in powers
-// of x = 2s - 1 in [-1,1] and integrated term by term.
-inline void q_matrix(int M, const double* tau, double* Q) {
+// Gauss-Lobatto nodes on [0,1].  The interior nodes are the roots of
+// P'_{M-1}, i.e. of the Jacobi polynomial P^{(1,1)}_{M-2}: eigenvalues of its
+// Jacobi matrix (zero diagonal, squared off-diagonals k(k+2)/((2k+1)(2k+3))).
+inline void lobatto_nodes(int M, double* tau) {
+  const int size = M - 2;
+  std::vector<double> alpha(std::max(size, 1), 0.0), beta(std::max(size, 1)), x(std::max(size, 1));
+  for (int k = 1; k < size; ++k) beta[k - 1] = double(k) * (k + 2) / ((2.0 * k + 1) * (2.0 * k + 3));
+  jacobi_matrix_eigs(alpha, beta, size, x.data());
+  tau[0] = 0.0;
+  tau[M - 1] = 1.0;
+  for (int e = 0; e < size; ++e) tau[e + 1] = 0.5 * (x[e] + 1.0);
+}
+
+// Right Gauss-Radau nodes on [0,1] (tau_M = 1).  The other M-1 nodes are the
+// roots of the Jacobi polynomial P^{(1,0)}_{M-1} (weight 1 - x on [-1,1]):
+// diagonal -1/((2k+1)(2k+3)), squared off-diagonals k(k+1)/(2k+1)^2.
+inline void radau_right_nodes(int M, double* tau) {
+  const int size = M - 1;
+  std::vector<double> alpha(size), beta(size), x(size);
+  for (int k = 0; k < size; ++k) alpha[k] = -1.0 / ((2.0 * k + 1) * (2.0 * k + 3));
+  for (int k = 1; k < size; ++k) beta[k - 1] = double(k) * (k + 1) / ((2.0 * k + 1) * (2.0 * k + 1));
+  jacobi_matrix_eigs(alpha, beta, size, x.data());
+  for (int e = 0; e < size; ++e) tau[e] = 0.5 * (x[e] + 1.0);
+  tau[M - 1] = 1.0;
+}
+
+// Gauss-Legendre nodes on [0,1]: roots of P_M, eigenvalues of the Legendre
+// Jacobi matrix (zero diagonal, squared off-diagonals k^2/(4k^2-1)).
+inline void legendre_nodes(int M, double* tau) {
+  std::vector<double> alpha(M, 0.0), beta(M), x(M);
+  for (int k = 1; k < M; ++k) beta[k - 1] = double(k) * k / (4.0 * k * k - 1.0);
+  jacobi_matrix_eigs(alpha, beta, M, x.data());
+  for (int e = 0; e < M; ++e) tau[e] = 0.5 * (x[e] + 1.0);
+}
+
+// Node family kind: 0 Gauss-Lobatto, 1 Gauss-Radau (right), 2 Gauss-Legendre.
+inline void collocation_nodes(int kind, int M, double* tau) {
+  if (kind == 1) radau_right_nodes(M, tau);
+  else if (kind == 2) legendre_nodes(M, tau);
+  else lobatto_nodes(M, tau);
+}
+
+// Integrals of the Lagrange basis over the nodes tau from 0 to each of the
+// points t[0..npts-1]: out[p*M + j] = int_0^{t_p} l_j(s) ds, computed exactly
+// (l_j expanded in powers of x = 2s - 1 in [-1,1], integrated term by term).
+inline void lagrange_integrals(int M, const double* tau, int npts, const double* t, double* out) {
   std::vector<double> x(M);
   for (int i = 0; i < M; ++i) x[i] = 2.0 * tau[i] - 1.0;
   for (int j = 0; j < M; ++j) {
@@ -66,17 +105,26 @@ inline void q_matrix(int M, const double* tau, double* Q) {
       c.swap(nc);
       denom *= (x[j] - x[i]);
     }
-    auto antider = [&](double t) {
-      double acc = 0.0, pw = t;
+    auto antider = [&](double v) {
+      double acc = 0.0, pw = v;
       for (size_t k = 0; k < c.size(); ++k) {
         acc += c[k] * pw / double(k + 1);
-        pw *= t;
+        pw *= v;
       }
       return acc;
     };
     const double base = antider(-1.0);
-    for (int m = 0; m < M; ++m) Q[m * M + j] = 0.5 * (antider(x[m]) - base) / denom;
+    for (int p = 0; p < npts; ++p) out[p * M + j] = 0.5 * (antider(2.0 * t[p] - 1.0) - base) / denom;
   }
+}
+
+// Q[m][j] = int_0^{tau_m} l_j(s) ds.
+inline void q_matrix(int M, const double* tau, double* Q) { lagrange_integrals(M, tau, M, tau, Q); }
+
+// Full-step weights w_j = int_0^1 l_j(s) ds.
+inline void end_weights(int M, const double* tau, double* w) {
+  const double one = 1.0;
+  lagrange_integrals(M, tau, 1, &one, w);
 }
 
 // Inverse of the dense matrix of H = I - a L_h on a side-3 grid (Gauss-Jordan

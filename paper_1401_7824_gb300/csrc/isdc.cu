@@ -8,6 +8,8 @@
 //                     L V-cycles on (I - dt_m nu L_h) u_{m+1} = b, from u_{m+1}^k
 //     f_{M-1}, SDC residual R, next C_m                   (k_sweep_end)
 //   until R < tol (or a fixed sweep count); u <- u_{M-1} (tau = 1).
+// FP32 V-cycles with a fixed count form the FP32 defect of u_{m+1}^k directly
+// (k_rhs_defect, sweep constants C'_m): b itself is never stored.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -84,11 +86,14 @@ struct isdc_ctx {
   isdc_options opt{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  int node_kind = 0;  // isdc_node_type
+  int P = 0, off = 0;  // points of a sweep (t_0 and the nodes) and P - M; node j is point j + off
   double tau[kMaxM] = {}, Q[kMaxM * kMaxM] = {}, S[kMaxM * kMaxM] = {};
   SweepTables tables{};
-  double* U = nullptr;  // M node arrays, node-major
-  double* F = nullptr;  // f(u_m), M arrays
-  double* C = nullptr;  // sweep constants, M-1 arrays
+  EndWeights ends{};   // dt * full-step weights (Gauss-Legendre end quadrature)
+  double* U = nullptr;  // P point arrays (t_0, then the nodes), point-major
+  double* F = nullptr;  // f(u_p), P arrays
+  double* C = nullptr;  // sweep constants, P-1 arrays
   double* b = nullptr;  // right-hand side of the current node solve
   double* u_dev = nullptr;  // device copy of u for isdc_step_host
   Hier<double> h64;
@@ -107,6 +112,7 @@ struct isdc_ctx {
   int last_sweeps = 0, hist_count = 0;
   long long last_vcycles = 0;
   int nodes_pending = 0;
+  int cprime = 0;  // this step keeps the sweep constants in the defect form C'_m (k_rhs_defect)
   int spare_slot = 0;  // Ainv slot for isdc_vcycles
   Profiler prof;
   // one SDC sweep (fixed V-cycle count) captured as a CUDA graph
@@ -116,6 +122,8 @@ struct isdc_ctx {
   unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
   // z-planes per thread of the fine-level red-black smoothers (autotuned)
   int zb64 = 1, zb32 = 1;
+  int tb_depth = 0, tb_zc = 32;  // temporal blocking of the split FP32 fine level (sweeps per pass, planes per block)
+  float* sp_xb = nullptr;        // second black array of the split level (blocked passes ping-pong into it)
   int zbl[kMaxLevels] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // per grid-wide level (natural layout)
   char err[512] = "";
 };
@@ -276,7 +284,7 @@ isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   size_t sm = 0;
   for (int q = H.lb; q < H.nlev; ++q) sm += 3 * H.npts[q] * sizeof(T);
   H.bottom_smem = sm;
-  const size_t ainv = size_t(ctx->M) * (ctx->dim == 2 ? 81 : 729) * sizeof(T);
+  const size_t ainv = size_t(ctx->P) * (ctx->dim == 2 ? 81 : 729) * sizeof(T);
   CUDA_TRY(ctx, cudaMalloc(&H.Ainv, ainv));
   return ISDC_OK;
 }
@@ -459,45 +467,88 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
   return ISDC_OK;
 }
 
+// One blocked pass of `depth` red-black sweeps on the split fine level (3D):
+// black read from xb_in, red written in place, black written to xb_out.
+inline void launch_rbgs_tb(cudaStream_t st, int depth, int zc, int s, float kappa, const float* xb_in, float* xr,
+                           float* xb_out, const float* br, const float* bb, bool zero) {
+  const dim3 g(unsigned(((s + 1) / 2 + kTbX - 1) / kTbX), unsigned((s + kTbY - 1) / kTbY), unsigned((s + zc - 1) / zc));
+  if (depth == 1)
+    k_rbgs_split_tb<2><<<g, kTbThreads, TbShape<2>::smem_bytes, st>>>(s, kappa, xb_in, xr, xb_out, br, bb,
+                                                                       zero ? 1 : 0, zc);
+  else
+    k_rbgs_split_tb<4><<<g, kTbThreads, TbShape<4>::smem_bytes, st>>>(s, kappa, xb_in, xr, xb_out, br, bb,
+                                                                       zero ? 1 : 0, zc);
+}
+
+// nsw red-black sweeps on the split fine level (the first from a zero guess
+// if `zero`).  *xb is the array holding the black values; blocked passes
+// move them to the other black array.
+template <int DIM>
+isdc_status smooth_split(isdc_ctx* ctx, float kappa, int nsw, bool zero, float** xb) {
+  const int s = ctx->n;
+  const size_t hn = ctx->hn;
+  float *x0 = ctx->sp_x, *b0 = ctx->sp_b, *b1 = ctx->sp_b + hn;
+  const double Np = double(ctx->N);
+  const double pass_ops = (nb_ops(DIM) + 1.0) * 0.5 * Np;
+  if (DIM == 3 && ctx->tb_depth > 0) {
+    while (nsw > 0) {
+      const int d = std::min(nsw, ctx->tb_depth);
+      float* xo = *xb == ctx->sp_xb ? ctx->sp_x + hn : ctx->sp_xb;
+      {
+        ProfScope ps(ctx, PC_SMOOTH0, (zero ? 2.0 : 2.5) * Np * 4, (2.0 * d - (zero ? 1.0 : 0.0)) * pass_ops, false);
+        launch_rbgs_tb(ctx->stream, d, ctx->tb_zc, s, kappa, *xb, x0, xo, b0, b1, zero);
+      }
+      LAUNCH_CHECK(ctx);
+      *xb = xo;
+      zero = false;
+      nsw -= d;
+    }
+    return ISDC_OK;
+  }
+  const dim3 gz = rb_grid(DIM, s, ctx->zb32);
+  for (int it = 0; it < nsw; ++it, zero = false) {
+    {
+      ProfScope ps(ctx, PC_SMOOTH0, (zero ? 1.0 : 1.5) * Np * 4, zero ? 0.0 : pass_ops, false);
+      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, *xb, b0, zero ? 1 : 0, ctx->zb32);
+    }
+    LAUNCH_CHECK(ctx);
+    {
+      ProfScope ps(ctx, PC_SMOOTH0, 1.5 * Np * 4, pass_ops, false);
+      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 1, *xb, x0, b1, 0, ctx->zb32);
+    }
+    LAUNCH_CHECK(ctx);
+  }
+  return ISDC_OK;
+}
+
 // FP32 V-cycles with red-black smoothing whose fine level is in the
 // colour-split layout (levels below it are natural): defect, n_cycles
 // V-cycles on the error equation, update.  Needs nu1, nu2 >= 1.
 template <int DIM>
-isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles) {
+isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles,
+                             bool defect_ready) {
   const int s = ctx->n, sc = ctx->h32.side[1];
   Hier<float>& H = ctx->h32;
   const size_t hn = ctx->hn;
-  float *x0 = ctx->sp_x, *x1 = ctx->sp_x + hn, *b0 = ctx->sp_b, *b1 = ctx->sp_b + hn;
+  float *x0 = ctx->sp_x, *xb = ctx->sp_x + hn, *b0 = ctx->sp_b, *b1 = ctx->sp_b + hn;
   const LevelCoef lf = level_coef(DIM, s, a);
   const float kappa = float(lf.kappa);
   const float ws = float(lf.d / (level_coef(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0)));
   const double Np = double(ctx->N), Nc = double(H.npts[1]);
-  const dim3 g = rb_grid(DIM, s), gz = rb_grid(DIM, s, ctx->zb32);
+  const dim3 g = rb_grid(DIM, s);
   isdc_status st;
-  {
-    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
-    k_defect_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, lf.kappa, x, beta, b0, b1);
+  if (!defect_ready) {
+    {
+      ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
+      k_defect_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, lf.kappa, x, beta, b0, b1);
+    }
+    LAUNCH_CHECK(ctx);
   }
-  LAUNCH_CHECK(ctx);
-  auto sweep = [&](bool zero) -> isdc_status {
-    {
-      ProfScope ps(ctx, PC_SMOOTH0, (zero ? 1.0 : 1.5) * Np * 4, (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, false);
-      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, x1, b0, zero ? 1 : 0, ctx->zb32);
-    }
-    LAUNCH_CHECK(ctx);
-    {
-      ProfScope ps(ctx, PC_SMOOTH0, 1.5 * Np * 4, (nb_ops(DIM) + 1.0) * 0.5 * Np, false);
-      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 1, x1, x0, b1, 0, ctx->zb32);
-    }
-    LAUNCH_CHECK(ctx);
-    return ISDC_OK;
-  };
   for (int c = 0; c < n_cycles; ++c) {
-    for (int it = 0; it < ctx->opt.nu1; ++it)
-      if ((st = sweep(c == 0 && it == 0)) != ISDC_OK) return st;
+    if ((st = smooth_split<DIM>(ctx, kappa, ctx->opt.nu1, c == 0, &xb)) != ISDC_OK) return st;
     {
       ProfScope ps(ctx, PC_RESIDUAL0, 2.0 * Np * 4, (nb_ops(DIM) + 2.0) * 0.5 * Np, false);
-      k_residual_red_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, x0, x1, b0, ctx->sp_r);
+      k_residual_red_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, x0, xb, b0, ctx->sp_r);
     }
     LAUNCH_CHECK(ctx);
     {
@@ -508,15 +559,14 @@ isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const
     if ((st = vcycle<float, DIM>(ctx, H, slot, a, H.x[1], H.b[1], true, 1)) != ISDC_OK) return st;
     {
       ProfScope ps(ctx, PC_PROLONG0, (Np + Nc) * 4, (DIM == 2 ? 1.25 : 1.75) * Np, false);
-      k_prolong_black_split<DIM><<<pt_grid(DIM, sc + 1), kBlock, 0, ctx->stream>>>(sc, H.x[1], x0, x1);
+      k_prolong_black_split<DIM><<<pt_grid(DIM, sc + 1), kBlock, 0, ctx->stream>>>(sc, H.x[1], x0, xb);
     }
     LAUNCH_CHECK(ctx);
-    for (int it = 0; it < ctx->opt.nu2; ++it)
-      if ((st = sweep(false)) != ISDC_OK) return st;
+    if ((st = smooth_split<DIM>(ctx, kappa, ctx->opt.nu2, false, &xb)) != ISDC_OK) return st;
   }
   {
     ProfScope ps(ctx, PC_UPDATE, 20.0 * Np, 1.0 * Np, true);
-    k_update_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, x, x0, x1);
+    k_update_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, x, x0, xb);
   }
   LAUNCH_CHECK(ctx);
   return ISDC_OK;
@@ -526,9 +576,11 @@ isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const
 // array, beta = b/d.  FP64 mode: V-cycles on x.  FP32 mode (defect
 // correction): the fine-level residual of the node equation in FP64, rounded
 // to FP32, n_cycles FP32 V-cycles on the error equation from e = 0, and one
-// FP64 update x += e.
+// FP64 update x += e.  defect_ready: the scaled FP32 defect is already in the
+// fine level's rhs (k_rhs_defect), beta is not read.
 template <int DIM>
-isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles) {
+isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const double* beta, int n_cycles,
+                       bool defect_ready = false) {
   isdc_status st;
   if (!ctx->opt.vcycle_fp32) {
     for (int c = 0; c < n_cycles; ++c)
@@ -536,15 +588,17 @@ isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const doubl
     return ISDC_OK;
   }
   if (n_cycles <= 0) return ISDC_OK;
-  if (ctx->sp_x) return node_solve_split<DIM>(ctx, slot, a, x, beta, n_cycles);
+  if (ctx->sp_x) return node_solve_split<DIM>(ctx, slot, a, x, beta, n_cycles, defect_ready);
   const int s = ctx->n;
   Hier<float>& H = ctx->h32;
   const double Np = double(ctx->N);
-  {
-    ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
-    k_defect<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, level_coef(DIM, s, a).kappa, x, beta, H.b[0]);
+  if (!defect_ready) {
+    {
+      ProfScope ps(ctx, PC_DEFECT, 20.0 * Np, (nb_ops(DIM) + 2.0) * Np, true);
+      k_defect<DIM><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, level_coef(DIM, s, a).kappa, x, beta, H.b[0]);
+    }
+    LAUNCH_CHECK(ctx);
   }
-  LAUNCH_CHECK(ctx);
   for (int c = 0; c < n_cycles; ++c)
     if ((st = vcycle<float, DIM>(ctx, H, slot, a, H.x[0], H.b[0], c == 0)) != ISDC_OK) return st;
   {
@@ -584,29 +638,56 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   {
-    const double M = ctx->M, Np = double(ctx->N);
-    // f_{M-1}: nb+2; f^E: 2M; dt Q f: M(M-1); residual: 2(M-1); C: 4(M-1) - 1
-    ProfScope ps(ctx, PC_SWEEP_END, (3.0 * M - 1.0) * 8.0 * Np,
-                 (nb_ops(DIM) + 2.0 + 2.0 * M + M * (M - 1.0) + 6.0 * (M - 1.0) - 1.0) * Np, true);
-    k_sweep_end<DIM><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->N, nu_h2, ctx->opt.reaction,
-                                                                      ctx->tables, ctx->U, ctx->F, ctx->C,
-                                                                      ctx->d_scal);
+    const double M = ctx->M, P = ctx->P, Np = double(ctx->N);
+    // reads P u, M-1 f; writes f_{P-1} and P-1 C.  Ops: f_{P-1}: nb+2; f^E: 2P;
+    // dt Q f: (P-1)M; residual: 2(P-1); C: 4(P-1) - 1 (C': 3(P-1) - 1)
+    ProfScope ps(ctx, PC_SWEEP_END, (2.0 * P + M - 1.0) * 8.0 * Np,
+                 (nb_ops(DIM) + 2.0 + 2.0 * P + (P - 1.0) * M + (ctx->cprime ? 5.0 : 6.0) * (P - 1.0) - 1.0) * Np,
+                 true);
+    if (ctx->off)
+      k_sweep_end<DIM, 1><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
+          ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
+    else
+      k_sweep_end<DIM, 0><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
+          ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
   }
   LAUNCH_CHECK(ctx);
   return ISDC_OK;
 }
 
-// One SDC sweep (Sec. 2, Eq. 4): the M-1 node solves and the sweep end
-// (f_{M-1}, SDC residual, next C_m).  *vcycles accumulates the V-cycles spent.
+// One SDC sweep (Sec. 2, Eq. 4): the P-1 node solves (M-1 for Gauss-Lobatto,
+// M otherwise) and the sweep end (f at the last point, SDC residual, next C_m).
+// *vcycles accumulates the V-cycles spent.
 template <int DIM>
 isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
-  const int n = ctx->n, M = ctx->M;
+  const int n = ctx->n, P = ctx->P;
   const size_t N = ctx->N;
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   isdc_status st;
-  for (int m = 0; m < M - 1; ++m) {
+  for (int m = 0; m < P - 1; ++m) {
     const double dtm = ctx->tables.dtm[m];
     const double inv_d0 = 1.0 / level_coef(DIM, n, dtm * ctx->nu).d;
+    double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
+    const double a = dtm * ctx->nu;
+    if (ctx->cprime) {  // FP32 V-cycles, fixed count: rhs and defect in one pass
+      {
+        ProfScope ps(ctx, PC_RHS, (m >= 1 ? 28.0 : 20.0) * double(N), (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N),
+                     true);
+        double* Fm = m >= 1 ? ctx->F + m * N : nullptr;
+        if (ctx->sp_x)
+          k_rhs_defect_split<DIM><<<rb_grid(DIM, n), kBlock, 0, ctx->stream>>>(
+              n, nu_h2, ctx->opt.reaction, dtm, inv_d0, ctx->U + m * N, ctx->C + m * N, Fm, ctx->sp_b,
+              ctx->sp_b + ctx->hn);
+        else
+          k_rhs_defect<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
+                                                                         ctx->U + m * N, ctx->C + m * N, Fm,
+                                                                         ctx->h32.b[0]);
+      }
+      LAUNCH_CHECK(ctx);
+      if ((st = node_solve<DIM>(ctx, m, a, x, nullptr, n_vcycles, true)) != ISDC_OK) return st;
+      *vcycles += n_vcycles;
+      continue;
+    }
     {
       ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
                    (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
@@ -616,8 +697,6 @@ isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
                                                               m >= 1 ? ctx->F + m * N : nullptr);
     }
     LAUNCH_CHECK(ctx);
-    double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
-    const double a = dtm * ctx->nu;
     if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
       if ((st = node_solve<DIM>(ctx, m, a, x, ctx->b, n_vcycles)) != ISDC_OK) return st;
       *vcycles += n_vcycles;
@@ -685,12 +764,15 @@ isdc_status capture_sweep(isdc_ctx* ctx, int n_vcycles) {
 
 template <int DIM>
 isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
-  const int n = ctx->n, M = ctx->M;
+  const int n = ctx->n, P = ctx->P;
   const size_t N = ctx->N;
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   isdc_status st;
   if (ctx->nodes_pending) {
-    for (int m = 0; m < M; ++m) {
+    // resume: the nodes were set; t_0 (not a node unless Gauss-Lobatto) is u
+    if (ctx->off)
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int m = ctx->off; m < P; ++m) {
       {
         ProfScope ps(ctx, PC_EVAL_F, 16.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
         k_eval_f<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, ctx->U + m * N,
@@ -701,12 +783,13 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
     ctx->nodes_pending = 0;
   } else {
     {
-      ProfScope ps(ctx, PC_SPREAD, (1.0 + 2.0 * M) * 8.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
-      k_spread<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, ctx->opt.reaction, M, u, ctx->U,
+      ProfScope ps(ctx, PC_SPREAD, (1.0 + 2.0 * P) * 8.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
+      k_spread<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, ctx->opt.reaction, P, u, ctx->U,
                                                                  ctx->F);
     }
     LAUNCH_CHECK(ctx);
   }
+  ctx->cprime = ctx->opt.vcycle_fp32 && n_vcycles > 0 && !ctx->opt.vcycle_cap;
   if ((st = sweep_end<DIM>(ctx)) != ISDC_OK) return st;  // C_m of the first sweep
 
   const bool until_tol = n_sweeps <= 0;
@@ -723,7 +806,7 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   for (;;) {
     if (graph) {
       CUDA_TRY(ctx, cudaGraphLaunch(ctx->sweep_graph, ctx->stream));
-      vcycles += (long long)n_vcycles * (M - 1);
+      vcycles += (long long)n_vcycles * (P - 1);
       if (ctx->prof.on) {  // read the replay's event nodes before the next replay re-records them
         CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         prof_graph_replayed(ctx);
@@ -757,7 +840,15 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   }
   CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 ctx->stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(u, ctx->U + (M - 1) * N, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->node_kind == ISDC_NODES_GAUSS_LEGENDRE) {
+    // tau_M < 1: the step ends with the full-step quadrature of the collocation rule
+    ProfScope ps(ctx, PC_SPREAD, (ctx->M + 2.0) * 8.0 * double(N), 2.0 * ctx->M * double(N), true);
+    k_gauss_end<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, ctx->ends, ctx->U, ctx->F, u);
+  } else {
+    CUDA_TRY(ctx, cudaMemcpyAsync(u, ctx->U + (P - 1) * N, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  }
+  LAUNCH_CHECK(ctx);
   ctx->last_sweeps = k;
   ctx->last_vcycles = vcycles;
   return result;
@@ -824,6 +915,38 @@ isdc_status tune_levels(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cu
   return ISDC_OK;
 }
 
+// Temporal blocking of the split FP32 fine level (3D): time max(nu1, nu2)
+// red-black sweeps as separate colour passes (with the planes per thread just
+// chosen) and as blocked passes of 1 and 2 sweeps with 16, 32, 64 and 128
+// planes per block, on the context's own arrays; keep the fastest.
+isdc_status tune_blocking(isdc_ctx* ctx, cudaEvent_t e0, cudaEvent_t e1) {
+  struct Cand { int depth, zc; };
+  const Cand cand[9] = {{0, 32}, {1, 16}, {1, 32}, {1, 64}, {1, 128}, {2, 16}, {2, 32}, {2, 64}, {2, 128}};
+  const int nsw = std::max(ctx->opt.nu1, ctx->opt.nu2);
+  float best = 1e30f;
+  Cand pick = cand[0];
+  for (int rep = 0; rep < 2; ++rep)  // the first round warms up
+    for (const Cand& c : cand) {
+      ctx->tb_depth = c.depth;
+      ctx->tb_zc = c.zc;
+      float* xb = ctx->sp_x + ctx->hn;
+      CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+      isdc_status st = smooth_split<3>(ctx, 0.1f, nsw, false, &xb);
+      if (st != ISDC_OK) return st;
+      CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
+      CUDA_TRY(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 && ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+  ctx->tb_depth = pick.depth;
+  ctx->tb_zc = pick.zc;
+  return ISDC_OK;
+}
+
 isdc_status tune_smoother(isdc_ctx* ctx) {
   if (ctx->dim != 3 || ctx->opt.smoother != ISDC_SMOOTHER_RBGS) return ISDC_OK;
   cudaEvent_t e0, e1;
@@ -832,6 +955,10 @@ isdc_status tune_smoother(isdc_ctx* ctx) {
   isdc_status st = ctx->opt.vcycle_fp32
                        ? tune_levels<float>(ctx, ctx->h32, ctx->h32.x[0], ctx->h32.b[0], ctx->sp_x != nullptr, e0, e1)
                        : tune_levels<double>(ctx, ctx->h64, ctx->U, ctx->b, false, e0, e1);
+  if (st == ISDC_OK && ctx->sp_xb) {
+    if (ctx->opt.temporal_blocking >= 0) ctx->tb_depth = ctx->opt.temporal_blocking;
+    else st = tune_blocking(ctx, e0, e1);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
@@ -856,24 +983,30 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->mg_max_cycles = 50;
   opt->vcycle_cap = 0;
   opt->use_graphs = 1;
+  opt->temporal_blocking = -1;
   opt->stream = nullptr;
   return ISDC_OK;
 }
 
 ISDC_API isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double* tau, double* Q, double* S) {
-  if (nodes != ISDC_NODES_GAUSS_LOBATTO) {
-    snprintf(g_create_error, sizeof g_create_error, "only Gauss-Lobatto nodes are implemented");
-    return ISDC_ERR_UNSUPPORTED;
+  if (nodes != ISDC_NODES_GAUSS_LOBATTO && nodes != ISDC_NODES_RADAU_RIGHT && nodes != ISDC_NODES_GAUSS_LEGENDRE) {
+    snprintf(g_create_error, sizeof g_create_error, "unknown node type %d", int(nodes));
+    return ISDC_ERR_INVALID_ARG;
   }
   if (M < 2 || M > kMaxM || !tau || !Q) {
     snprintf(g_create_error, sizeof g_create_error, "M must be in [2, %d] and tau, Q non-NULL", kMaxM);
     return ISDC_ERR_INVALID_ARG;
   }
-  lobatto_nodes(M, tau);
+  collocation_nodes(int(nodes), M, tau);
   q_matrix(M, tau, Q);
-  if (S)
-    for (int m = 0; m < M - 1; ++m)
-      for (int j = 0; j < M; ++j) S[m * M + j] = Q[(m + 1) * M + j] - Q[m * M + j];
+  if (S) {  // point to point: rows of Q, preceded by a zero row for t_0 unless t_0 is node 1
+    const int off = nodes == ISDC_NODES_GAUSS_LOBATTO ? 0 : 1;
+    for (int m = 0; m < M - 1 + off; ++m)
+      for (int j = 0; j < M; ++j) {
+        const double lo = m - off >= 0 ? Q[(m - off) * M + j] : 0.0;
+        S[m * M + j] = Q[(m + 1 - off) * M + j] - lo;
+      }
+  }
   return ISDC_OK;
 }
 
@@ -888,6 +1021,7 @@ ISDC_API void isdc_destroy(isdc_ctx* ctx) {
   free_hier(ctx->h64, false);
   free_hier(ctx->h32, true);
   cudaFree(ctx->sp_x);
+  cudaFree(ctx->sp_xb);
   cudaFree(ctx->sp_b);
   cudaFree(ctx->sp_r);
   cudaFree(ctx->d_scal);
@@ -919,7 +1053,8 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   if (n < 3 || ((n + 1) & n) != 0) return fail(nullptr, ISDC_ERR_INVALID_ARG, "side must be 2^j - 1 with j >= 2 (got %lld)", (long long)n);
   if ((ndim == 2 && n > 46339) || (ndim == 3 && n > 1289))
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "grid too large for 32-bit point indices");
-  if (nodes != ISDC_NODES_GAUSS_LOBATTO) return fail(nullptr, ISDC_ERR_UNSUPPORTED, "only Gauss-Lobatto nodes are implemented");
+  if (nodes != ISDC_NODES_GAUSS_LOBATTO && nodes != ISDC_NODES_RADAU_RIGHT && nodes != ISDC_NODES_GAUSS_LEGENDRE)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown node type %d", int(nodes));
   if (M < 2 || M > kMaxM) return fail(nullptr, ISDC_ERR_INVALID_ARG, "M must be in [2, %d] (got %d)", kMaxM, M);
   if (!(nu > 0) || !std::isfinite(nu) || !(dt > 0) || !std::isfinite(dt))
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "nu and dt must be positive and finite");
@@ -933,12 +1068,17 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown reaction %d", o.reaction);
   if (o.max_sweeps < 1 || o.max_sweeps > 100000 || o.mg_max_cycles < 1)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps and mg_max_cycles must be >= 1");
+  if (o.temporal_blocking < -1 || o.temporal_blocking > 2)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "temporal_blocking must be -1, 0, 1 or 2");
 
   isdc_ctx* ctx = new isdc_ctx();
   ctx->dim = ndim;
   ctx->n = int(n);
   ctx->N = pow_dim(ndim, size_t(n));
   ctx->M = M;
+  ctx->node_kind = int(nodes);
+  ctx->off = nodes == ISDC_NODES_GAUSS_LOBATTO ? 0 : 1;
+  ctx->P = M + ctx->off;
   ctx->nu = nu;
   ctx->dt = dt;
   ctx->h = 1.0 / double(n + 1);
@@ -958,16 +1098,20 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
     }
     ctx->own_stream = true;
   }
-  lobatto_nodes(M, ctx->tau);
-  q_matrix(M, ctx->tau, ctx->Q);
-  for (int m = 0; m < M - 1; ++m)
-    for (int j = 0; j < M; ++j) ctx->S[m * M + j] = ctx->Q[(m + 1) * M + j] - ctx->Q[m * M + j];
+  isdc_collocation_tables(nodes, M, ctx->tau, ctx->Q, ctx->S);
+  const int P = ctx->P, off = ctx->off;
+  double tpt[kMaxP];  // t_p - T_n over dt: 0, then the nodes
+  tpt[0] = 0.0;
+  for (int m = 0; m < M; ++m) tpt[m + off] = ctx->tau[m];
   ctx->tables.M = M;
-  for (int m = 0; m < M; ++m)
-    for (int j = 0; j < M; ++j) {
-      ctx->tables.dtQ[m][j] = dt * ctx->Q[m * M + j];
-    }
-  for (int m = 0; m < M - 1; ++m) ctx->tables.dtm[m] = dt * (ctx->tau[m + 1] - ctx->tau[m]);
+  ctx->tables.P = P;
+  for (int p = 0; p < P; ++p)
+    for (int j = 0; j < M; ++j) ctx->tables.dtQ[p][j] = p - off >= 0 ? dt * ctx->Q[(p - off) * M + j] : 0.0;
+  for (int m = 0; m < P - 1; ++m) ctx->tables.dtm[m] = dt * (tpt[m + 1] - tpt[m]);
+  double w[kMaxM];
+  end_weights(M, ctx->tau, w);
+  ctx->ends.M = M;
+  for (int j = 0; j < M; ++j) ctx->ends.dtw[j] = dt * w[j];
 
   const size_t N = ctx->N;
   isdc_status st;
@@ -980,9 +1124,9 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       return bail(s_);                                        \
     }                                                         \
   } while (0)
-  CREATE_TRY(cudaMalloc(&ctx->U, size_t(M) * N * sizeof(double)));
-  CREATE_TRY(cudaMalloc(&ctx->F, size_t(M) * N * sizeof(double)));
-  CREATE_TRY(cudaMalloc(&ctx->C, size_t(M - 1) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->U, size_t(P) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->F, size_t(P) * N * sizeof(double)));
+  CREATE_TRY(cudaMalloc(&ctx->C, size_t(P - 1) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->b, N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->d_scal, 4 * sizeof(unsigned long long)));
   CREATE_TRY(cudaMemset(ctx->d_scal, 0, 4 * sizeof(unsigned long long)));
@@ -1000,17 +1144,26 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       CREATE_TRY(cudaMemset(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float)));
       CREATE_TRY(cudaMemset(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float)));
       CREATE_TRY(cudaMemset(ctx->sp_r, 0, ctx->hn * sizeof(float)));
+      if (ndim == 3) {
+        CREATE_TRY(cudaMalloc(&ctx->sp_xb, ctx->hn * sizeof(float)));
+        CREATE_TRY(cudaMemset(ctx->sp_xb, 0, ctx->hn * sizeof(float)));
+        // the blocked passes stage their planes in more than the default 48 KB
+        CREATE_TRY(cudaFuncSetAttribute(k_rbgs_split_tb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(TbShape<2>::smem_bytes)));
+        CREATE_TRY(cudaFuncSetAttribute(k_rbgs_split_tb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(TbShape<4>::smem_bytes)));
+      }
     }
     if (ndim == 2) configure_bottom<float, 2>(ctx->h32); else configure_bottom<float, 3>(ctx->h32);
-    for (int m = 0; m < M - 1; ++m)
+    for (int m = 0; m < P - 1; ++m)
       if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   } else {
     if ((st = alloc_hier(ctx, ctx->h64, false)) != ISDC_OK) return bail(st);
     if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
-    for (int m = 0; m < M - 1; ++m)
+    for (int m = 0; m < P - 1; ++m)
       if ((st = upload_ainv(ctx, ctx->h64, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   }
-  ctx->spare_slot = M - 1;
+  ctx->spare_slot = P - 1;
   if ((st = tune_smoother(ctx)) != ISDC_OK) return bail(st);
   CREATE_TRY(cudaGetLastError());
 #undef CREATE_TRY
@@ -1073,15 +1226,15 @@ ISDC_API isdc_status isdc_set_record_history(isdc_ctx* ctx, int record) {
 ISDC_API isdc_status isdc_get_nodes(const isdc_ctx* cctx, double* dst) {
   isdc_ctx* ctx = const_cast<isdc_ctx*>(cctx);
   if (!ctx || !dst) return ISDC_ERR_INVALID_ARG;
-  CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->U, size_t(ctx->M) * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
-                                ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->U + size_t(ctx->off) * ctx->N, size_t(ctx->M) * ctx->N * sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->stream));
   return ISDC_OK;
 }
 
 ISDC_API isdc_status isdc_set_nodes(isdc_ctx* ctx, const double* src) {
   if (!ctx || !src) return ISDC_ERR_INVALID_ARG;
-  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, src, size_t(ctx->M) * ctx->N * sizeof(double), cudaMemcpyDeviceToDevice,
-                                ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U + size_t(ctx->off) * ctx->N, src, size_t(ctx->M) * ctx->N * sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->nodes_pending = 1;
   return ISDC_OK;
 }
@@ -1141,10 +1294,12 @@ ISDC_API isdc_status isdc_profile_read(isdc_ctx* ctx, isdc_kernel_stat* out, int
   return ISDC_OK;
 }
 
-ISDC_API isdc_status isdc_tuning(const isdc_ctx* ctx, int* zb_fp64, int* zb_fp32) {
+ISDC_API isdc_status isdc_tuning(const isdc_ctx* ctx, int* zb_fp64, int* zb_fp32, int* tb_depth, int* tb_planes) {
   if (!ctx) return ISDC_ERR_INVALID_ARG;
   if (zb_fp64) *zb_fp64 = ctx->zb64;
   if (zb_fp32) *zb_fp32 = ctx->zb32;
+  if (tb_depth) *tb_depth = ctx->tb_depth;
+  if (tb_planes) *tb_planes = ctx->tb_zc;
   return ISDC_OK;
 }
 

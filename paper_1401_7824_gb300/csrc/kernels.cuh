@@ -357,6 +357,203 @@ __global__ void __launch_bounds__(kBX* kBY)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Temporal blocking (3D, split layout): S/2 complete red-black sweeps in one
+// pass over HBM.  A block owns a tile of kTbX slots x kTbY rows and a chunk
+// of zc planes and walks z as a wavefront of S colour stages: at iteration
+// `it` stage s (red for even s, black for odd s) updates plane it - s from the
+// three planes of stage s-1 around it.  Stage s is computed on the tile plus
+// a ring of S-1-s slots / rows (and S-1-s extra planes at each end of the
+// chunk), so the last stage needs nothing from other blocks; the halo work is
+// recomputed.  Only the black input and the right-hand sides are read from
+// HBM (a Gauss-Seidel red update never reads the old red values) and only the
+// last red and black stages are written: S/2 sweeps move 2.5 values per point
+// instead of 3 per sweep.  The black result goes to a second array
+// (xb_out != xb_in), because other blocks still read the old black values in
+// their halos.  The global loads of iteration it+1 (black input plane it+2,
+// right-hand-side planes it+1) are issued into registers before the stages of
+// iteration it run, so the stages work out of shared memory only.  Every
+// stage does the same FP32 operations in the same order as k_rbgs_split, so
+// the result is bitwise that of S separate colour passes.
+// ---------------------------------------------------------------------------
+constexpr int kTbX = 32, kTbY = 16, kTbThreads = kTbX * kTbY;
+
+template <int S>
+struct TbShape {
+  static constexpr int WX = kTbX + 2 * S, WY = kTbY + 2 * S, PL = WX * WY;
+  static constexpr int LOADS = (PL + kTbThreads - 1) / kTbThreads;  // plane elements per thread
+  // black input (3 planes), stages 0..S-2 (3 planes each), red and black rhs (4 planes each)
+  static constexpr int BUF_IN = 0, BUF_STAGE = 3 * PL, BUF_BR = BUF_STAGE + 3 * (S - 1) * PL, BUF_BB = BUF_BR + 4 * PL;
+  static constexpr size_t smem_bytes = size_t(BUF_BB + 4 * PL) * sizeof(float);
+  // slot 1 of the kTbThreads threads covers every point of the rings 1..S-1
+  static constexpr int RING_POINTS = (kTbX + 2 * (S - 1)) * (kTbY + 2 * (S - 1)) - kTbX * kTbY;
+  static_assert(RING_POINTS <= kTbThreads, "rings 1..S-1 need more than one point per thread");
+};
+
+__device__ __forceinline__ int tb_zslot(int z, int S) { return (z + 3 * (S + 2)) % 3; }
+__device__ __forceinline__ int tb_bslot(int z) { return (z + 1024) & 3; }
+
+// A point of the shared-memory plane owned by a thread: for the stages, slot 0
+// is tile point t and slot 1 the t-th point of the rings 1..S-1 around the
+// tile, ring by ring (a stage with ring r uses slot 1 only where dist <= r, so
+// the work stays spread over all threads); for the plane loads, element q of
+// the whole buffer.  Everything but z is fixed for the whole pass: in plane z
+// the colour-c point of the slot has x offset i0 = ((c + z + 1) & 1) ^ ypar and
+// lies in the grid iff ok[i0].
+struct TbSlot {
+  int e;        // shared-memory index in a plane (-1: unused)
+  int g;        // h + H*y: global slot offset within a plane
+  int ypar;     // y & 1
+  int dist;     // ring (0 = tile); larger than any ring when unused
+  bool ok0, ok1;  // inside the grid with i0 = 0 / 1
+};
+
+template <int S>
+__device__ __forceinline__ TbSlot tb_at(int hs, int ys, int dist, int n, int H, int h0, int y0) {
+  TbSlot t;
+  const int h = h0 - S + hs, y = y0 - S + ys;
+  const bool inxy = h >= 0 && y >= 0 && y < n;
+  t.e = ys * TbShape<S>::WX + hs;
+  t.g = h + H * y;
+  t.ypar = y & 1;
+  t.dist = dist;
+  t.ok0 = inxy && 2 * h < n;
+  t.ok1 = inxy && 2 * h + 1 < n;
+  return t;
+}
+
+template <int S>
+__device__ __forceinline__ TbSlot tb_slot(int q, int ring, int n, int H, int h0, int y0) {
+  if (ring == 0) return tb_at<S>(S + q % kTbX, S + q / kTbX, 0, n, H, h0, y0);
+  for (int d = 1; d < S; ++d) {
+    const int Wd = kTbX + 2 * d, Hd = kTbY + 2 * d, c = 2 * Wd + 2 * (Hd - 2);
+    if (q < c) {
+      if (q < Wd) return tb_at<S>(S - d + q, S - d, d, n, H, h0, y0);
+      if (q < 2 * Wd) return tb_at<S>(S - d + (q - Wd), S + kTbY + d - 1, d, n, H, h0, y0);
+      const int r = q - 2 * Wd;
+      return tb_at<S>((r & 1) ? S + kTbX + d - 1 : S - d, S - d + 1 + (r >> 1), d, n, H, h0, y0);
+    }
+    q -= c;
+  }
+  TbSlot t = tb_at<S>(S, S, 1 << 20, n, H, h0, y0);
+  t.e = -1;
+  return t;
+}
+
+// Loads of one plane z of colour c (value 0 outside the grid) into registers.
+template <int S>
+__device__ __forceinline__ void tb_load(float (&v)[TbShape<S>::LOADS], const TbSlot (&ld)[TbShape<S>::LOADS],
+                                        const float* __restrict__ a, int c, int z, int n, size_t plane, bool need) {
+  need = need && z >= 0 && z < n;
+  const float* az = a + plane * size_t(need ? z : 0);
+  const int par = (c + z + 1) & 1;
+#pragma unroll
+  for (int k = 0; k < TbShape<S>::LOADS; ++k) {
+    const TbSlot& t = ld[k];
+    const bool ok = need && t.e >= 0 && ((par ^ t.ypar) ? t.ok1 : t.ok0);
+    v[k] = ok ? az[t.g] : 0.f;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void tb_store(float* __restrict__ dst, const float (&v)[TbShape<S>::LOADS],
+                                         const TbSlot (&ld)[TbShape<S>::LOADS]) {
+#pragma unroll
+  for (int k = 0; k < TbShape<S>::LOADS; ++k)
+    if (ld[k].e >= 0) dst[ld[k].e] = v[k];
+}
+
+template <int S, int s>
+__device__ __forceinline__ void tb_stage(float* __restrict__ sm, const TbSlot (&sl)[2], int it, int n, size_t plane,
+                                         int z0, int z1, float kappa, float* __restrict__ xr_out,
+                                         float* __restrict__ xb_out, bool zero_guess) {
+  using Sh = TbShape<S>;
+  constexpr int r = S - 1 - s;           // ring of this stage
+  constexpr int c = s & 1;               // colour updated: 0 red, 1 black
+  const int z = it - s;
+  const bool active = z >= z0 - r && z < z1 + r && z >= 0 && z < n;
+  const bool store = s >= S - 2 && z >= z0 && z < z1;  // last red / last black stage, own planes
+  const int par = (c + z + 1) & 1;
+  const float* src = sm + (s == 0 ? Sh::BUF_IN : Sh::BUF_STAGE + (s - 1) * 3 * Sh::PL);
+  const float* om = src + tb_zslot(z - 1, S) * Sh::PL;
+  const float* o0 = src + tb_zslot(z, S) * Sh::PL;
+  const float* op = src + tb_zslot(z + 1, S) * Sh::PL;
+  float* dst = s < S - 1 ? sm + Sh::BUF_STAGE + s * 3 * Sh::PL + tb_zslot(z, S) * Sh::PL : nullptr;
+  const float* bz = sm + (c ? Sh::BUF_BB : Sh::BUF_BR) + tb_bslot(z) * Sh::PL;
+  float* outz = (c ? xb_out : xr_out) + plane * size_t(store ? z : 0);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const TbSlot& t = sl[k];
+    if (t.dist > r) continue;
+    float v = 0.f;
+    const int i0 = par ^ t.ypar;
+    if (active && (i0 ? t.ok1 : t.ok0)) {
+      const int e = t.e;
+      const float bv = bz[e];
+      if (s == 0 && zero_guess) {
+        v = bv;
+      } else {
+        const float sx = o0[e - 1 + i0] + o0[e + i0];
+        const float sy = o0[e - Sh::WX] + o0[e + Sh::WX];
+        const float sz = om[e] + op[e];
+        v = fmaf(kappa, (sx + sy) + sz, bv);
+      }
+      if (k == 0 && store) outz[t.g] = v;
+    }
+    if (dst) dst[t.e] = v;
+  }
+  __syncthreads();
+}
+
+template <int S, int s>
+__device__ __forceinline__ void tb_stages(float* sm, const TbSlot (&sl)[2], int it, int n, size_t plane, int z0,
+                                          int z1, float kappa, float* xr_out, float* xb_out, bool zero_guess) {
+  tb_stage<S, s>(sm, sl, it, n, plane, z0, z1, kappa, xr_out, xb_out, zero_guess);
+  if constexpr (s + 1 < S) tb_stages<S, s + 1>(sm, sl, it, n, plane, z0, z1, kappa, xr_out, xb_out, zero_guess);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTbThreads, 2)
+    k_rbgs_split_tb(int n, float kappa, const float* __restrict__ xb_in, float* __restrict__ xr_out,
+                    float* __restrict__ xb_out, const float* __restrict__ br, const float* __restrict__ bb,
+                    int zero_guess, int zc) {
+  using Sh = TbShape<S>;
+  extern __shared__ float sm[];
+  const int H = (n + 1) >> 1;
+  const size_t plane = size_t(H) * n;
+  const int h0 = blockIdx.x * kTbX, y0 = blockIdx.y * kTbY, z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, n);
+  const bool zg = zero_guess != 0;
+  const TbSlot sl[2] = {tb_slot<S>(threadIdx.x, 0, n, H, h0, y0), tb_slot<S>(threadIdx.x, 1, n, H, h0, y0)};
+  TbSlot ld[Sh::LOADS];
+#pragma unroll
+  for (int k = 0; k < Sh::LOADS; ++k) {
+    const int q = threadIdx.x + k * kTbThreads;
+    ld[k] = tb_at<S>(q % Sh::WX, q / Sh::WX, 0, n, H, h0, y0);
+    if (q >= Sh::PL) ld[k].e = -1;
+  }
+  // iteration it stores the black input plane it+1 and the rhs planes it,
+  // loaded during iteration it-1
+  const int it_first = z0 - S - 1, it_last = z1 + S - 2;
+  float vin[Sh::LOADS], vbr[Sh::LOADS], vbb[Sh::LOADS];
+  tb_load<S>(vin, ld, xb_in, 1, it_first + 1, n, plane, !zg);
+  tb_load<S>(vbr, ld, br, 0, it_first, n, plane, true);
+  tb_load<S>(vbb, ld, bb, 1, it_first, n, plane, true);
+  for (int it = it_first; it <= it_last; ++it) {
+    if (!zg) tb_store<S>(sm + Sh::BUF_IN + tb_zslot(it + 1, S) * Sh::PL, vin, ld);
+    tb_store<S>(sm + Sh::BUF_BR + tb_bslot(it) * Sh::PL, vbr, ld);
+    tb_store<S>(sm + Sh::BUF_BB + tb_bslot(it) * Sh::PL, vbb, ld);
+    __syncthreads();
+    if (it < it_last) {
+      const int zi = it + 2;
+      tb_load<S>(vin, ld, xb_in, 1, zi, n, plane, !zg && zi >= z0 - S && zi < z1 + S);
+      tb_load<S>(vbr, ld, br, 0, it + 1, n, plane, true);
+      tb_load<S>(vbb, ld, bb, 1, it + 1, n, plane, true);
+    }
+    tb_stages<S, 0>(sm, sl, it, n, plane, z0, z1, kappa, xr_out, xb_out, zg);
+  }
+}
+
 // Scaled residual at the red points after a complete red-black sweep (the
 // black rows are satisfied), stored in a red-only array with the red slots.
 template <int DIM>
@@ -442,12 +639,16 @@ __global__ void __launch_bounds__(kBX* kBY)
 // SDC kernels (FP64).
 // ---------------------------------------------------------------------------
 constexpr int kMaxM = 7;
+constexpr int kMaxP = kMaxM + 1;
 
-// Collocation tables premultiplied by dt (Sec. 2, Eq. 2).
+// Collocation tables premultiplied by dt (Sec. 2, Eq. 2), over the P points of
+// a sweep: t_0 = T_n and the M nodes (P = M for Gauss-Lobatto, whose first
+// node is t_0; P = M + 1 for Gauss-Radau and Gauss-Legendre).  Node j is
+// point j + OFF with OFF = P - M.
 struct SweepTables {
-  int M;
-  double dtQ[kMaxM][kMaxM];   // dt * Q[m][j]; row 0 is zero for Gauss-Lobatto (tau_1 = 0)
-  double dtm[kMaxM];          // dt_m = dt (tau_{m+1} - tau_m)
+  int M, P;
+  double dtQ[kMaxP][kMaxM];   // dt * int_{t_0}^{t_p} l_j; row 0 is zero
+  double dtm[kMaxP];          // dt_m = t_{m+1} - t_m between consecutive points
 };
 
 // Start of a step: every node u_m = u, f_m = f^E(u) + nu L_h u.
@@ -501,6 +702,56 @@ __global__ void __launch_bounds__(kBX* kBY)
   if (Fm) Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
 }
 
+// Mixed precision with a fixed V-cycle count: the defect of node m's system at
+// its initial guess x = u_{m+1}^k (Sec. 4.3).  With the sweep constant in the
+// defect form
+//   C'_m = dt sum_j s_{m,j} f(u_j^k) - dt_m f^E(u_m^k) - u_{m+1}^k
+// the implicit terms of b and of (I - a L_h) x cancel (a L_h u_{m+1}^k =
+// dt_m f^I(u_{m+1}^k)), so
+//   r = b - (I - a L_h) u_{m+1}^k = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C'_m
+// needs no stencil of u_{m+1}^k.  r / d is computed in FP64 and stored in FP32;
+// for m >= 1 the same pass stores f_m = f(u_m^{k+1}).
+template <int DIM>
+__device__ __forceinline__ float rhs_defect_point(int i, int j, int k, int n, int p, double nu_h2, int reaction,
+                                                  double dtm, double inv_d, const double* __restrict__ Um,
+                                                  const double* __restrict__ Cm, double* __restrict__ Fm) {
+  const double up = Um[p];
+  const double fe = reaction_term(reaction, up);
+  if (Fm) Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
+  return float((fma(dtm, fe, up) + Cm[p]) * inv_d);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rhs_defect(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
+                 const double* __restrict__ Cm, double* __restrict__ Fm, float* __restrict__ r32) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = lin<DIM>(i, j, k, n);
+  r32[p] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+}
+
+// The same into the colour-split FP32 arrays: one thread per slot pair (points
+// 2h and 2h+1 of a row, one of each colour).
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rhs_defect_split(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
+                       const double* __restrict__ Cm, double* __restrict__ Fm, float* __restrict__ r0,
+                       float* __restrict__ r1) {
+  const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int H = (n + 1) >> 1;
+  if (h >= H || j >= n) return;
+  const int c0 = (j + (DIM == 3 ? k : 0) + DIM) & 1;  // colour of the even point 2h
+  const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+  const int i = 2 * h;
+  const int p = lin<DIM>(i, j, k, n);
+  (c0 ? r1 : r0)[slot] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+  if (i + 1 < n)
+    (c0 ? r0 : r1)[slot] = rhs_defect_point<DIM>(i + 1, j, k, n, p + 1, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+}
+
 __device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned long long* out) {
   // Non-negative doubles order like their bit patterns; NaN sorts above Inf.
 #pragma unroll
@@ -525,11 +776,12 @@ __device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned 
 
 // End of a sweep: f_{M-1} = f(u_{M-1}), the SDC residual
 //   R = max_m max_x | u_0 + dt sum_j q_{m,j} f_j - u_m |         (Sec. 3)
-// and the sweep constants C_m of the next sweep.  Node arrays are node-major
-// with stride N.  *Rbits must be zero on entry.
-template <int DIM>
+// and the sweep constants of the next sweep: C_m (cmode 0, the form k_rhs
+// adds) or C'_m (cmode 1, the defect form of k_rhs_defect).  Node arrays are
+// node-major with stride N.  *Rbits must be zero on entry.
+template <int DIM, int OFF>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_sweep_end(int n, size_t N, double nu_h2, int reaction, SweepTables tb,
+    k_sweep_end(int n, size_t N, double nu_h2, int reaction, int cmode, SweepTables tb,
                 const double* __restrict__ U, double* __restrict__ F, double* __restrict__ C,
                 unsigned long long* __restrict__ Rbits) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
@@ -537,55 +789,79 @@ __global__ void __launch_bounds__(kBX* kBY)
   unsigned long long rb = 0;
   if (i < n && j < n) {
     const int p = lin<DIM>(i, j, k, n);
-    const int M = tb.M;
-    double u[kMaxM], f[kMaxM], fe[kMaxM], qf[kMaxM];
+    const int M = tb.M, P = tb.P;
+    double u[kMaxP], f[kMaxP], fe[kMaxP], qf[kMaxP];
 #pragma unroll
-    for (int m = 0; m < kMaxM; ++m)
-      if (m < M) {
+    for (int m = 0; m < kMaxP; ++m)
+      if (m < P) {
         u[m] = U[m * N + p];
         fe[m] = reaction_term(reaction, u[m]);
       }
-    // f at the last node from its stencil; the other f_m were stored during the sweep
-    const double* ul = U + (size_t)(M - 1) * N;
+    // f at the last point from its stencil; the other nodes' f were stored during the sweep
+    const double* ul = U + (size_t)(P - 1) * N;
     const double ulast = ul[p];
     const double flast = reaction_term(reaction, ulast) +
                          nu_h2 * (nbsum<double, DIM>(ul, i, j, k, n, p) - double(2 * DIM) * ulast);
-    F[(size_t)(M - 1) * N + p] = flast;
+    F[(size_t)(P - 1) * N + p] = flast;
 #pragma unroll
-    for (int m = 0; m < kMaxM; ++m) {
-      if (m < M - 1) f[m] = F[m * N + p];
-      else if (m == M - 1) f[m] = flast;
+    for (int m = OFF; m < kMaxP; ++m) {
+      if (m < P - 1) f[m] = F[m * N + p];
+      else if (m == P - 1) f[m] = flast;
     }
-    // dt sum_j q_{m,j} f_j for m >= 1 (row 0 of Q is zero); the node-to-node
-    // term dt sum_j s_{m,j} f_j of Eq. 2 is the difference of consecutive rows.
+    // dt sum_j q_{m,j} f_j for the points m >= 1 (row 0 is zero); the
+    // point-to-point term dt sum_j s_{m,j} f_j of Eq. 2 is the difference of
+    // consecutive rows.  Node j is point j + OFF.
 #pragma unroll
-    for (int m = 1; m < kMaxM; ++m)
-      if (m < M) {
-        double acc = tb.dtQ[m][0] * f[0];
+    for (int m = 1; m < kMaxP; ++m)
+      if (m < P) {
+        double acc = tb.dtQ[m][0] * f[OFF];
 #pragma unroll
         for (int jj = 1; jj < kMaxM; ++jj)
-          if (jj < M) acc = fma(tb.dtQ[m][jj], f[jj], acc);
+          if (jj < M) acc = fma(tb.dtQ[m][jj], f[jj + OFF], acc);
         qf[m] = acc;
       }
     // max of |r| on the integer pipe: with the sign bit cleared, doubles order
     // like their bit patterns (NaN above Inf), so no FP64 compares are needed
 #pragma unroll
-    for (int m = 1; m < kMaxM; ++m)
-      if (m < M) {
+    for (int m = 1; m < kMaxP; ++m)
+      if (m < P) {
         const unsigned long long rbits =
             (unsigned long long)__double_as_longlong((u[0] - u[m]) + qf[m]) & 0x7fffffffffffffffull;
         rb = rbits > rb ? rbits : rb;
       }
 #pragma unroll
-    for (int m = 0; m < kMaxM - 1; ++m)
-      if (m < M - 1) {
+    for (int m = 0; m < kMaxP - 1; ++m)
+      if (m < P - 1) {
         const double sf = m == 0 ? qf[1] : qf[m + 1] - qf[m];
         // f^I(u_{m+1}) = f_{m+1} - f^E(u_{m+1})
-        C[m * N + p] = fma(-tb.dtm[m], fe[m] + (f[m + 1] - fe[m + 1]), sf);
+        C[m * N + p] = cmode ? fma(-tb.dtm[m], fe[m], sf) - u[m + 1]
+                             : fma(-tb.dtm[m], fe[m] + (f[m + 1] - fe[m + 1]), sf);
       }
-
   }
   block_max_atomic(rb, Rbits);
+}
+
+// End of a Gauss-Legendre step (tau_M < 1): the collocation rule's full-step
+// quadrature u = u_0 + dt sum_j w_j f(u_j) (Sec. 2), with u_0 in point 0 and
+// f of node j in point j + 1.
+struct EndWeights {
+  int M;
+  double dtw[kMaxM];  // dt * w_j, w_j = int_0^1 l_j
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_gauss_end(int n, size_t N, EndWeights ew, const double* __restrict__ U, const double* __restrict__ F,
+                double* __restrict__ u) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = lin<DIM>(i, j, k, n);
+  double acc = ew.dtw[0] * F[N + p];
+#pragma unroll
+  for (int m = 1; m < kMaxM; ++m)
+    if (m < ew.M) acc = fma(ew.dtw[m], F[(m + 1) * N + p], acc);
+  u[p] = U[p] + acc;
 }
 
 // Max-norm of b - H x (classical SDC stopping test), FP64.

@@ -39,7 +39,7 @@ class isdc_options(ctypes.Structure):
                 ("omega", ctypes.c_double), ("vcycle_fp32", ctypes.c_int), ("reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_max_cycles", ctypes.c_int), ("vcycle_cap", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("temporal_blocking", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class isdc_kernel_stat(ctypes.Structure):
@@ -118,7 +118,7 @@ def load(build_if_missing: bool = True):
         "isdc_batch_destroy": (None, [_ctx_p]),
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
-        "isdc_tuning": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "isdc_tuning": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
         "isdc_destroy": (None, [_ctx_p]),
     }
@@ -155,13 +155,15 @@ def isdc_default_options() -> isdc_options:
 
 
 def isdc_collocation_tables(M: int, nodes: int = ISDC_NODES_GAUSS_LOBATTO):
-    """Host-only tables (tau, Q, S) as nested lists."""
+    """Host-only tables (tau, Q, S) as nested lists; S has one row per sweep
+    step between consecutive points (M - 1 for Gauss-Lobatto, else M)."""
+    rows = M - 1 if nodes == ISDC_NODES_GAUSS_LOBATTO else M
     tau = (ctypes.c_double * M)()
     Q = (ctypes.c_double * (M * M))()
-    S = (ctypes.c_double * ((M - 1) * M))()
+    S = (ctypes.c_double * (rows * M))()
     _check(load().isdc_collocation_tables(nodes, M, tau, Q, S))
     return (list(tau), [list(Q[m * M:(m + 1) * M]) for m in range(M)],
-            [list(S[m * M:(m + 1) * M]) for m in range(M - 1)])
+            [list(S[m * M:(m + 1) * M]) for m in range(rows)])
 
 
 def isdc_create(ndim, n, nu, M, dt, options: isdc_options | None = None,
@@ -279,9 +281,9 @@ def isdc_profile_read(ctx):
 
 
 def isdc_tuning(ctx):
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(load().isdc_tuning(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
-    return {"zb_fp64": a.value, "zb_fp32": b.value}
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().isdc_tuning(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), ctx)
+    return {"zb_fp64": a.value, "zb_fp32": b.value, "tb_depth": c.value, "tb_planes": d.value}
 
 
 def isdc_last_error(ctx=None) -> str:
@@ -414,13 +416,14 @@ class Isdc:
 
     def __init__(self, ndim, n, nu, M, dt, *, smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1,
                  omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
-                 max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True, stream=None):
+                 max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True,
+                 temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stream=None):
         import torch
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
         o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
         o.mg_tol, o.mg_max_cycles, o.vcycle_cap = mg_tol, mg_max_cycles, int(vcycle_cap)
-        o.use_graphs = int(use_graphs)
+        o.use_graphs, o.temporal_blocking = int(use_graphs), int(temporal_blocking)
         s = stream if stream is not None else torch.cuda.current_stream()
         # torch's default stream has handle 0, which the C ABI reads as "create a
         # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.
@@ -428,7 +431,7 @@ class Isdc:
         self.stream = s
         self.ndim, self.n, self.M = ndim, n, M
         self.N = n ** ndim
-        self.ctx = isdc_create(ndim, n, nu, M, dt, o)
+        self.ctx = isdc_create(ndim, n, nu, M, dt, o, nodes)
 
     def step(self, u, n_sweeps=0, n_vcycles=2):
         return isdc_step(self.ctx, u, n_sweeps, n_vcycles)

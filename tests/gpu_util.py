@@ -27,4 +27,6 @@ def make_gpu(p: O.Problem, vcycle_fp32=False, **kw):
                   omega=p.omega, vcycle_fp32=vcycle_fp32,
                   reaction=G.ISDC_REACTION_ALLEN_CAHN if p.reaction == O.REACTION_ALLEN_CAHN
                   else G.ISDC_REACTION_NONE,
-                  tol=p.tol, max_sweeps=p.max_sweeps, mg_tol=p.mg_tol, mg_max_cycles=p.mg_max_cycles, **kw)
+                  tol=p.tol, max_sweeps=p.max_sweeps, mg_tol=p.mg_tol, mg_max_cycles=p.mg_max_cycles,
+                  nodes={O.NODES_LOBATTO: G.ISDC_NODES_GAUSS_LOBATTO, O.NODES_RADAU_RIGHT: G.ISDC_NODES_RADAU_RIGHT,
+                         O.NODES_LEGENDRE: G.ISDC_NODES_GAUSS_LEGENDRE}[p.nodes], **kw)

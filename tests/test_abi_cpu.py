@@ -45,11 +45,27 @@ def test_library_collocation_tables_match_oracle(M):
     np.testing.assert_allclose(S, O.s_matrix(M), atol=2e-15)
 
 
+@pytest.mark.parametrize("kind", ["radau", "legendre"])
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 6, 7])
+def test_library_radau_legendre_tables_match_oracle(kind, M):
+    """The library's Golub-Welsch nodes and exact Lagrange integrals against the
+    oracle's (root bracketing / Newton, Gauss quadrature of l_j); S runs over the
+    M steps t_0 -> t_1 -> ... -> t_M (Eq. 2)."""
+    import paper_1401_7824_gb300 as G
+    lib_kind = {"radau": G.ISDC_NODES_RADAU_RIGHT, "legendre": G.ISDC_NODES_GAUSS_LEGENDRE}[kind]
+    orc_kind = {"radau": O.NODES_RADAU_RIGHT, "legendre": O.NODES_LEGENDRE}[kind]
+    tau, Q, S = G.isdc_collocation_tables(M, nodes=lib_kind)
+    np.testing.assert_allclose(tau, O.nodes(M, orc_kind), rtol=0, atol=2e-16)
+    Qo = O.q_matrix(M, orc_kind)
+    np.testing.assert_allclose(Q, Qo, rtol=0, atol=2e-15)
+    np.testing.assert_allclose(S, np.diff(np.vstack([np.zeros(M), Qo]), axis=0), rtol=0, atol=2e-15)
+
+
 def test_host_validation_without_gpu():
     import paper_1401_7824_gb300 as G
     with pytest.raises(G.IsdcError) as e:
-        G.isdc_collocation_tables(3, nodes=G.ISDC_NODES_GAUSS_LEGENDRE)
-    assert e.value.status == G.ISDC_ERR_UNSUPPORTED
+        G.isdc_collocation_tables(3, nodes=3)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG
     with pytest.raises(G.IsdcError) as e:
         G.isdc_collocation_tables(9)
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
@@ -60,3 +76,22 @@ def test_host_validation_without_gpu():
         assert "must" in G.isdc_last_error()
     o = G.isdc_default_options()
     assert (o.smoother, o.nu1, o.nu2, o.max_sweeps, o.tol) == (0, 1, 1, 100, 1e-10)
+
+
+@pytest.mark.parametrize("struct", ["isdc_options", "isdc_problem", "isdc_slot_info", "isdc_batch_info",
+                                    "isdc_kernel_stat"])
+def test_binding_structs_match_the_header_layout(struct, tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's size and
+    field offsets (a layout mismatch would silently misread every option)."""
+    import paper_1401_7824_gb300.isdc as B
+    cls = getattr(B, struct)
+    fields = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"isdc.h\"\nint main(void){\n"
+                   + f'printf("%zu\\n", sizeof({struct}));\n'
+                   + "".join(f'printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields) + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in fields]

@@ -231,8 +231,8 @@ def test_invalid_arguments_are_rejected():
         G.isdc_create(2, 64, 0.1, 3, 0.05)
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
     with pytest.raises(G.IsdcError) as e:
-        G.isdc_create(2, 63, 0.1, 3, 0.05, nodes=G.ISDC_NODES_RADAU_RIGHT)
-    assert e.value.status == G.ISDC_ERR_UNSUPPORTED
+        G.isdc_create(2, 63, 0.1, 3, 0.05, nodes=7)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG
     with pytest.raises(G.IsdcError) as e:
         G.isdc_create(3, 31, -1.0, 3, 0.05)
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
@@ -322,3 +322,123 @@ def test_workload_3d_511_fp32_vcycles_full_size_residual():
     g.close()
     R_oracle = O.sdc_residual(p, nodes)
     assert R_oracle < 1e-10 and abs(R_oracle - R) <= 1e-13, (R, R_oracle)
+
+
+@pytest.mark.parametrize("nu12", [(2, 2), (3, 1)])
+def test_temporal_blocking_is_bitwise_identical(nu12):
+    """Blocked passes of 1 or 2 red-black sweeps over the FP32 colour-split fine
+    level (3D) do the same FP32 operations in the same order as one pass per
+    colour, so whole steps agree bit for bit; the result still matches the
+    oracle.  Side 127: several tiles in x and y, several z-chunks, ragged edges."""
+    import paper_1401_7824_gb300 as G
+    nu1, nu2 = nu12
+    p = O.Problem(3, 127, 0.1, 3, 0.02, smoother=RB, nu1=nu1, nu2=nu2, max_sweeps=150)
+    u0 = initial_condition(3, 127, seed=41)
+    outs = []
+    for depth in (0, 1, 2):
+        g = make_gpu(p, vcycle_fp32=True, temporal_blocking=depth)
+        assert g.tuning()["tb_depth"] == depth
+        u = to_dev(u0)
+        assert g.step(u, 0, 2) == 0
+        outs.append((u.cpu().numpy(), g.stats(), g.residual()))
+        g.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        assert o[1] == outs[0][1] and o[2] == outs[0][2]
+    ref = O.integrate(p, u0, 1, 0, 2)
+    assert rel_l2(outs[0][0], ref.per_step_u[0]) <= 1e-9
+
+
+def test_temporal_blocking_option_is_validated_and_tuned():
+    import paper_1401_7824_gb300 as G
+    p = O.Problem(3, 63, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2)
+    g = make_gpu(p, vcycle_fp32=True)
+    t = g.tuning()
+    assert t["tb_depth"] in (0, 1, 2) and t["tb_planes"] in (16, 32, 64, 128)
+    g.close()
+    with pytest.raises(G.IsdcError) as e:
+        make_gpu(p, vcycle_fp32=True, temporal_blocking=3)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG
+
+
+
+# --- Gauss-Radau (right) and Gauss-Legendre nodes (Sec. 2) ---------------------
+RL = (O.NODES_RADAU_RIGHT, O.NODES_LEGENDRE)
+NODE_STEP_CASES = [
+    # ndim, n, nu, M, dt, smoother, nu1, nu2, L, nodes
+    (2, 63, 0.1, 3, 0.05, J, 1, 1, 2, O.NODES_RADAU_RIGHT),
+    (2, 63, 0.1, 3, 0.05, J, 1, 1, 2, O.NODES_LEGENDRE),
+    (3, 31, 0.1, 5, 0.02, RB, 2, 2, 2, O.NODES_RADAU_RIGHT),
+    (3, 31, 0.1, 4, 0.02, RB, 2, 2, 2, O.NODES_LEGENDRE),
+    (2, 31, 0.5, 7, 0.01, RB, 2, 2, 1, O.NODES_LEGENDRE),
+    (3, 15, 0.3, 2, 0.05, J, 1, 1, 3, O.NODES_RADAU_RIGHT),
+]
+
+
+@pytest.mark.parametrize("case", NODE_STEP_CASES)
+def test_radau_legendre_steps_match_oracle_fp64(case):
+    """M node solves per sweep from t_0; Gauss-Legendre ends each step with the
+    full-step quadrature.  FP64 path against the oracle, relative L2 <= 1e-12."""
+    d, n, nu, M, dt, sm, nu1, nu2, L, kind = case
+    p = O.Problem(d, n, nu, M, dt, smoother=sm, nu1=nu1, nu2=nu2, max_sweeps=100, nodes=kind)
+    u0 = initial_condition(d, n, seed=400 + n + d + M)
+    ref = O.integrate(p, u0, 3, 0, L)
+    assert all(st == 0 for st in ref.status)
+    g = make_gpu(p)
+    g.record_history(True)
+    u = to_dev(u0)
+    for s in range(3):
+        g.step(u, ref.sweeps[s], L)
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-12
+        np.testing.assert_allclose(g.history(), ref.residuals[s], rtol=1e-6, atol=1e-13)
+        sweeps, vcyc = g.stats()
+        assert vcyc == sweeps * M * L
+
+
+@pytest.mark.parametrize("kind", RL)
+def test_radau_legendre_fp32_vcycles_converge_to_oracle(kind):
+    p = O.Problem(3, 63, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2, max_sweeps=150, nodes=kind)
+    u0 = initial_condition(3, 63, seed=430 + kind)
+    ref = O.integrate(p, u0, 2, 0, 2)
+    g = make_gpu(p, vcycle_fp32=True)
+    u = to_dev(u0)
+    for s in range(2):
+        assert g.step(u, 0, 2) == 0
+        assert g.residual() < 1e-10
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", RL)
+def test_radau_legendre_nodes_residual_and_resume(kind):
+    """Node values come back without t_0; the oracle's residual of them (with
+    u_0 given) equals the library's; resuming from them is bitwise."""
+    p = O.Problem(2, 63, 0.2, 3, 0.03, smoother=J, nodes=kind)
+    u0 = initial_condition(2, 63, seed=440 + kind)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    g.step(u, 5, 2)
+    nodes = g.nodes().cpu().numpy()
+    assert nodes.shape == (3,) + p.shape
+    assert abs(O.sdc_residual(p, nodes, u0) - g.residual()) <= 1e-13
+    g2 = make_gpu(p)
+    v = to_dev(u0)
+    g2.step(v, 3, 2)
+    g3 = make_gpu(p)
+    g3.set_nodes(g2.nodes().clone())
+    w = to_dev(u0)
+    g3.step(w, 2, 2)
+    np.testing.assert_array_equal(w.cpu().numpy(), u.cpu().numpy())
+
+
+@pytest.mark.parametrize("kind", RL)
+def test_radau_legendre_graph_replay_is_bitwise_identical(kind):
+    p = O.Problem(3, 31, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2, nodes=kind)
+    u0 = initial_condition(3, 31, seed=450 + kind)
+    outs = []
+    for graphs in (True, False):
+        g = make_gpu(p, vcycle_fp32=True, use_graphs=graphs)
+        u = to_dev(u0)
+        g.step(u, 0, 2)
+        outs.append((u.cpu().numpy(), g.stats()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
