@@ -100,11 +100,21 @@ class ClockSampler:
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
 
 
+SDC_CLASSES = ("spread", "eval_f", "rhs", "sweep_end", "resnorm")  # kernels in csrc/sdc_kernels.cuh
+
+
+def kernel_source_sha(cls: str) -> str:
+    """sha256 prefix of the header that holds the kernels of class cls."""
+    name = "sdc_kernels.cuh" if cls in SDC_CLASSES else "kernels.cuh"
+    with open(os.path.join(ROOT, "paper_1401_7824_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def traffic_for(workload: str, cls: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (profiles/ncu_traffic.txt: workload class sha bytes)."""
-    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1401_7824_gb300", "csrc", "kernels.cuh"), "rb").read())
-    sha = sha.hexdigest()[:16]
+    the current kernel source (profiles/ncu_traffic.txt: workload class sha bytes,
+    sha of the header holding that class's kernels)."""
+    sha = kernel_source_sha(cls)
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")) as f:
             for line in f:

@@ -6,7 +6,7 @@
 // part in that phase.  Node state and the SDC update are FP64; the V-cycles
 // run in FP32 on the error equation (defect correction, as in isdc.cu).
 #pragma once
-#include "kernels.cuh"
+#include "sdc_kernels.cuh"
 
 namespace isdc {
 namespace batch {

@@ -22,6 +22,7 @@
 #include "../../include/isdc.h"
 #include "host_util.h"
 #include "kernels.cuh"
+#include "sdc_kernels.cuh"
 
 #define ISDC_API extern "C" __attribute__((visibility("default")))
 
@@ -633,6 +634,37 @@ inline double bits_to_double(unsigned long long b) {
   return v;
 }
 
+// k_sweep_end for the context's point count (compile-time P: straight-line
+// code, registers for exactly P points).
+template <int DIM, int OFF, int P>
+void launch_sweep_end_p(isdc_ctx* ctx, double nu_h2) {
+  k_sweep_end<DIM, OFF, P><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
+      ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
+}
+
+template <int DIM>
+void launch_sweep_end(isdc_ctx* ctx, double nu_h2) {
+  if (ctx->off) {
+    switch (ctx->P) {
+      case 3: launch_sweep_end_p<DIM, 1, 3>(ctx, nu_h2); break;
+      case 4: launch_sweep_end_p<DIM, 1, 4>(ctx, nu_h2); break;
+      case 5: launch_sweep_end_p<DIM, 1, 5>(ctx, nu_h2); break;
+      case 6: launch_sweep_end_p<DIM, 1, 6>(ctx, nu_h2); break;
+      case 7: launch_sweep_end_p<DIM, 1, 7>(ctx, nu_h2); break;
+      default: launch_sweep_end_p<DIM, 1, 8>(ctx, nu_h2); break;
+    }
+  } else {
+    switch (ctx->P) {
+      case 2: launch_sweep_end_p<DIM, 0, 2>(ctx, nu_h2); break;
+      case 3: launch_sweep_end_p<DIM, 0, 3>(ctx, nu_h2); break;
+      case 4: launch_sweep_end_p<DIM, 0, 4>(ctx, nu_h2); break;
+      case 5: launch_sweep_end_p<DIM, 0, 5>(ctx, nu_h2); break;
+      case 6: launch_sweep_end_p<DIM, 0, 6>(ctx, nu_h2); break;
+      default: launch_sweep_end_p<DIM, 0, 7>(ctx, nu_h2); break;
+    }
+  }
+}
+
 template <int DIM>
 isdc_status sweep_end(isdc_ctx* ctx) {
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
@@ -644,12 +676,7 @@ isdc_status sweep_end(isdc_ctx* ctx) {
     ProfScope ps(ctx, PC_SWEEP_END, (2.0 * P + M - 1.0) * 8.0 * Np,
                  (nb_ops(DIM) + 2.0 + 2.0 * P + (P - 1.0) * M + (ctx->cprime ? 5.0 : 6.0) * (P - 1.0) - 1.0) * Np,
                  true);
-    if (ctx->off)
-      k_sweep_end<DIM, 1><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
-          ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
-    else
-      k_sweep_end<DIM, 0><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
-          ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
+    launch_sweep_end<DIM>(ctx, nu_h2);
   }
   LAUNCH_CHECK(ctx);
   return ISDC_OK;
