@@ -20,6 +20,13 @@
  *     with f^I(u) = A u, A = nu * L_h (5-point 2D / 7-point 3D Laplacian,
  *     zero Dirichlet ghosts, W = I in Eq. 5), and f^E(u) = u - u^3
  *     (or none, or lambda_E*u for the Dahlquist order test);
+ *   - or, in 2D, the 4th-order compact discretisation of Sec. 3: the 9-point
+ *     Laplacian L_9 with the weighting matrix W = I + (h^2/12) L_5, so that
+ *     W u' = nu L_9 u + W f^E(u), f^I = W^{-1} nu L_9, and the sweep of Eq. 5
+ *       (W - dt_m A) u_{m+1}^{k+1} = W u_m^{k+1} + dt_m W[f^E(u_m^{k+1}) - f^E(u_m^k)]
+ *                                  - dt_m A u_{m+1}^k + S_m^{m+1} F~(u^k)
+ *     with A = nu L_9 and f~ = W f^E + A u; the SDC residual inverts W once
+ *     per node (exactly, by the sine transform);
  *   - each implicit Euler solve (I - dt_m A) x = b done either exactly
  *     (sine-transform diagonalisation: classical SDC with an exact spatial
  *     solve, Sec. 3), by multigrid until a tolerance (classical SDC, Sec. 3),
@@ -69,6 +76,9 @@ typedef struct {
     int    mg_max_cycles;
     int    nodes;       /* 0 Gauss-Lobatto, 1 Gauss-Radau (right, tau_M = 1),
                            2 Gauss-Legendre */
+    int    stencil;     /* 0: 5-point (2D) / 7-point (3D) Laplacian, W = I;
+                           1: 4th-order compact 9-point Laplacian with the
+                           weighting matrix W (Sec. 3, Eq. 5), 2D only */
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -424,12 +434,79 @@ void orc_prolong_add(int d, int nc, const double *ec, double *x)
             }
 }
 
+/* ------------------------------------------------------------------------ */
+/* 4th-order compact discretisation (Sec. 3), 2D only.                       */
+/* ------------------------------------------------------------------------ */
+
+/* Sum of the 4 corner (diagonal) neighbours of (i,j); zero outside. */
+static double corner_sum(const double *u, int n, int i, int j)
+{
+    return val(u, 2, n, i - 1, j - 1, 1) + val(u, 2, n, i + 1, j - 1, 1)
+         + val(u, 2, n, i - 1, j + 1, 1) + val(u, 2, n, i + 1, j + 1, 1);
+}
+
+/* L_9 u = (4 * edge neighbours + corner neighbours - 20 u) / (6 h^2) */
+static double lap9_at(const double *u, int n, int i, int j)
+{
+    double h = 1.0 / (n + 1);
+    return (4.0 * neighbour_sum(u, 2, n, i, j, 1) + corner_sum(u, n, i, j) - 20.0 * val(u, 2, n, i, j, 1))
+           / (6.0 * h * h);
+}
+
+/* W u = u + (h^2/12) L_5 u = (8 u + edge neighbours) / 12 */
+static double w_at(const double *u, int n, int i, int j)
+{
+    return (8.0 * val(u, 2, n, i, j, 1) + neighbour_sum(u, 2, n, i, j, 1)) / 12.0;
+}
+
+/* out = L_9 u */
+void orc_laplacian9(int n, const double *u, double *out)
+{
+    for (int j = 1; j <= n; ++j)
+        for (int i = 1; i <= n; ++i) out[idx(2, n, i, j, 1)] = lap9_at(u, n, i, j);
+}
+
+/* out = W u */
+void orc_apply_w(int n, const double *u, double *out)
+{
+    for (int j = 1; j <= n; ++j)
+        for (int i = 1; i <= n; ++i) out[idx(2, n, i, j, 1)] = w_at(u, n, i, j);
+}
+
+/* r = b - (W - a L_9) x */
+void orc_residual9(int n, double a, const double *x, const double *b, double *r)
+{
+    for (int j = 1; j <= n; ++j)
+        for (int i = 1; i <= n; ++i) {
+            long p = idx(2, n, i, j, 1);
+            r[p] = b[p] - (w_at(x, n, i, j) - a * lap9_at(x, n, i, j));
+        }
+}
+
 /*
- * Exact solve of (I - a L_h) x = b on a small grid by assembling the dense
- * matrix column by column (applying the operator to unit vectors) and Gaussian
- * elimination with partial pivoting.  Used on the coarsest multigrid level.
+ * One damped-Jacobi sweep on (W - a L_9) x = b: every point from the old
+ * iterate, x += omega (b - (W - a L_9) x_old) / diag, diag = 8/12 + 20 a/(6 h^2).
  */
-void orc_dense_solve(int d, int n, double a, const double *b, double *x)
+void orc_smooth_jacobi9(int n, double a, double omega, double *x, const double *b, double *old)
+{
+    double h = 1.0 / (n + 1);
+    double diag = 8.0 / 12.0 + 20.0 * a / (6.0 * h * h);
+    memcpy(old, x, sizeof(double) * npoints(2, n));
+    for (int j = 1; j <= n; ++j)
+        for (int i = 1; i <= n; ++i) {
+            long p = idx(2, n, i, j, 1);
+            double r = b[p] - (w_at(old, n, i, j) - a * lap9_at(old, n, i, j));
+            x[p] = old[p] + omega * r / diag;
+        }
+}
+
+/*
+ * Exact solve on a small grid: the dense matrix of the operator (I - a L_h for
+ * stencil 0, W - a L_9 for stencil 1) assembled column by column by applying
+ * it to unit vectors, then Gaussian elimination with partial pivoting.  Used
+ * on the coarsest multigrid level.
+ */
+static void dense_solve(int stencil, int d, int n, double a, const double *b, double *x)
 {
     long N = npoints(d, n);
     double *A = (double *)malloc(sizeof(double) * N * N);
@@ -439,8 +516,9 @@ void orc_dense_solve(int d, int n, double a, const double *b, double *x)
     double *zero = (double *)calloc(N, sizeof(double));
     for (long c = 0; c < N; ++c) {
         e[c] = 1.0;
-        /* column c of (I - a L_h) = -(residual of x=e with b=0) */
-        orc_residual(d, n, a, e, zero, col);
+        /* column c of the operator = -(residual of x = e with b = 0) */
+        if (stencil) orc_residual9(n, a, e, zero, col);
+        else orc_residual(d, n, a, e, zero, col);
         for (long r = 0; r < N; ++r) A[r * N + c] = -col[r];
         e[c] = 0.0;
     }
@@ -468,6 +546,9 @@ void orc_dense_solve(int d, int n, double a, const double *b, double *x)
     }
     free(A); free(e); free(col); free(rhs); free(zero);
 }
+
+void orc_dense_solve(int d, int n, double a, const double *b, double *x) { dense_solve(0, d, n, a, b, x); }
+void orc_dense_solve9(int n, double a, const double *b, double *x) { dense_solve(1, 2, n, a, b, x); }
 
 /* Multigrid hierarchy: level 0 is the fine grid, sides n_l = (n_{l-1}-1)/2 down to 3. */
 typedef struct {
@@ -504,20 +585,29 @@ static void mg_free(orc_mg *mg)
 
 static void smooth(const orc_problem *P, int n, double a, double *x, const double *b, double *tmp)
 {
-    if (P->smoother == 0) orc_smooth_jacobi(P->ndim, n, a, P->omega, x, b, tmp);
+    if (P->stencil == 1) orc_smooth_jacobi9(n, a, P->omega, x, b, tmp);
+    else if (P->smoother == 0) orc_smooth_jacobi(P->ndim, n, a, P->omega, x, b, tmp);
     else orc_smooth_rbgs(P->ndim, n, a, x, b);
 }
 
-/* One V-cycle on level l for (I - a L_{h_l}) x = b, x updated in place. */
+/* r = b - H x for the problem's operator (I - a L_h, or W - a L_9) */
+static void node_residual(const orc_problem *P, int n, double a, const double *x, const double *b, double *r)
+{
+    if (P->stencil == 1) orc_residual9(n, a, x, b, r);
+    else orc_residual(P->ndim, n, a, x, b, r);
+}
+
+/* One V-cycle on level l for H x = b (H = I - a L_{h_l}, or W - a L_9 rediscretised
+ * on level l), x updated in place. */
 static void vcycle(const orc_problem *P, orc_mg *mg, int l, double a, double *x, const double *b)
 {
     int d = P->ndim, n = mg->side[l];
     if (l == mg->levels - 1) { /* coarsest grid: exact solve */
-        orc_dense_solve(d, n, a, b, x);
+        dense_solve(P->stencil, d, n, a, b, x);
         return;
     }
     for (int s = 0; s < P->nu1; ++s) smooth(P, n, a, x, b, mg->tmp[l]);
-    orc_residual(d, n, a, x, b, mg->r[l]);
+    node_residual(P, n, a, x, b, mg->r[l]);
     orc_restrict_fw(d, n, mg->r[l], mg->b[l + 1]);
     memset(mg->x[l + 1], 0, sizeof(double) * npoints(d, mg->side[l + 1]));
     vcycle(P, mg, l + 1, a, mg->x[l + 1], mg->b[l + 1]);
@@ -590,6 +680,35 @@ void orc_solve_exact(int d, int n, double a, const double *b, double *x)
     free(T); free(lam1);
 }
 
+/*
+ * Exact solve of (W - a L_9) x = b (2D) by the same sine transform: the sine
+ * modes are eigenvectors of W and L_9 with eigenvalues
+ *   lambda_W = 2/3 + (c_p + c_q)/6,
+ *   lambda_9 = (8 (c_p + c_q) + 4 c_p c_q - 20) / (6 h^2),   c_p = cos(p pi h).
+ * With a = 0 this applies W^{-1}.
+ */
+void orc_solve_exact9(int n, double a, const double *b, double *x)
+{
+    long N = npoints(2, n);
+    double h = 1.0 / (n + 1);
+    double *T = (double *)malloc(sizeof(double) * n * n);
+    for (int p = 1; p <= n; ++p)
+        for (int i = 1; i <= n; ++i)
+            T[(p - 1) * n + (i - 1)] = sin(M_PI * (double)i * (double)p / (n + 1));
+    memcpy(x, b, sizeof(double) * N);
+    for (int ax = 0; ax < 2; ++ax) sine_along_axis(2, n, ax, x, T);
+    double scale = (2.0 / (n + 1)) * (2.0 / (n + 1));
+    for (int j = 1; j <= n; ++j)
+        for (int i = 1; i <= n; ++i) {
+            double cp = cos(M_PI * i * h), cq = cos(M_PI * j * h);
+            double lw = 2.0 / 3.0 + (cp + cq) / 6.0;
+            double l9 = (8.0 * (cp + cq) + 4.0 * cp * cq - 20.0) / (6.0 * h * h);
+            x[idx(2, n, i, j, 1)] *= scale / (lw - a * l9);
+        }
+    for (int ax = 0; ax < 2; ++ax) sine_along_axis(2, n, ax, x, T);
+    free(T);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Right-hand side f = f^E + f^I of the ODE system (Sec. 2, Sec. 3).         */
 /* ------------------------------------------------------------------------ */
@@ -600,11 +719,12 @@ static double f_explicit(const orc_problem *P, double u)
     return 0.0;
 }
 
-/* fE = f^E(u) pointwise, fI = nu L_h u */
+/* fE = f^E(u) pointwise, fI = nu L_h u (compact stencil: f~^I = W f^I = nu L_9 u) */
 static void eval_f(const orc_problem *P, const double *u, double *fE, double *fI)
 {
     long N = npoints(P->ndim, P->n);
-    orc_laplacian(P->ndim, P->n, u, fI);
+    if (P->stencil == 1) orc_laplacian9(P->n, u, fI);
+    else orc_laplacian(P->ndim, P->n, u, fI);
     for (long p = 0; p < N; ++p) {
         fI[p] *= P->nu;
         fE[p] = f_explicit(P, u[p]);
@@ -642,7 +762,9 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     const int d = P->ndim, n = P->n, M = P->M;
     if ((d != 2 && d != 3) || n < 1 || M < 2 || M > ORC_MAX_M) return 3;
     if (P->nodes < 0 || P->nodes > 2) return 3;
+    if (P->stencil == 1 && (d != 2 || P->smoother != 0)) return 3; /* compact: 2D, Jacobi */
     const long N = npoints(d, n);
+    const int W9 = P->stencil == 1;
     /* points: t_0 and the nodes; node j (0-based) is point j + off */
     const int off = P->nodes == 0 ? 0 : 1, NP = M + off;
     double tau[ORC_MAX_M], Q[ORC_MAX_M * ORC_MAX_M], w[ORC_MAX_M];
@@ -674,6 +796,8 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     double *res = (double *)malloc(sizeof(double) * N);
     double *fe_new = (double *)malloc(sizeof(double) * N);
     double *tmp = (double *)malloc(sizeof(double) * N);
+    double *v = (double *)malloc(sizeof(double) * N);
+    double *wv = (double *)malloc(sizeof(double) * N);
     orc_mg mg;
     mg_alloc(&mg, d, n);
 
@@ -704,12 +828,28 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
              *     + dt_m [f^E(u_m^{k+1}) - f^E(u_m^k)] - dt_m f^I(u_{m+1}^k)
              *     + S_m^{m+1} F(u^k),   S_m^{m+1}F = dt sum_j s_{m,j} f(u_j^k)
              * (the sum runs over the nodes j, which are points j + off) */
-            for (long p = 0; p < N; ++p) {
-                double sf = 0.0;
-                for (int j = 0; j < M; ++j)
-                    sf += Spt[m * M + j] * (FEold[(j + off) * N + p] + FIold[(j + off) * N + p]);
-                rhs[p] = Um_new[p] + dtm * (fe_new[p] - FEold[m * N + p])
-                       - dtm * FIold[(m + 1) * N + p] + P->dt * sf;
+            if (!W9) {
+                for (long p = 0; p < N; ++p) {
+                    double sf = 0.0;
+                    for (int j = 0; j < M; ++j)
+                        sf += Spt[m * M + j] * (FEold[(j + off) * N + p] + FIold[(j + off) * N + p]);
+                    rhs[p] = Um_new[p] + dtm * (fe_new[p] - FEold[m * N + p])
+                           - dtm * FIold[(m + 1) * N + p] + P->dt * sf;
+                }
+            } else {
+                /* Eq. 5: W [u_m^{k+1} + dt_m (f^E(u_m^{k+1}) - f^E(u_m^k))] - dt_m A u_{m+1}^k
+                 *        + dt sum_j s_{m,j} (W f^E(u_j^k) + A u_j^k),   A u = nu L_9 u = FI */
+                for (long p = 0; p < N; ++p) {
+                    double se = 0.0;
+                    for (int j = 0; j < M; ++j) se += Spt[m * M + j] * FEold[(j + off) * N + p];
+                    v[p] = Um_new[p] + dtm * (fe_new[p] - FEold[m * N + p]) + P->dt * se;
+                }
+                orc_apply_w(n, v, wv);
+                for (long p = 0; p < N; ++p) {
+                    double si = 0.0;
+                    for (int j = 0; j < M; ++j) si += Spt[m * M + j] * FIold[(j + off) * N + p];
+                    rhs[p] = wv[p] - dtm * FIold[(m + 1) * N + p] + P->dt * si;
+                }
             }
             /* initial guess for the spatial solver (Sec. 4.3) */
             if (P->guess == 0) memcpy(x, Uold + (m + 1) * N, sizeof(double) * N);
@@ -717,17 +857,18 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
             else memcpy(x, Um_new, sizeof(double) * N);
 
             if (P->solver == 2) {
-                orc_solve_exact(d, n, a, rhs, x);
+                if (W9) orc_solve_exact9(n, a, rhs, x);
+                else orc_solve_exact(d, n, a, rhs, x);
             } else if (P->solver == 1) {
                 for (int c = 0; c < P->mg_max_cycles; ++c) {
-                    orc_residual(d, n, a, x, rhs, tmp);
+                    node_residual(P, n, a, x, rhs, tmp);
                     if (max_abs(tmp, N) <= P->mg_tol) break;
                     vcycle(P, &mg, 0, a, x, rhs);
                     ++vcycles;
                 }
             } else if (P->solver == 3) {
                 for (int c = 0; c < n_vcycles; ++c) {
-                    orc_residual(d, n, a, x, rhs, tmp);
+                    node_residual(P, n, a, x, rhs, tmp);
                     if (max_abs(tmp, N) <= P->mg_tol) break;
                     vcycle(P, &mg, 0, a, x, rhs);
                     ++vcycles;
@@ -746,14 +887,36 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
          * max_m max_x | u_0 + dt sum_j q_{m,j} f(u_j^{k+1}) - u_m^{k+1} |   (Sec. 3) */
         for (int p = 0; p < NP; ++p) eval_f(P, U + p * N, FE + p * N, FI + p * N);
         double R = 0.0;
-        for (int m = 0; m < M; ++m)
-            for (long p = 0; p < N; ++p) {
-                double qf = 0.0;
-                for (int j = 0; j < M; ++j)
-                    qf += Q[m * M + j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
-                double r = fabs(u0[p] + P->dt * qf - U[(m + off) * N + p]);
-                if (r > R || r != r) R = r;
+        for (int m = 0; m < M; ++m) {
+            if (!W9) {
+                for (long p = 0; p < N; ++p) {
+                    double qf = 0.0;
+                    for (int j = 0; j < M; ++j)
+                        qf += Q[m * M + j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
+                    double r = fabs(u0[p] + P->dt * qf - U[(m + off) * N + p]);
+                    if (r > R || r != r) R = r;
+                }
+            } else {
+                /* W r_m = W (u_0 - u_m + dt sum_j q_{m,j} f^E_j) + dt sum_j q_{m,j} A u_j:
+                 * one inversion of W per node (Sec. 3) */
+                for (long p = 0; p < N; ++p) {
+                    double qe = 0.0;
+                    for (int j = 0; j < M; ++j) qe += Q[m * M + j] * FE[(j + off) * N + p];
+                    v[p] = u0[p] - U[(m + off) * N + p] + P->dt * qe;
+                }
+                orc_apply_w(n, v, wv);
+                for (long p = 0; p < N; ++p) {
+                    double qi = 0.0;
+                    for (int j = 0; j < M; ++j) qi += Q[m * M + j] * FI[(j + off) * N + p];
+                    wv[p] += P->dt * qi;
+                }
+                orc_solve_exact9(n, 0.0, wv, res);
+                for (long p = 0; p < N; ++p) {
+                    double r = fabs(res[p]);
+                    if (r > R || r != r) R = r;
+                }
             }
+        }
         if (res_hist) res_hist[k - 1] = R;
         if (!(R == R) || isinf(R)) { status = 2; break; }
         if (n_sweeps > 0) {
@@ -764,12 +927,25 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
         }
     }
 
-    if (P->nodes == 2) {
+    if (P->nodes == 2 && !W9) {
         /* Gauss-Legendre: tau_M < 1, end-point quadrature of the collocation rule */
         for (long p = 0; p < N; ++p) {
             double wf = 0.0;
             for (int j = 0; j < M; ++j) wf += w[j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
             u[p] = u0[p] + P->dt * wf;
+        }
+    } else if (P->nodes == 2) {
+        /* the same with f = f^E + W^{-1} A u */
+        for (long p = 0; p < N; ++p) {
+            double wi = 0.0;
+            for (int j = 0; j < M; ++j) wi += w[j] * FI[(j + off) * N + p];
+            v[p] = wi;
+        }
+        orc_solve_exact9(n, 0.0, v, wv);
+        for (long p = 0; p < N; ++p) {
+            double we = 0.0;
+            for (int j = 0; j < M; ++j) we += w[j] * FE[(j + off) * N + p];
+            u[p] = u0[p] + P->dt * (we + wv[p]);
         }
     } else {
         memcpy(u, U + (NP - 1) * N, sizeof(double) * N); /* tau_M = 1 */
@@ -778,7 +954,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     if (sweeps_out) *sweeps_out = k;
     if (vcycles_out) *vcycles_out = vcycles;
     free(U); free(Uold); free(FE); free(FI); free(FEold); free(FIold);
-    free(u0); free(rhs); free(x); free(res); free(fe_new); free(tmp);
+    free(u0); free(rhs); free(x); free(res); free(fe_new); free(tmp); free(v); free(wv);
     mg_free(&mg);
     return status;
 }
@@ -800,15 +976,38 @@ double orc_sdc_residual(const orc_problem *P, const double *u0, const double *U)
     orc_q_matrix(M, tau, Q);
     double *FE = (double *)malloc(sizeof(double) * M * N);
     double *FI = (double *)malloc(sizeof(double) * M * N);
+    double *v = (double *)malloc(sizeof(double) * N);
+    double *wv = (double *)malloc(sizeof(double) * N);
+    double *r9 = (double *)malloc(sizeof(double) * N);
     for (int m = 0; m < M; ++m) eval_f(P, U + m * N, FE + m * N, FI + m * N);
     double R = 0.0;
-    for (int m = 0; m < M; ++m)
-        for (long p = 0; p < N; ++p) {
-            double qf = 0.0;
-            for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
-            double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
-            if (r > R || r != r) R = r;
+    for (int m = 0; m < M; ++m) {
+        if (P->stencil != 1) {
+            for (long p = 0; p < N; ++p) {
+                double qf = 0.0;
+                for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
+                double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
+                if (r > R || r != r) R = r;
+            }
+        } else { /* compact stencil: r_m = W^{-1} [W (u_0 - u_m + dt Q f^E) + dt Q A u] */
+            for (long p = 0; p < N; ++p) {
+                double qe = 0.0;
+                for (int j = 0; j < M; ++j) qe += Q[m * M + j] * FE[j * N + p];
+                v[p] = u0[p] - U[m * N + p] + P->dt * qe;
+            }
+            orc_apply_w(P->n, v, wv);
+            for (long p = 0; p < N; ++p) {
+                double qi = 0.0;
+                for (int j = 0; j < M; ++j) qi += Q[m * M + j] * FI[j * N + p];
+                wv[p] += P->dt * qi;
+            }
+            orc_solve_exact9(P->n, 0.0, wv, r9);
+            for (long p = 0; p < N; ++p) {
+                double r = fabs(r9[p]);
+                if (r > R || r != r) R = r;
+            }
         }
-    free(FE); free(FI);
+    }
+    free(FE); free(FI); free(v); free(wv); free(r9);
     return R;
 }

@@ -38,6 +38,8 @@ REACTION_LINEAR = 2       # f^E(u) = lambda_e * u
 NODES_LOBATTO = 0         # Gauss-Lobatto, tau_1 = 0, tau_M = 1 (M - 1 solves per sweep)
 NODES_RADAU_RIGHT = 1     # Gauss-Radau, tau_M = 1 (M solves per sweep)
 NODES_LEGENDRE = 2        # Gauss-Legendre, interior nodes (M solves, end-point quadrature)
+STENCIL_SECOND_ORDER = 0  # 5-point (2D) / 7-point (3D) Laplacian, W = I
+STENCIL_COMPACT = 1       # 4th-order compact 9-point Laplacian with weighting matrix W (2D, Sec. 3 Eq. 5)
 
 
 def build(force: bool = False) -> str:
@@ -58,7 +60,7 @@ class _Problem(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("solver", ctypes.c_int), ("guess", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
-                ("mg_max_cycles", ctypes.c_int), ("nodes", ctypes.c_int)]
+                ("mg_max_cycles", ctypes.c_int), ("nodes", ctypes.c_int), ("stencil", ctypes.c_int)]
 
 
 @dataclass
@@ -82,11 +84,12 @@ class Problem:
     mg_tol: float = 1e-12
     mg_max_cycles: int = 100
     nodes: int = NODES_LOBATTO
+    stencil: int = STENCIL_SECOND_ORDER
 
     def _c(self) -> _Problem:
         return _Problem(self.ndim, self.n, self.nu, self.M, self.dt, self.reaction, self.lambda_e,
                         self.smoother, self.nu1, self.nu2, self.omega, self.solver, self.guess,
-                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles, self.nodes)
+                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles, self.nodes, self.stencil)
 
     @property
     def shape(self):
@@ -116,6 +119,12 @@ def _L():
         lib.orc_prolong_add.argtypes = [I, I, dp, dp]
         lib.orc_dense_solve.argtypes = [I, I, D, dp, dp]
         lib.orc_solve_exact.argtypes = [I, I, D, dp, dp]
+        lib.orc_laplacian9.argtypes = [I, dp, dp]
+        lib.orc_apply_w.argtypes = [I, dp, dp]
+        lib.orc_residual9.argtypes = [I, D, dp, dp, dp]
+        lib.orc_smooth_jacobi9.argtypes = [I, D, D, dp, dp, dp]
+        lib.orc_dense_solve9.argtypes = [I, D, dp, dp]
+        lib.orc_solve_exact9.argtypes = [I, D, dp, dp]
         lib.orc_vcycle.argtypes = [ctypes.POINTER(_Problem), D, dp, dp]
         lib.orc_isdc_step.argtypes = [ctypes.POINTER(_Problem), dp, I, I, ctypes.POINTER(I),
                                       ctypes.POINTER(ctypes.c_long), dp, dp, dp]
@@ -237,6 +246,64 @@ def dense_solve(a, b):
     d, n = _dims(b)
     x = np.zeros_like(b)
     _L().orc_dense_solve(d, n, a, _p(b), _p(x))
+    return x
+
+
+# --- 4th-order compact discretisation (Sec. 3, Eq. 5), 2D ----------------------
+def _dims2(u: np.ndarray):
+    d, n = _dims(u)
+    assert d == 2, "the compact stencil is 2D"
+    return n
+
+
+def laplacian9(u):
+    """The 9-point compact Laplacian L_9 u."""
+    u = _f64(u)
+    n = _dims2(u)
+    out = np.empty_like(u)
+    _L().orc_laplacian9(n, _p(u), _p(out))
+    return out
+
+
+def apply_w(u):
+    """The weighting matrix W u = u + (h^2/12) L_5 u."""
+    u = _f64(u)
+    n = _dims2(u)
+    out = np.empty_like(u)
+    _L().orc_apply_w(n, _p(u), _p(out))
+    return out
+
+
+def residual9(a, x, b):
+    x, b = _f64(x), _f64(b)
+    n = _dims2(x)
+    r = np.empty_like(x)
+    _L().orc_residual9(n, a, _p(x), _p(b), _p(r))
+    return r
+
+
+def smooth_jacobi9(a, omega, x, b):
+    x, b = _f64(x).copy(), _f64(b)
+    n = _dims2(x)
+    tmp = np.empty_like(x)
+    _L().orc_smooth_jacobi9(n, a, omega, _p(x), _p(b), _p(tmp))
+    return x
+
+
+def dense_solve9(a, b):
+    b = _f64(b)
+    n = _dims2(b)
+    x = np.zeros_like(b)
+    _L().orc_dense_solve9(n, a, _p(b), _p(x))
+    return x
+
+
+def solve_exact9(a, b):
+    """(W - a L_9)^{-1} b by the sine transform (a = 0: W^{-1} b)."""
+    b = _f64(b)
+    n = _dims2(b)
+    x = np.zeros_like(b)
+    _L().orc_solve_exact9(n, a, _p(b), _p(x))
     return x
 
 

@@ -26,3 +26,17 @@ def red_mask(d, n):
     """True where i+j(+k) is even with 1-based interior indices."""
     g = np.indices((n,) * d).sum(axis=0) + d  # 0-based indices sum + d
     return (g % 2 == 0).reshape(-1)
+
+
+def laplacian9(n):
+    """The 4th-order compact Laplacian as D_xx + D_yy + (h^2/6) D_xx D_yy
+    (Kronecker products of the 1D second difference; 2D)."""
+    h = 1.0 / (n + 1)
+    L1, I = lap1d(n), np.eye(n)
+    return np.kron(I, L1) + np.kron(L1, I) + h ** 2 / 6.0 * np.kron(L1, L1)
+
+
+def weighting(n):
+    """W = I + (h^2/12) L_5 (2D)."""
+    h = 1.0 / (n + 1)
+    return np.eye(n * n) + h ** 2 / 12.0 * laplacian(2, n)
