@@ -93,6 +93,10 @@ typedef struct {
                              sweeps per pass over HBM (temporal blocking; the same FP32
                              operations in the same order, so the same result bit for bit).
                              Other configurations ignore it. */
+    int    stencil;       /* 0 (default): 5-point (2D) / 7-point (3D) Laplacian, W = I.
+                             1: the 4th-order compact 9-point Laplacian with the weighting
+                             matrix W of Sec. 3 (Eq. 5), 2D, damped-Jacobi smoothing, FP64
+                             V-cycles (other combinations: ISDC_ERR_UNSUPPORTED). */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream

@@ -1,11 +1,13 @@
 """Accumulated V-cycles (sweeps) of classical SDC and ISDC on the heat equation
 of Sec. 4.1, computed with the oracle, beside the paper's Table 1a.
 
-TEST INFRASTRUCTURE: runs the oracle only.  Usage: python -m oracle.table1
+TEST INFRASTRUCTURE: runs the oracle only.
+Usage: python -m oracle.table1 [--compact]
 
 Settings: unit square, u0 = sin(pi x) sin(pi y), zero Dirichlet values, one
-step dt = 0.001, 63^2 interior points (dx = 1/64), 5-point Laplacian (the paper
-uses a 4th-order compact stencil), SDC residual < 5e-8.  Classical SDC: V-cycles
+step dt = 0.001, 63^2 interior points (dx = 1/64), the 5-point Laplacian or,
+with --compact, the paper's 4th-order compact stencil with the weighting
+matrix W (Sec. 3, Eq. 5), SDC residual < 5e-8.  Classical SDC: V-cycles
 until the node residual is <= mg_tol.  ISDC: at most L = 2 V-cycles per node
 solve, stopping early at the same mg_tol (the paper's counts are below
 K~(M-1)L, so L acts as a cap).  The paper does not describe its multigrid
@@ -30,24 +32,27 @@ PAPER_TABLE_1A = {
 }
 
 
-def heat_problem(nu, M, solver, smoother=O.SMOOTHER_JACOBI, nu1=3, nu2=3, mg_tol=5e-9):
+def heat_problem(nu, M, solver, smoother=O.SMOOTHER_JACOBI, nu1=3, nu2=3, mg_tol=5e-9,
+                 stencil=O.STENCIL_SECOND_ORDER):
     return O.Problem(2, 63, float(nu), M, 0.001, reaction=O.REACTION_NONE, smoother=smoother, nu1=nu1, nu2=nu2,
-                     solver=solver, tol=5e-8, max_sweeps=100, mg_tol=mg_tol, mg_max_cycles=100)
+                     solver=solver, tol=5e-8, max_sweeps=100, mg_tol=mg_tol, mg_max_cycles=100, stencil=stencil)
 
 
-def table(smoother=O.SMOOTHER_JACOBI, nu1=3, nu2=3, mg_tol=5e-9):
+def table(smoother=O.SMOOTHER_JACOBI, nu1=3, nu2=3, mg_tol=5e-9, stencil=O.STENCIL_SECOND_ORDER):
     u0 = sine_mode(2, 63)
     rows = {}
     for nu in (1, 10, 100):
         for M in (3, 5, 7):
-            sdc = O.isdc_step(heat_problem(nu, M, O.SOLVER_MG_TOL, smoother, nu1, nu2, mg_tol), u0, 0, 0)
-            isdc = O.isdc_step(heat_problem(nu, M, O.SOLVER_ISDC_CAPPED, smoother, nu1, nu2, mg_tol), u0, 0, 2)
+            sdc = O.isdc_step(heat_problem(nu, M, O.SOLVER_MG_TOL, smoother, nu1, nu2, mg_tol, stencil), u0, 0, 0)
+            isdc = O.isdc_step(heat_problem(nu, M, O.SOLVER_ISDC_CAPPED, smoother, nu1, nu2, mg_tol, stencil),
+                               u0, 0, 2)
             rows[(nu, M)] = (sdc.vcycles, sdc.sweeps, isdc.vcycles, isdc.sweeps)
     return rows
 
 
 def main():
-    rows = table()
+    compact = "--compact" in sys.argv[1:]
+    rows = table(stencil=O.STENCIL_COMPACT if compact else O.STENCIL_SECOND_ORDER)
     print("| nu | M | SDC (this) | ISDC (this) | savings | SDC (paper) | ISDC (paper) | savings (paper) |")
     print("|---|---|---|---|---|---|---|---|")
     for (nu, M), (sc, ss, ic, isw) in rows.items():

@@ -165,6 +165,44 @@ inline void coarse_inverse(int dim, double a, std::vector<double>& inv) {
   }
 }
 
+// Inverse of the dense 9 x 9 matrix of W - a L_9 (4th-order compact stencil,
+// 2D) on the side-3 grid, row-major.
+inline void coarse_inverse9(double a, std::vector<double>& inv) {
+  const int n = 3, Np = 9;
+  const double h = 1.0 / (n + 1), q = a / (6.0 * h * h);
+  const double c0 = 8.0 / 12.0 + 20.0 * q, ce = 1.0 / 12.0 - 4.0 * q, cc = -q;
+  std::vector<double> A(Np * Np, 0.0);
+  for (int p = 0; p < Np; ++p) {
+    const int i = p % n, j = p / n;
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
+        const int nz = (di != 0) + (dj != 0);
+        A[p * Np + ii + n * jj] = nz == 0 ? c0 : (nz == 1 ? ce : cc);
+      }
+  }
+  inv.assign(Np * Np, 0.0);
+  for (int p = 0; p < Np; ++p) inv[p * Np + p] = 1.0;
+  for (int col = 0; col < Np; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Np; ++r)
+      if (std::fabs(A[r * Np + col]) > std::fabs(A[piv * Np + col])) piv = r;
+    if (piv != col)
+      for (int c = 0; c < Np; ++c) {
+        std::swap(A[col * Np + c], A[piv * Np + c]);
+        std::swap(inv[col * Np + c], inv[piv * Np + c]);
+      }
+    const double s = 1.0 / A[col * Np + col];
+    for (int c = 0; c < Np; ++c) { A[col * Np + c] *= s; inv[col * Np + c] *= s; }
+    for (int r = 0; r < Np; ++r) {
+      if (r == col) continue;
+      const double f = A[r * Np + col];
+      if (f == 0.0) continue;
+      for (int c = 0; c < Np; ++c) { A[r * Np + c] -= f * A[col * Np + c]; inv[r * Np + c] -= f * inv[col * Np + c]; }
+    }
+  }
+}
 
 }  // namespace host
 }  // namespace isdc

@@ -23,6 +23,7 @@
 #include "host_util.h"
 #include "kernels.cuh"
 #include "sdc_kernels.cuh"
+#include "compact_kernels.cuh"
 
 #define ISDC_API extern "C" __attribute__((visibility("default")))
 
@@ -53,12 +54,12 @@ struct Hier {
 // Kernel classes timed by the built-in profiler (isdc_profile_*).
 enum ProfClass {
   PC_SPREAD, PC_EVAL_F, PC_RHS, PC_SWEEP_END, PC_SMOOTH0, PC_RESIDUAL0, PC_RESTRICT0, PC_PROLONG0,
-  PC_SMOOTHC, PC_RESIDUALC, PC_RESTRICTC, PC_PROLONGC, PC_BOTTOM, PC_DEFECT, PC_UPDATE, PC_RESNORM, PC_COUNT
+  PC_SMOOTHC, PC_RESIDUALC, PC_RESTRICTC, PC_PROLONGC, PC_BOTTOM, PC_DEFECT, PC_UPDATE, PC_RESNORM, PC_WINV, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT] = {
     "spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine", "prolong_fine",
     "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse", "bottom", "defect", "update",
-    "resnorm"};
+    "resnorm", "w_inverse"};
 
 struct Profiler {
   bool on = false;
@@ -95,6 +96,9 @@ struct isdc_ctx {
   double* U = nullptr;  // P point arrays (t_0, then the nodes), point-major
   double* F = nullptr;  // f(u_p), P arrays
   double* C = nullptr;  // sweep constants, P-1 arrays
+  int stencil = 0;      // 0: 5/7-point, W = I; 1: 4th-order compact with W (2D)
+  double* G = nullptr;  // compact: nu L_9 u per point (P arrays); F holds f~ = W f^E + nu L_9 u
+  double* Rs = nullptr; // compact: W-weighted SDC residuals and two Jacobi iterates, 3 (P-1) arrays
   double* b = nullptr;  // right-hand side of the current node solve
   double* u_dev = nullptr;  // device copy of u for isdc_step_host
   Hier<double> h64;
@@ -267,7 +271,9 @@ isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   }
   H.nlev = l;
   H.lb = 0;
-  while (H.side[H.lb] > bottom_threshold(ctx->dim, sizeof(T) == 8)) ++H.lb;
+  if (ctx->stencil == 1) H.lb = H.nlev - 1;  // compact: grid-wide levels, dense side-3 solve
+  else
+    while (H.side[H.lb] > bottom_threshold(ctx->dim, sizeof(T) == 8)) ++H.lb;
   for (int q = 0; q < H.nlev; ++q) {
     const size_t bytes = H.npts[q] * sizeof(T);
     const bool global_level = q < H.lb;
@@ -308,8 +314,14 @@ void free_hier(Hier<T>& H, bool own_level0) {
 template <typename T>
 isdc_status upload_ainv(isdc_ctx* ctx, Hier<T>& H, int slot, double a) {
   std::vector<double> inv;
-  coarse_inverse(ctx->dim, a, inv);
-  const double d3 = 1.0 + 2.0 * ctx->dim * a * 16.0;  // h = 1/4 on the side-3 grid
+  double d3;
+  if (ctx->stencil == 1) {  // c0 (W - a L_9)^{-1}, c0 = 2/3 + 10 a / (3 h^2), h = 1/4
+    coarse_inverse9(a, inv);
+    d3 = 2.0 / 3.0 + 10.0 * a * 16.0 / 3.0;
+  } else {
+    coarse_inverse(ctx->dim, a, inv);
+    d3 = 1.0 + 2.0 * ctx->dim * a * 16.0;  // h = 1/4 on the side-3 grid
+  }
   std::vector<T> tv(inv.size());
   for (size_t q = 0; q < inv.size(); ++q) tv[q] = T(d3 * inv[q]);
   const size_t each = ctx->dim == 2 ? 81 : 729;
@@ -610,6 +622,188 @@ isdc_status node_solve(isdc_ctx* ctx, int slot, double a, double* x, const doubl
   return ISDC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 4th-order compact stencil (Sec. 3, Eq. 5), 2D, FP64: multigrid on
+// (W - a L_9) x = b and the sweep pieces that differ from W = I.
+// ---------------------------------------------------------------------------
+struct Coef9 {
+  double c0, ke, kc;  // diagonal; row-scaled edge and corner couplings
+};
+inline Coef9 coef9(int s, double a) {
+  const double h = 1.0 / (s + 1), q = a / (6.0 * h * h);
+  const double c0 = 2.0 / 3.0 + 20.0 * q, ce = 1.0 / 12.0 - 4.0 * q, cc = -q;
+  return {c0, -ce / c0, -cc / c0};
+}
+
+// Damped-Jacobi sweeps on level l (x ping-pongs between home and H.t[l]).
+isdc_status smooth_level9(isdc_ctx* ctx, Hier<double>& H, int l, double a, double*& x, double* home, const double* b,
+                          bool& zero, int sweeps) {
+  const int s = H.side[l];
+  const Coef9 k = coef9(s, a);
+  for (int it = 0; it < sweeps; ++it) {
+    double* out = (x == H.t[l]) ? home : H.t[l];
+    {
+      const double Np = double(H.npts[l]);
+      ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 2.0 : 3.0) * Np * 8, (zero ? 1.0 : 12.0) * Np, true);
+      k_jacobi9<double><<<pt_grid(2, s), kBlock, 0, ctx->stream>>>(s, k.ke, k.kc, ctx->opt.omega, x, b, out,
+                                                                   zero ? 1 : 0);
+    }
+    LAUNCH_CHECK(ctx);
+    x = out;
+    zero = false;
+  }
+  return ISDC_OK;
+}
+
+// One V-cycle on the row-scaled compact system x - ke E - kc C = beta.
+isdc_status vcycle9(isdc_ctx* ctx, int slot, double a, double* x0, const double* b0) {
+  Hier<double>& H = ctx->h64;
+  double* xcur[kMaxLevels];
+  isdc_status st;
+  for (int l = 0; l < H.lb; ++l) {
+    double* home = l == 0 ? x0 : H.x[l];
+    double* x = home;
+    const double* b = l == 0 ? b0 : H.b[l];
+    bool zero = l > 0;
+    const int s = H.side[l], sc = H.side[l + 1];
+    if (ctx->opt.nu1 == 0 && zero) {
+      CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(double), ctx->stream));
+      zero = false;
+    }
+    if ((st = smooth_level9(ctx, H, l, a, x, home, b, zero, ctx->opt.nu1)) != ISDC_OK) return st;
+    const Coef9 k = coef9(s, a);
+    const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+    {
+      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * Np * 8, 11.0 * Np, true);
+      k_residual9<double><<<pt_grid(2, s), kBlock, 0, ctx->stream>>>(s, k.ke, k.kc, x, b, H.r[l]);
+    }
+    LAUNCH_CHECK(ctx);
+    {
+      const double ws = k.c0 / (coef9(sc, a).c0 * 16.0);
+      ProfScope ps(ctx, l == 0 ? PC_RESTRICT0 : PC_RESTRICTC, (Np + Nc) * 8, 9.0 * Nc, true);
+      k_restrict<double, 2, false><<<pt_grid(2, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
+    }
+    LAUNCH_CHECK(ctx);
+    xcur[l] = x;
+  }
+  {  // side-3 level: dense solve (a one-level grid is the whole hierarchy)
+    const double* bb = H.lb == 0 ? b0 : H.b[H.lb];
+    double* xb = H.lb == 0 ? x0 : H.x[H.lb];
+    ProfScope ps(ctx, PC_BOTTOM, 18.0 * 8, 81.0, true);
+    k_coarse9<double><<<1, 32, 0, ctx->stream>>>(H.Ainv + size_t(slot) * 81, bb, xb);
+    LAUNCH_CHECK(ctx);
+    xcur[H.lb] = xb;
+  }
+  for (int l = H.lb - 1; l >= 0; --l) {
+    const int sc = H.side[l + 1];
+    double* home = l == 0 ? x0 : H.x[l];
+    double* x = xcur[l];
+    {
+      const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+      ProfScope ps(ctx, l == 0 ? PC_PROLONG0 : PC_PROLONGC, (2.0 * Np + Nc) * 8, 2.0 * Np, true);
+      k_prolong_add<double, 2, false><<<pt_grid(2, sc + 1), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
+    }
+    LAUNCH_CHECK(ctx);
+    bool zero = false;
+    if ((st = smooth_level9(ctx, H, l, a, x, home, l == 0 ? b0 : H.b[l], zero, ctx->opt.nu2)) != ISDC_OK) return st;
+    xcur[l] = x;
+  }
+  if (xcur[0] != x0)
+    CUDA_TRY(ctx, cudaMemcpyAsync(x0, xcur[0], H.npts[0] * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return ISDC_OK;
+}
+
+isdc_status node_residual_norm9(isdc_ctx* ctx, double a, const double* x, const double* b, double* out) {
+  const int s = ctx->n;
+  const Coef9 k = coef9(s, a);
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal + 1, 0, sizeof(unsigned long long), ctx->stream));
+  {
+    ProfScope ps(ctx, PC_RESNORM, 16.0 * double(ctx->N), 13.0 * double(ctx->N), true);
+    k_resnorm9<<<pt_grid(2, s), kBlock, 0, ctx->stream>>>(s, k.ke, k.kc, k.c0, x, b, ctx->d_scal + 1);
+  }
+  LAUNCH_CHECK(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  unsigned long long bits = ctx->h_scal[1];
+  std::memcpy(out, &bits, sizeof(double));
+  return ISDC_OK;
+}
+
+// W^{-1} of `count` arrays rho (each N) by Jacobi steps r <- (3/2) rho - E(r)/8,
+// starting from 0; the result is in *res (one of the two scratch sets).
+constexpr int kWinvSweepIters = 16;  // residual for the stopping test: error <= 4.5 * 2^-16 relative
+constexpr int kWinvEndIters = 54;    // Gauss-Legendre end value: error below FP64 rounding
+isdc_status w_inverse(isdc_ctx* ctx, int count, const double* rho, double* s0, double* s1, int iters,
+                      const double** res) {
+  const int n = ctx->n;
+  const size_t N = ctx->N;
+  const dim3 g(unsigned((n + kBX - 1) / kBX), unsigned((n + kBY - 1) / kBY), unsigned(count));
+  const double* in = nullptr;
+  for (int it = 0; it < iters; ++it) {
+    double* out = (it & 1) ? s1 : s0;
+    {
+      ProfScope ps(ctx, PC_WINV, (it ? 3.0 : 2.0) * 8.0 * double(N) * count, 6.0 * double(N) * count, true);
+      k_winv_jacobi<<<g, kBlock, 0, ctx->stream>>>(n, N, rho, in, out);
+    }
+    LAUNCH_CHECK(ctx);
+    in = out;
+  }
+  *res = in;
+  return ISDC_OK;
+}
+
+template <int OFF, int P>
+void launch_sweep_end9_p(isdc_ctx* ctx, double nu6) {
+  k_sweep_end9<OFF, P><<<pt_grid(2, ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->N, nu6, ctx->opt.reaction,
+                                                                       ctx->tables, ctx->U, ctx->F, ctx->G, ctx->C,
+                                                                       ctx->Rs);
+}
+
+// End of a compact sweep: f~ at the last point, the W-weighted residuals, the
+// next C_m; then W^{-1} of the residuals and their max norm into d_scal[0].
+isdc_status sweep_end9(isdc_ctx* ctx) {
+  const int P = ctx->P;
+  const size_t N = ctx->N;
+  const double nu6 = ctx->nu / (6.0 * ctx->h * ctx->h);
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
+  {
+    const double Pd = P, M = ctx->M, Np = double(N);
+    ProfScope ps(ctx, PC_SWEEP_END, (2.0 * Pd + 2.0 * (Pd - 1.0) + (Pd - 1.0) + 2.0) * 8.0 * Np,
+                 (30.0 + (Pd - 1.0) * (M + 8.0) + 4.0 * (Pd - 1.0)) * Np, true);
+    if (ctx->off) {
+      switch (P) {
+        case 3: launch_sweep_end9_p<1, 3>(ctx, nu6); break;
+        case 4: launch_sweep_end9_p<1, 4>(ctx, nu6); break;
+        case 5: launch_sweep_end9_p<1, 5>(ctx, nu6); break;
+        case 6: launch_sweep_end9_p<1, 6>(ctx, nu6); break;
+        case 7: launch_sweep_end9_p<1, 7>(ctx, nu6); break;
+        default: launch_sweep_end9_p<1, 8>(ctx, nu6); break;
+      }
+    } else {
+      switch (P) {
+        case 2: launch_sweep_end9_p<0, 2>(ctx, nu6); break;
+        case 3: launch_sweep_end9_p<0, 3>(ctx, nu6); break;
+        case 4: launch_sweep_end9_p<0, 4>(ctx, nu6); break;
+        case 5: launch_sweep_end9_p<0, 5>(ctx, nu6); break;
+        case 6: launch_sweep_end9_p<0, 6>(ctx, nu6); break;
+        default: launch_sweep_end9_p<0, 7>(ctx, nu6); break;
+      }
+    }
+  }
+  LAUNCH_CHECK(ctx);
+  const size_t R = size_t(P - 1) * N;
+  const double* r = nullptr;
+  isdc_status st = w_inverse(ctx, P - 1, ctx->Rs, ctx->Rs + R, ctx->Rs + 2 * R, kWinvSweepIters, &r);
+  if (st != ISDC_OK) return st;
+  {
+    ProfScope ps(ctx, PC_WINV, double(R) * 8, 0.0, true);
+    k_maxabs<<<4 * 152, 256, 0, ctx->stream>>>(R, r, ctx->d_scal);
+  }
+  LAUNCH_CHECK(ctx);
+  return ISDC_OK;
+}
+
 template <int DIM>
 isdc_status node_residual_norm(isdc_ctx* ctx, double a, const double* x, const double* b, double* out) {
   const int s = ctx->n;
@@ -682,11 +876,48 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   return ISDC_OK;
 }
 
+// One SDC sweep with the compact stencil (Sec. 3, Eq. 5): the right-hand
+// sides carry W, the node solves invert W - dt_m nu L_9 (FP64 V-cycles).
+isdc_status sweep_once9(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
+  const int n = ctx->n, P = ctx->P;
+  const size_t N = ctx->N;
+  const double nu6 = ctx->nu / (6.0 * ctx->h * ctx->h);
+  isdc_status st;
+  for (int m = 0; m < P - 1; ++m) {
+    const double dtm = ctx->tables.dtm[m], a = dtm * ctx->nu;
+    const Coef9 k = coef9(n, a);
+    {
+      ProfScope ps(ctx, PC_RHS, (m >= 1 ? 5.0 : 3.0) * 8.0 * double(N), (m >= 1 ? 40.0 : 12.0) * double(N), true);
+      k_rhs9<<<pt_grid(2, n), kBlock, 0, ctx->stream>>>(n, nu6, ctx->opt.reaction, dtm, 1.0 / k.c0, ctx->U + m * N,
+                                                        ctx->C + m * N, ctx->b, m >= 1 ? ctx->F + m * N : nullptr,
+                                                        m >= 1 ? ctx->G + m * N : nullptr);
+    }
+    LAUNCH_CHECK(ctx);
+    double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
+    if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
+      for (int c = 0; c < n_vcycles; ++c)
+        if ((st = vcycle9(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+      *vcycles += n_vcycles;
+    } else {  // classical SDC, or L as a cap, with the node residual test
+      const int limit = n_vcycles > 0 ? n_vcycles : ctx->opt.mg_max_cycles;
+      for (int c = 0; c < limit; ++c) {
+        double rn;
+        if ((st = node_residual_norm9(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
+        if (!(rn > ctx->opt.mg_tol)) break;
+        if ((st = vcycle9(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+        ++*vcycles;
+      }
+    }
+  }
+  return sweep_end9(ctx);
+}
+
 // One SDC sweep (Sec. 2, Eq. 4): the P-1 node solves (M-1 for Gauss-Lobatto,
 // M otherwise) and the sweep end (f at the last point, SDC residual, next C_m).
 // *vcycles accumulates the V-cycles spent.
 template <int DIM>
 isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
+  if (ctx->stencil == 1) return sweep_once9(ctx, n_vcycles, vcycles);
   const int n = ctx->n, P = ctx->P;
   const size_t N = ctx->N;
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
@@ -795,7 +1026,28 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   const size_t N = ctx->N;
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   isdc_status st;
-  if (ctx->nodes_pending) {
+  const double nu6 = ctx->nu / (6.0 * ctx->h * ctx->h);
+  if (ctx->nodes_pending && ctx->stencil == 1) {
+    // resume with the compact stencil: f~ and nu L_9 u at t_0 and every node
+    if (ctx->off)
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int m = 0; m < P; ++m) {
+      {
+        ProfScope ps(ctx, PC_EVAL_F, 24.0 * double(N), 30.0 * double(N), true);
+        k_eval_f9<<<pt_grid(2, n), kBlock, 0, ctx->stream>>>(n, nu6, ctx->opt.reaction, ctx->U + m * N,
+                                                             ctx->F + m * N, ctx->G + m * N);
+      }
+      LAUNCH_CHECK(ctx);
+    }
+    ctx->nodes_pending = 0;
+  } else if (ctx->stencil == 1) {
+    {
+      ProfScope ps(ctx, PC_SPREAD, (1.0 + 3.0 * P) * 8.0 * double(N), 30.0 * double(N), true);
+      k_spread9<<<pt_grid(2, n), kBlock, 0, ctx->stream>>>(n, N, nu6, ctx->opt.reaction, P, u, ctx->U, ctx->F,
+                                                           ctx->G);
+    }
+    LAUNCH_CHECK(ctx);
+  } else if (ctx->nodes_pending) {
     // resume: the nodes were set; t_0 (not a node unless Gauss-Lobatto) is u
     if (ctx->off)
       CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -817,7 +1069,8 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
     LAUNCH_CHECK(ctx);
   }
   ctx->cprime = ctx->opt.vcycle_fp32 && n_vcycles > 0 && !ctx->opt.vcycle_cap;
-  if ((st = sweep_end<DIM>(ctx)) != ISDC_OK) return st;  // C_m of the first sweep
+  // C_m of the first sweep
+  if ((st = ctx->stencil == 1 ? sweep_end9(ctx) : sweep_end<DIM>(ctx)) != ISDC_OK) return st;
 
   const bool until_tol = n_sweeps <= 0;
   const int cap = until_tol ? ctx->opt.max_sweeps : n_sweeps;
@@ -867,7 +1120,20 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   }
   CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 ctx->stream));
-  if (ctx->node_kind == ISDC_NODES_GAUSS_LEGENDRE) {
+  if (ctx->node_kind == ISDC_NODES_GAUSS_LEGENDRE && ctx->stencil == 1) {
+    // the same with f = f^E + W^{-1} nu L_9 u: u = u_0 + dt sum w f^E + W^{-1} (dt sum w nu L_9 u)
+    {
+      ProfScope ps(ctx, PC_SPREAD, (ctx->M + 1.0) * 8.0 * double(N), 2.0 * ctx->M * double(N), true);
+      k_gauss_end9_sum<<<pt_grid(2, n), kBlock, 0, ctx->stream>>>(n, N, ctx->ends, ctx->G, ctx->b);
+    }
+    LAUNCH_CHECK(ctx);
+    const double* wy = nullptr;
+    if ((st = w_inverse(ctx, 1, ctx->b, ctx->Rs, ctx->Rs + N, kWinvEndIters, &wy)) != ISDC_OK) return st;
+    {
+      ProfScope ps(ctx, PC_SPREAD, (ctx->M + 3.0) * 8.0 * double(N), 4.0 * ctx->M * double(N), true);
+      k_gauss_end9<<<pt_grid(2, n), kBlock, 0, ctx->stream>>>(n, N, ctx->ends, ctx->opt.reaction, ctx->U, wy, u);
+    }
+  } else if (ctx->node_kind == ISDC_NODES_GAUSS_LEGENDRE) {
     // tau_M < 1: the step ends with the full-step quadrature of the collocation rule
     ProfScope ps(ctx, PC_SPREAD, (ctx->M + 2.0) * 8.0 * double(N), 2.0 * ctx->M * double(N), true);
     k_gauss_end<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, ctx->ends, ctx->U, ctx->F, u);
@@ -1011,6 +1277,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->vcycle_cap = 0;
   opt->use_graphs = 1;
   opt->temporal_blocking = -1;
+  opt->stencil = 0;
   opt->stream = nullptr;
   return ISDC_OK;
 }
@@ -1043,6 +1310,8 @@ ISDC_API void isdc_destroy(isdc_ctx* ctx) {
   cudaFree(ctx->U);
   cudaFree(ctx->F);
   cudaFree(ctx->C);
+  cudaFree(ctx->G);
+  cudaFree(ctx->Rs);
   cudaFree(ctx->b);
   cudaFree(ctx->u_dev);
   free_hier(ctx->h64, false);
@@ -1097,6 +1366,10 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps and mg_max_cycles must be >= 1");
   if (o.temporal_blocking < -1 || o.temporal_blocking > 2)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "temporal_blocking must be -1, 0, 1 or 2");
+  if (o.stencil != 0 && o.stencil != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown stencil %d", o.stencil);
+  if (o.stencil == 1 && (ndim != 2 || o.smoother != ISDC_SMOOTHER_JACOBI || o.vcycle_fp32))
+    return fail(nullptr, ISDC_ERR_UNSUPPORTED,
+                "the compact stencil is implemented in 2D with damped-Jacobi smoothing and FP64 V-cycles");
 
   isdc_ctx* ctx = new isdc_ctx();
   ctx->dim = ndim;
@@ -1110,6 +1383,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   ctx->dt = dt;
   ctx->h = 1.0 / double(n + 1);
   ctx->opt = o;
+  ctx->stencil = o.stencil;
   auto bail = [&](isdc_status st) {
     snprintf(g_create_error, sizeof g_create_error, "%s", ctx->err);
     isdc_destroy(ctx);
@@ -1154,6 +1428,10 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   CREATE_TRY(cudaMalloc(&ctx->U, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->F, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->C, size_t(P - 1) * N * sizeof(double)));
+  if (ctx->stencil == 1) {
+    CREATE_TRY(cudaMalloc(&ctx->G, size_t(P) * N * sizeof(double)));
+    CREATE_TRY(cudaMalloc(&ctx->Rs, 3 * size_t(P - 1) * N * sizeof(double)));
+  }
   CREATE_TRY(cudaMalloc(&ctx->b, N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->d_scal, 4 * sizeof(unsigned long long)));
   CREATE_TRY(cudaMemset(ctx->d_scal, 0, 4 * sizeof(unsigned long long)));
@@ -1186,7 +1464,9 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   } else {
     if ((st = alloc_hier(ctx, ctx->h64, false)) != ISDC_OK) return bail(st);
-    if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
+    if (ctx->stencil == 0) {
+      if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
+    }
     for (int m = 0; m < P - 1; ++m)
       if ((st = upload_ainv(ctx, ctx->h64, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   }
@@ -1273,6 +1553,13 @@ ISDC_API isdc_status isdc_vcycles(isdc_ctx* ctx, double a, double* x, const doub
   if (ctx->opt.vcycle_fp32) st = upload_ainv(ctx, ctx->h32, ctx->spare_slot, a);
   else st = upload_ainv(ctx, ctx->h64, ctx->spare_slot, a);
   if (st != ISDC_OK) return st;
+  if (ctx->stencil == 1) {  // (W - a L_9) x = b, row-scaled by c0
+    k_scale<double><<<4 * 152, 256, 0, ctx->stream>>>(ctx->N, 1.0 / coef9(ctx->n, a).c0, b, ctx->b);
+    LAUNCH_CHECK(ctx);
+    for (int c = 0; c < n_cycles; ++c)
+      if ((st = vcycle9(ctx, ctx->spare_slot, a, x, ctx->b)) != ISDC_OK) return st;
+    return ISDC_OK;
+  }
   // the V-cycles act on the row-scaled system: beta = b / d (in the context's rhs buffer)
   const double d0 = level_coef(ctx->dim, ctx->n, a).d;
   k_scale<double><<<4 * 152, 256, 0, ctx->stream>>>(ctx->N, 1.0 / d0, b, ctx->b);

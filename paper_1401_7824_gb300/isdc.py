@@ -32,6 +32,8 @@ ISDC_SMOOTHER_JACOBI = 0
 ISDC_SMOOTHER_RBGS = 1
 ISDC_REACTION_NONE = 0
 ISDC_REACTION_ALLEN_CAHN = 1
+ISDC_STENCIL_SECOND_ORDER = 0
+ISDC_STENCIL_COMPACT = 1
 
 
 class isdc_options(ctypes.Structure):
@@ -39,7 +41,7 @@ class isdc_options(ctypes.Structure):
                 ("omega", ctypes.c_double), ("vcycle_fp32", ctypes.c_int), ("reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_max_cycles", ctypes.c_int), ("vcycle_cap", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("temporal_blocking", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("temporal_blocking", ctypes.c_int), ("stencil", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class isdc_kernel_stat(ctypes.Structure):
@@ -251,7 +253,7 @@ def isdc_vcycles_static(ndim, n, a: float, x, b, n_cycles: int, smoother=ISDC_SM
 
 PROFILE_CLASSES = ["spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine",
                    "prolong_fine", "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse",
-                   "bottom", "defect", "update", "resnorm"]
+                   "bottom", "defect", "update", "resnorm", "w_inverse"]
 
 
 def isdc_profile_enable(ctx, enable, classes=None):
@@ -417,13 +419,14 @@ class Isdc:
     def __init__(self, ndim, n, nu, M, dt, *, smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1,
                  omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
                  max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True,
-                 temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stream=None):
+                 temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stencil=ISDC_STENCIL_SECOND_ORDER,
+                 stream=None):
         import torch
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
         o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
         o.mg_tol, o.mg_max_cycles, o.vcycle_cap = mg_tol, mg_max_cycles, int(vcycle_cap)
-        o.use_graphs, o.temporal_blocking = int(use_graphs), int(temporal_blocking)
+        o.use_graphs, o.temporal_blocking, o.stencil = int(use_graphs), int(temporal_blocking), int(stencil)
         s = stream if stream is not None else torch.cuda.current_stream()
         # torch's default stream has handle 0, which the C ABI reads as "create a
         # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.

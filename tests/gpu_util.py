@@ -29,4 +29,6 @@ def make_gpu(p: O.Problem, vcycle_fp32=False, **kw):
                   else G.ISDC_REACTION_NONE,
                   tol=p.tol, max_sweeps=p.max_sweeps, mg_tol=p.mg_tol, mg_max_cycles=p.mg_max_cycles,
                   nodes={O.NODES_LOBATTO: G.ISDC_NODES_GAUSS_LOBATTO, O.NODES_RADAU_RIGHT: G.ISDC_NODES_RADAU_RIGHT,
-                         O.NODES_LEGENDRE: G.ISDC_NODES_GAUSS_LEGENDRE}[p.nodes], **kw)
+                         O.NODES_LEGENDRE: G.ISDC_NODES_GAUSS_LEGENDRE}[p.nodes],
+                  stencil={O.STENCIL_SECOND_ORDER: G.ISDC_STENCIL_SECOND_ORDER,
+                           O.STENCIL_COMPACT: G.ISDC_STENCIL_COMPACT}[p.stencil], **kw)

@@ -1,0 +1,108 @@
+"""Parity of the CUDA path with the 4th-order compact stencil and weighting
+matrix W (Sec. 3, Eq. 5; 2D, FP64) against the oracle on the same seeded inputs.
+The library inverts W for the SDC residual with 16 Jacobi steps (each halves
+the max-norm error), so residuals agree to ~1e-4 relative; the solution does
+not depend on that and agrees to the FP64 budget (relative L2 1e-12 per step)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import make_gpu, rel_l2, to_dev
+from isdc_inputs import initial_condition
+
+pytestmark = pytest.mark.gpu
+
+C, J = O.STENCIL_COMPACT, O.SMOOTHER_JACOBI
+
+
+@pytest.mark.parametrize("n,a,nu1,nu2", [(63, 0.001, 1, 1), (127, 0.0003, 2, 1), (31, 0.05, 1, 2), (3, 0.2, 1, 1)])
+def test_compact_vcycles_match_oracle(n, a, nu1, nu2):
+    p = O.Problem(2, n, 0.1, 3, 0.05, stencil=C, smoother=J, nu1=nu1, nu2=nu2)
+    rng = np.random.default_rng(500 + n)
+    x0, b = rng.standard_normal(p.shape), rng.standard_normal(p.shape)
+    ref = x0.copy()
+    for _ in range(3):
+        ref = O.vcycle(p, a, ref, b)
+    g = make_gpu(p)
+    x = to_dev(x0)
+    g.vcycles(a, x, to_dev(b), 3)
+    assert np.abs(x.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+CASES = [
+    # n, nu, M, dt, L, nodes
+    (63, 0.1, 3, 0.05, 2, O.NODES_LOBATTO),
+    (127, 1.0, 5, 0.002, 2, O.NODES_LOBATTO),
+    (63, 0.2, 3, 0.03, 2, O.NODES_RADAU_RIGHT),
+    (31, 0.5, 4, 0.02, 3, O.NODES_LEGENDRE),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_compact_steps_match_oracle(case):
+    n, nu, M, dt, L, kind = case
+    p = O.Problem(2, n, nu, M, dt, stencil=C, smoother=J, max_sweeps=100, nodes=kind)
+    u0 = initial_condition(2, n, seed=510 + n + M)
+    ref = O.integrate(p, u0, 3, 0, L)
+    assert all(st == 0 for st in ref.status)
+    g = make_gpu(p)
+    g.record_history(True)
+    u = to_dev(u0)
+    for s in range(3):
+        g.step(u, ref.sweeps[s], L)
+        assert rel_l2(u.cpu().numpy(), ref.per_step_u[s]) <= 1e-12
+        np.testing.assert_allclose(g.history(), ref.residuals[s], rtol=2e-4, atol=1e-13)
+
+
+def test_compact_until_tolerance_and_classical_mode():
+    p = O.Problem(2, 63, 1.0, 3, 0.001, reaction=O.REACTION_NONE, stencil=C, smoother=J, tol=1e-10, max_sweeps=100)
+    u0 = initial_condition(2, 63, seed=520)
+    ref = O.isdc_step(p, u0, 0, 2)
+    g = make_gpu(p)
+    u = to_dev(u0)
+    assert g.step(u, 0, 2) == 0
+    sweeps, _ = g.stats()
+    assert abs(sweeps - ref.sweeps) <= 1 and g.residual() < 1e-10
+    assert rel_l2(u.cpu().numpy(), ref.u) <= 1e-9
+    pc = O.Problem(2, 63, 1.0, 3, 0.001, reaction=O.REACTION_NONE, stencil=C, smoother=J, solver=O.SOLVER_MG_TOL,
+                   mg_tol=1e-9, tol=1e-9)
+    refc = O.isdc_step(pc, u0, 0, 0)
+    gc = make_gpu(pc)
+    v = to_dev(u0)
+    gc.step(v, refc.sweeps, 0)
+    _, vc = gc.stats()
+    assert abs(vc - refc.vcycles) <= 2
+    assert rel_l2(v.cpu().numpy(), refc.u) <= 1e-9
+
+
+def test_compact_graph_replay_and_resume_are_bitwise():
+    p = O.Problem(2, 127, 0.1, 3, 0.05, stencil=C, smoother=J)
+    u0 = initial_condition(2, 127, seed=530)
+    outs = []
+    for graphs in (True, False):
+        g = make_gpu(p, use_graphs=graphs)
+        u = to_dev(u0)
+        g.step(u, 0, 2)
+        outs.append((u.cpu().numpy(), g.stats()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    g = make_gpu(p)
+    u = to_dev(u0)
+    g.step(u, 5, 2)
+    g2 = make_gpu(p)
+    v = to_dev(u0)
+    g2.step(v, 3, 2)
+    g3 = make_gpu(p)
+    g3.set_nodes(g2.nodes().clone())
+    w = to_dev(u0)
+    g3.step(w, 2, 2)
+    np.testing.assert_array_equal(w.cpu().numpy(), u.cpu().numpy())
+
+
+def test_compact_unsupported_combinations():
+    import paper_1401_7824_gb300 as G
+    for kw in (dict(ndim=3, n=15), dict(ndim=2, n=15, smoother=G.ISDC_SMOOTHER_RBGS),
+               dict(ndim=2, n=15, vcycle_fp32=True)):
+        with pytest.raises(G.IsdcError) as e:
+            G.Isdc(kw.pop("ndim"), kw.pop("n"), 0.1, 3, 0.05, stencil=G.ISDC_STENCIL_COMPACT, **kw)
+        assert e.value.status == G.ISDC_ERR_UNSUPPORTED

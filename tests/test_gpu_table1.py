@@ -31,3 +31,29 @@ def test_sdc_and_isdc_counts_match_oracle(nu, M):
     assert gs[0] == sdc.sweeps and abs(gs[1] - sdc.vcycles) <= 1
     assert gis[0] == isdc.sweeps and abs(gis[1] - isdc.vcycles) <= 1
     assert isdc.sweeps >= sdc.sweeps  # K <= K~
+
+
+@pytest.mark.parametrize("nu", [1, 10, 100])
+@pytest.mark.parametrize("M", [3, 5, 7])
+def test_compact_stencil_counts_match_oracle(nu, M):
+    """The same accounting with the paper's own discretisation, the 4th-order
+    compact stencil with W (Sec. 3, Eq. 5).  The library's residual inverts W by
+    16 Jacobi steps (~1e-4 relative), which cannot move a sweep count here unless
+    a residual lands within that of the tolerance."""
+    from oracle.table1 import heat_problem
+    u0 = sine_mode(2, 63)
+    ps = heat_problem(nu, M, O.SOLVER_MG_TOL, stencil=O.STENCIL_COMPACT)
+    pi = heat_problem(nu, M, O.SOLVER_ISDC_CAPPED, stencil=O.STENCIL_COMPACT)
+    sdc = O.isdc_step(ps, u0, 0, 0)
+    isdc = O.isdc_step(pi, u0, 0, 2)
+    g = make_gpu(ps)
+    u = to_dev(u0)
+    g.step(u, 0, 0)
+    gs = g.stats()
+    gi = make_gpu(pi, vcycle_cap=True)
+    v = to_dev(u0)
+    gi.step(v, 0, 2)
+    gis = gi.stats()
+    assert gs[0] == sdc.sweeps and abs(gs[1] - sdc.vcycles) <= 1
+    assert gis[0] == isdc.sweeps and abs(gis[1] - isdc.vcycles) <= 1
+    assert isdc.sweeps >= sdc.sweeps  # K <= K~
