@@ -31,7 +31,12 @@
  *     (sine-transform diagonalisation: classical SDC with an exact spatial
  *     solve, Sec. 3), by multigrid until a tolerance (classical SDC, Sec. 3),
  *     or by L fixed V-cycles started from u_{m+1}^k (ISDC, Sec. 3 and Sec. 4.3);
- *   - the max-norm SDC residual after every sweep               -- Sec. 3.
+ *   - the max-norm SDC residual after every sweep               -- Sec. 3;
+ *   - or the viscous Burgers equation of Sec. 4.1 on a periodic grid: the
+ *     Laplacian implicit (periodic 5/7-point), the advection sum_axes (u^2/2)_x
+ *     explicit with the 5th-order WENO finite-difference scheme of Jiang and
+ *     Shu (local Lax-Friedrichs flux splitting), periodic multigrid and an
+ *     exact solve by the discrete Fourier transform.
  *
  * The multigrid solver is not described in the paper (Acknowledgments); the
  * one here is textbook geometric multigrid: vertex-centred coarsening
@@ -79,6 +84,11 @@ typedef struct {
     int    stencil;     /* 0: 5-point (2D) / 7-point (3D) Laplacian, W = I;
                            1: 4th-order compact 9-point Laplacian with the
                            weighting matrix W (Sec. 3, Eq. 5), 2D only */
+    int    equation;    /* 0: u_t = nu Lap u + f^E(u) on the unit square/cube with
+                           zero Dirichlet values (n = 2^j - 1 interior points);
+                           1: viscous Burgers u_t + sum_axes u u_x = nu Lap u on
+                           the periodic [-1,1)^d (n = 2^j points, h = 2/n),
+                           advection explicit by 5th-order WENO (Sec. 4.1) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -500,9 +510,11 @@ void orc_smooth_jacobi9(int n, double a, double omega, double *x, const double *
         }
 }
 
+void orc_residual_per(int d, int n, double a, const double *x, const double *b, double *r);
+
 /*
  * Exact solve on a small grid: the dense matrix of the operator (I - a L_h for
- * stencil 0, W - a L_9 for stencil 1) assembled column by column by applying
+ * stencil 0, W - a L_9 for stencil 1, periodic I - a L_h for 2) assembled column by column by applying
  * it to unit vectors, then Gaussian elimination with partial pivoting.  Used
  * on the coarsest multigrid level.
  */
@@ -517,7 +529,8 @@ static void dense_solve(int stencil, int d, int n, double a, const double *b, do
     for (long c = 0; c < N; ++c) {
         e[c] = 1.0;
         /* column c of the operator = -(residual of x = e with b = 0) */
-        if (stencil) orc_residual9(n, a, e, zero, col);
+        if (stencil == 1) orc_residual9(n, a, e, zero, col);
+        else if (stencil == 2) orc_residual_per(d, n, a, e, zero, col);
         else orc_residual(d, n, a, e, zero, col);
         for (long r = 0; r < N; ++r) A[r * N + c] = -col[r];
         e[c] = 0.0;
@@ -550,6 +563,239 @@ static void dense_solve(int stencil, int d, int n, double a, const double *b, do
 void orc_dense_solve(int d, int n, double a, const double *b, double *x) { dense_solve(0, d, n, a, b, x); }
 void orc_dense_solve9(int n, double a, const double *b, double *x) { dense_solve(1, 2, n, a, b, x); }
 
+/* ------------------------------------------------------------------------ */
+/* Periodic grids (viscous Burgers, Sec. 4.1): n points per side with        */
+/* 0-based indices i = 0..n-1 at x_i = -1 + i h, h = 2/n, wrapping around.   */
+/* ------------------------------------------------------------------------ */
+static long pidx(int d, int n, int i, int j, int k)
+{
+    i = ((i % n) + n) % n;
+    j = ((j % n) + n) % n;
+    if (d == 2) return i + (long)n * j;
+    k = ((k % n) + n) % n;
+    return i + (long)n * (j + (long)n * k);
+}
+
+static double pnsum(const double *u, int d, int n, int i, int j, int k)
+{
+    double s = u[pidx(d, n, i - 1, j, k)] + u[pidx(d, n, i + 1, j, k)]
+             + u[pidx(d, n, i, j - 1, k)] + u[pidx(d, n, i, j + 1, k)];
+    if (d == 3) s += u[pidx(d, n, i, j, k - 1)] + u[pidx(d, n, i, j, k + 1)];
+    return s;
+}
+
+/* periodic L_h u at (i,j,k), h = 2/n */
+static double plap_at(const double *u, int d, int n, int i, int j, int k)
+{
+    double h = 2.0 / n;
+    return (pnsum(u, d, n, i, j, k) - 2.0 * d * u[pidx(d, n, i, j, k)]) / (h * h);
+}
+
+static int pkmax(int d, int n) { return d == 3 ? n : 1; }
+
+void orc_laplacian_per(int d, int n, const double *u, double *out)
+{
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) out[pidx(d, n, i, j, k)] = plap_at(u, d, n, i, j, k);
+}
+
+/* r = b - (I - a L_h) x, periodic */
+void orc_residual_per(int d, int n, double a, const double *x, const double *b, double *r)
+{
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                long p = pidx(d, n, i, j, k);
+                r[p] = b[p] - (x[p] - a * plap_at(x, d, n, i, j, k));
+            }
+}
+
+void orc_smooth_jacobi_per(int d, int n, double a, double omega, double *x, const double *b, double *old)
+{
+    double h = 2.0 / n, diag = 1.0 + 2.0 * d * a / (h * h);
+    memcpy(old, x, sizeof(double) * npoints(d, n));
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                long p = pidx(d, n, i, j, k);
+                double r = b[p] - (old[p] - a * plap_at(old, d, n, i, j, k));
+                x[p] = old[p] + omega * r / diag;
+            }
+}
+
+/* red-black Gauss-Seidel, red = i+j(+k) even (0-based); n even keeps the
+ * colouring consistent across the wrap-around */
+void orc_smooth_rbgs_per(int d, int n, double a, double *x, const double *b)
+{
+    double h = 2.0 / n, diag = 1.0 + 2.0 * d * a / (h * h);
+    for (int colour = 0; colour < 2; ++colour)
+        for (int k = 0; k < pkmax(d, n); ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    int parity = (d == 3) ? (i + j + k) % 2 : (i + j) % 2;
+                    if (parity != colour) continue;
+                    long p = pidx(d, n, i, j, k);
+                    x[p] = (b[p] + a * pnsum(x, d, n, i, j, k) / (h * h)) / diag;
+                }
+}
+
+/* full weighting to the coarse periodic grid (n/2 points): coarse I sits on
+ * fine 2I, weights (1/4, 1/2, 1/4) per axis, wrapping around */
+void orc_restrict_per(int d, int n, const double *r, double *rc)
+{
+    int nc = n / 2;
+    for (int K = 0; K < pkmax(d, nc); ++K)
+        for (int J = 0; J < nc; ++J)
+            for (int I = 0; I < nc; ++I) {
+                double acc = 0.0;
+                for (int dk = (d == 3 ? -1 : 0); dk <= (d == 3 ? 1 : 0); ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            double w = (di ? 0.25 : 0.5) * (dj ? 0.25 : 0.5);
+                            if (d == 3) w *= dk ? 0.25 : 0.5;
+                            acc += w * r[pidx(d, n, 2 * I + di, 2 * J + dj, 2 * K + dk)];
+                        }
+                rc[pidx(d, nc, I, J, K)] = acc;
+            }
+}
+
+/* x += P e_c: linear interpolation from the coarse periodic grid */
+void orc_prolong_per(int d, int nc, const double *ec, double *x)
+{
+    int n = 2 * nc;
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                /* fine i lies on coarse i/2 (even) or between (i-1)/2 and (i+1)/2 (odd) */
+                for (int K = (d == 3 ? k / 2 : 0); K <= (d == 3 ? (k + 1) / 2 : 0); ++K)
+                    for (int J = j / 2; J <= (j + 1) / 2; ++J)
+                        for (int I = i / 2; I <= (i + 1) / 2; ++I) {
+                            double w = (i % 2 ? 0.5 : (I * 2 == i ? 1.0 : 0.0))
+                                     * (j % 2 ? 0.5 : (J * 2 == j ? 1.0 : 0.0));
+                            if (d == 3) w *= k % 2 ? 0.5 : (K * 2 == k ? 1.0 : 0.0);
+                            acc += w * ec[pidx(d, nc, I, J, K)];
+                        }
+                x[pidx(d, n, i, j, k)] += acc;
+            }
+}
+
+/*
+ * Exact solve of (I - a L_h) x = b on the periodic grid by the discrete
+ * Fourier transform: the modes exp(2 pi i (p i' + q j' [+ r k'])/n) are
+ * eigenvectors of L_h with eigenvalues -(4/h^2) sum_axes sin^2(pi p/n).  The
+ * transforms are dense complex sums along each axis.
+ */
+static void dft_along_axis(int d, int n, int axis, double *re, double *im, int sign)
+{
+    long N = npoints(d, n), st = 1;
+    for (int a = 0; a < axis; ++a) st *= n;
+    double *lr = (double *)malloc(sizeof(double) * n), *li = (double *)malloc(sizeof(double) * n);
+    for (long base = 0; base < N; ++base) {
+        if ((base / st) % n != 0) continue;
+        for (int p = 0; p < n; ++p) {
+            double ar = 0.0, ai = 0.0;
+            for (int q = 0; q < n; ++q) {
+                double ang = sign * 2.0 * M_PI * (double)p * (double)q / n;
+                double c = cos(ang), s = sin(ang);
+                double xr = re[base + q * st], xi = im[base + q * st];
+                ar += xr * c - xi * s;
+                ai += xr * s + xi * c;
+            }
+            lr[p] = ar;
+            li[p] = ai;
+        }
+        for (int p = 0; p < n; ++p) { re[base + p * st] = lr[p]; im[base + p * st] = li[p]; }
+    }
+    free(lr); free(li);
+}
+
+void orc_solve_exact_per(int d, int n, double a, const double *b, double *x)
+{
+    long N = npoints(d, n);
+    double h = 2.0 / n;
+    double *re = (double *)malloc(sizeof(double) * N), *im = (double *)calloc(N, sizeof(double));
+    memcpy(re, b, sizeof(double) * N);
+    for (int ax = 0; ax < d; ++ax) dft_along_axis(d, n, ax, re, im, -1);
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double si = sin(M_PI * i / n), sj = sin(M_PI * j / n), sk = d == 3 ? sin(M_PI * k / n) : 0.0;
+                double lam = -4.0 * (si * si + sj * sj + sk * sk) / (h * h);
+                long p = pidx(d, n, i, j, k);
+                double f = 1.0 / ((1.0 - a * lam) * (double)N);
+                re[p] *= f;
+                im[p] *= f;
+            }
+    for (int ax = 0; ax < d; ++ax) dft_along_axis(d, n, ax, re, im, +1);
+    memcpy(x, re, sizeof(double) * N);
+    free(re); free(im);
+}
+
+/*
+ * 5th-order WENO reconstruction (Jiang and Shu, 1996) of the numerical flux at
+ * the face between v[2] and v[3] from the upwind-biased values v[0..4]
+ * (v[0] = f_{i-2} ... v[4] = f_{i+2}): three 3-point candidate fluxes, their
+ * smoothness indicators, nonlinear weights from the linear weights
+ * (1/10, 6/10, 3/10) with epsilon = 1e-6.
+ */
+double orc_weno5_face(const double *v)
+{
+    double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+    double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+    double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+    double b0 = 13.0 / 12.0 * (v[0] - 2.0 * v[1] + v[2]) * (v[0] - 2.0 * v[1] + v[2])
+              + 0.25 * (v[0] - 4.0 * v[1] + 3.0 * v[2]) * (v[0] - 4.0 * v[1] + 3.0 * v[2]);
+    double b1 = 13.0 / 12.0 * (v[1] - 2.0 * v[2] + v[3]) * (v[1] - 2.0 * v[2] + v[3])
+              + 0.25 * (v[1] - v[3]) * (v[1] - v[3]);
+    double b2 = 13.0 / 12.0 * (v[2] - 2.0 * v[3] + v[4]) * (v[2] - 2.0 * v[3] + v[4])
+              + 0.25 * (3.0 * v[2] - 4.0 * v[3] + v[4]) * (3.0 * v[2] - 4.0 * v[3] + v[4]);
+    const double eps = 1e-6;
+    double a0 = 0.1 / ((eps + b0) * (eps + b0));
+    double a1 = 0.6 / ((eps + b1) * (eps + b1));
+    double a2 = 0.3 / ((eps + b2) * (eps + b2));
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/*
+ * Advection term of the viscous Burgers equation, f^E(u) = -sum_axes d/dx (u^2/2),
+ * by conservative finite differences: F_{i+1/2} = F^+ + F^- with the local
+ * Lax-Friedrichs splitting f^(+/-) = (u^2/2 +/- alpha u)/2, alpha = max |u| over the
+ * six points i-2..i+3 of the face's stencil; F^+ from f^+_{i-2..i+2}, F^- from
+ * f^-_{i+3..i-1} (mirrored); f^E_i -= (F_{i+1/2} - F_{i-1/2}) / h per axis.
+ */
+static double weno_face_flux(const double *u, int d, int n, int i, int j, int k, int axis)
+{
+    double w[6], fp[5], fm[5], alpha = 0.0;
+    for (int t = 0; t < 6; ++t) {
+        int o = t - 2;
+        w[t] = u[pidx(d, n, i + (axis == 0) * o, j + (axis == 1) * o, k + (axis == 2) * o)];
+        if (fabs(w[t]) > alpha) alpha = fabs(w[t]);
+    }
+    for (int t = 0; t < 5; ++t) {
+        fp[t] = 0.5 * (0.5 * w[t] * w[t] + alpha * w[t]);          /* points i-2..i+2 */
+        fm[t] = 0.5 * (0.5 * w[5 - t] * w[5 - t] - alpha * w[5 - t]); /* points i+3..i-1 */
+    }
+    return orc_weno5_face(fp) + orc_weno5_face(fm);
+}
+
+void orc_burgers_advection(int d, int n, const double *u, double *fe)
+{
+    double h = 2.0 / n;
+    for (int k = 0; k < pkmax(d, n); ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int ax = 0; ax < d; ++ax) {
+                    double Fr = weno_face_flux(u, d, n, i, j, k, ax);
+                    double Fl = weno_face_flux(u, d, n, i - (ax == 0), j - (ax == 1), k - (ax == 2), ax);
+                    acc -= (Fr - Fl) / h;
+                }
+                fe[pidx(d, n, i, j, k)] = acc;
+            }
+}
+
 /* Multigrid hierarchy: level 0 is the fine grid, sides n_l = (n_{l-1}-1)/2 down to 3. */
 typedef struct {
     int d, levels;
@@ -557,7 +803,8 @@ typedef struct {
     double *x[32], *b[32], *r[32], *tmp[32];
 } orc_mg;
 
-static void mg_alloc(orc_mg *mg, int d, int n)
+/* Dirichlet: sides n, (n-1)/2, ... down to 3; periodic: n, n/2, ... down to 4. */
+static void mg_alloc(orc_mg *mg, int d, int n, int periodic)
 {
     memset(mg, 0, sizeof(*mg));
     mg->d = d;
@@ -570,8 +817,8 @@ static void mg_alloc(orc_mg *mg, int d, int n)
         mg->r[l] = (double *)calloc(N, sizeof(double));
         mg->tmp[l] = (double *)calloc(N, sizeof(double));
         ++l;
-        if (s <= 3) break;
-        s = (s - 1) / 2;
+        if (periodic ? s <= 4 : s <= 3) break;
+        s = periodic ? s / 2 : (s - 1) / 2;
     }
     mg->levels = l;
 }
@@ -585,7 +832,10 @@ static void mg_free(orc_mg *mg)
 
 static void smooth(const orc_problem *P, int n, double a, double *x, const double *b, double *tmp)
 {
-    if (P->stencil == 1) orc_smooth_jacobi9(n, a, P->omega, x, b, tmp);
+    if (P->equation == 1) {
+        if (P->smoother == 0) orc_smooth_jacobi_per(P->ndim, n, a, P->omega, x, b, tmp);
+        else orc_smooth_rbgs_per(P->ndim, n, a, x, b);
+    } else if (P->stencil == 1) orc_smooth_jacobi9(n, a, P->omega, x, b, tmp);
     else if (P->smoother == 0) orc_smooth_jacobi(P->ndim, n, a, P->omega, x, b, tmp);
     else orc_smooth_rbgs(P->ndim, n, a, x, b);
 }
@@ -593,7 +843,8 @@ static void smooth(const orc_problem *P, int n, double a, double *x, const doubl
 /* r = b - H x for the problem's operator (I - a L_h, or W - a L_9) */
 static void node_residual(const orc_problem *P, int n, double a, const double *x, const double *b, double *r)
 {
-    if (P->stencil == 1) orc_residual9(n, a, x, b, r);
+    if (P->equation == 1) orc_residual_per(P->ndim, n, a, x, b, r);
+    else if (P->stencil == 1) orc_residual9(n, a, x, b, r);
     else orc_residual(P->ndim, n, a, x, b, r);
 }
 
@@ -603,15 +854,17 @@ static void vcycle(const orc_problem *P, orc_mg *mg, int l, double a, double *x,
 {
     int d = P->ndim, n = mg->side[l];
     if (l == mg->levels - 1) { /* coarsest grid: exact solve */
-        dense_solve(P->stencil, d, n, a, b, x);
+        dense_solve(P->equation == 1 ? 2 : P->stencil, d, n, a, b, x);
         return;
     }
     for (int s = 0; s < P->nu1; ++s) smooth(P, n, a, x, b, mg->tmp[l]);
     node_residual(P, n, a, x, b, mg->r[l]);
-    orc_restrict_fw(d, n, mg->r[l], mg->b[l + 1]);
+    if (P->equation == 1) orc_restrict_per(d, n, mg->r[l], mg->b[l + 1]);
+    else orc_restrict_fw(d, n, mg->r[l], mg->b[l + 1]);
     memset(mg->x[l + 1], 0, sizeof(double) * npoints(d, mg->side[l + 1]));
     vcycle(P, mg, l + 1, a, mg->x[l + 1], mg->b[l + 1]);
-    orc_prolong_add(d, mg->side[l + 1], mg->x[l + 1], x);
+    if (P->equation == 1) orc_prolong_per(d, mg->side[l + 1], mg->x[l + 1], x);
+    else orc_prolong_add(d, mg->side[l + 1], mg->x[l + 1], x);
     for (int s = 0; s < P->nu2; ++s) smooth(P, n, a, x, b, mg->tmp[l]);
 }
 
@@ -619,7 +872,7 @@ static void vcycle(const orc_problem *P, orc_mg *mg, int l, double a, double *x,
 int orc_vcycle(const orc_problem *P, double a, double *x, const double *b)
 {
     orc_mg mg;
-    mg_alloc(&mg, P->ndim, P->n);
+    mg_alloc(&mg, P->ndim, P->n, P->equation == 1);
     vcycle(P, &mg, 0, a, x, b);
     mg_free(&mg);
     return 0;
@@ -723,6 +976,12 @@ static double f_explicit(const orc_problem *P, double u)
 static void eval_f(const orc_problem *P, const double *u, double *fE, double *fI)
 {
     long N = npoints(P->ndim, P->n);
+    if (P->equation == 1) {  /* Burgers: f^I = nu L_h u (periodic), f^E = WENO5 advection */
+        orc_laplacian_per(P->ndim, P->n, u, fI);
+        orc_burgers_advection(P->ndim, P->n, u, fE);
+        for (long p = 0; p < N; ++p) fI[p] *= P->nu;
+        return;
+    }
     if (P->stencil == 1) orc_laplacian9(P->n, u, fI);
     else orc_laplacian(P->ndim, P->n, u, fI);
     for (long p = 0; p < N; ++p) {
@@ -763,6 +1022,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     if ((d != 2 && d != 3) || n < 1 || M < 2 || M > ORC_MAX_M) return 3;
     if (P->nodes < 0 || P->nodes > 2) return 3;
     if (P->stencil == 1 && (d != 2 || P->smoother != 0)) return 3; /* compact: 2D, Jacobi */
+    if (P->equation == 1 && (P->stencil != 0 || n < 8 || (n & (n - 1)) != 0)) return 3; /* periodic n = 2^j */
     const long N = npoints(d, n);
     const int W9 = P->stencil == 1;
     /* points: t_0 and the nodes; node j (0-based) is point j + off */
@@ -799,7 +1059,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     double *v = (double *)malloc(sizeof(double) * N);
     double *wv = (double *)malloc(sizeof(double) * N);
     orc_mg mg;
-    mg_alloc(&mg, d, n);
+    mg_alloc(&mg, d, n, P->equation == 1);
 
     /* Initial iterate: u_0 spread to every node (the paper does not state it). */
     memcpy(u0, u, sizeof(double) * N);
@@ -822,7 +1082,9 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
             double dtm = P->dt * (tpt[m + 1] - tpt[m]);
             double a = dtm * P->nu; /* (I - dt_m A) with A = nu L_h */
             const double *Um_new = U + m * N;
-            for (long p = 0; p < N; ++p) fe_new[p] = f_explicit(P, Um_new[p]);
+            if (P->equation == 1) orc_burgers_advection(d, n, Um_new, fe_new);
+            else
+                for (long p = 0; p < N; ++p) fe_new[p] = f_explicit(P, Um_new[p]);
             /* Eq. 4 with the implicit unknown moved left:
              * (I - dt_m A) u_{m+1}^{k+1} = u_m^{k+1}
              *     + dt_m [f^E(u_m^{k+1}) - f^E(u_m^k)] - dt_m f^I(u_{m+1}^k)
@@ -858,6 +1120,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
 
             if (P->solver == 2) {
                 if (W9) orc_solve_exact9(n, a, rhs, x);
+                else if (P->equation == 1) orc_solve_exact_per(d, n, a, rhs, x);
                 else orc_solve_exact(d, n, a, rhs, x);
             } else if (P->solver == 1) {
                 for (int c = 0; c < P->mg_max_cycles; ++c) {

@@ -40,6 +40,8 @@ NODES_RADAU_RIGHT = 1     # Gauss-Radau, tau_M = 1 (M solves per sweep)
 NODES_LEGENDRE = 2        # Gauss-Legendre, interior nodes (M solves, end-point quadrature)
 STENCIL_SECOND_ORDER = 0  # 5-point (2D) / 7-point (3D) Laplacian, W = I
 STENCIL_COMPACT = 1       # 4th-order compact 9-point Laplacian with weighting matrix W (2D, Sec. 3 Eq. 5)
+EQUATION_REACTION_DIFFUSION = 0  # unit square / cube, zero Dirichlet values, n = 2^j - 1 interior points
+EQUATION_BURGERS = 1             # viscous Burgers, periodic [-1,1)^d, n = 2^j points, WENO5 advection (Sec. 4.1)
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +62,8 @@ class _Problem(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("solver", ctypes.c_int), ("guess", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
-                ("mg_max_cycles", ctypes.c_int), ("nodes", ctypes.c_int), ("stencil", ctypes.c_int)]
+                ("mg_max_cycles", ctypes.c_int), ("nodes", ctypes.c_int), ("stencil", ctypes.c_int),
+                ("equation", ctypes.c_int)]
 
 
 @dataclass
@@ -85,11 +88,13 @@ class Problem:
     mg_max_cycles: int = 100
     nodes: int = NODES_LOBATTO
     stencil: int = STENCIL_SECOND_ORDER
+    equation: int = EQUATION_REACTION_DIFFUSION
 
     def _c(self) -> _Problem:
         return _Problem(self.ndim, self.n, self.nu, self.M, self.dt, self.reaction, self.lambda_e,
                         self.smoother, self.nu1, self.nu2, self.omega, self.solver, self.guess,
-                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles, self.nodes, self.stencil)
+                        self.tol, self.max_sweeps, self.mg_tol, self.mg_max_cycles, self.nodes, self.stencil,
+                        self.equation)
 
     @property
     def shape(self):
@@ -125,6 +130,16 @@ def _L():
         lib.orc_smooth_jacobi9.argtypes = [I, D, D, dp, dp, dp]
         lib.orc_dense_solve9.argtypes = [I, D, dp, dp]
         lib.orc_solve_exact9.argtypes = [I, D, dp, dp]
+        lib.orc_laplacian_per.argtypes = [I, I, dp, dp]
+        lib.orc_residual_per.argtypes = [I, I, D, dp, dp, dp]
+        lib.orc_smooth_jacobi_per.argtypes = [I, I, D, D, dp, dp, dp]
+        lib.orc_smooth_rbgs_per.argtypes = [I, I, D, dp, dp]
+        lib.orc_restrict_per.argtypes = [I, I, dp, dp]
+        lib.orc_prolong_per.argtypes = [I, I, dp, dp]
+        lib.orc_solve_exact_per.argtypes = [I, I, D, dp, dp]
+        lib.orc_weno5_face.argtypes = [dp]
+        lib.orc_weno5_face.restype = D
+        lib.orc_burgers_advection.argtypes = [I, I, dp, dp]
         lib.orc_vcycle.argtypes = [ctypes.POINTER(_Problem), D, dp, dp]
         lib.orc_isdc_step.argtypes = [ctypes.POINTER(_Problem), dp, I, I, ctypes.POINTER(I),
                                       ctypes.POINTER(ctypes.c_long), dp, dp, dp]
@@ -399,4 +414,77 @@ def integrate(problem: Problem, u0, steps: int, n_sweeps=0, n_vcycles: int = 2,
         out.residuals.append(r.residuals)
         out.status.append(r.status)
     out.u = u
+    return out
+
+
+# --- periodic grids and WENO5 advection (viscous Burgers, Sec. 4.1) ------------
+def laplacian_per(u):
+    u = _f64(u)
+    d, n = _dims(u)
+    out = np.empty_like(u)
+    _L().orc_laplacian_per(d, n, _p(u), _p(out))
+    return out
+
+
+def residual_per(a, x, b):
+    x, b = _f64(x), _f64(b)
+    d, n = _dims(x)
+    r = np.empty_like(x)
+    _L().orc_residual_per(d, n, a, _p(x), _p(b), _p(r))
+    return r
+
+
+def smooth_jacobi_per(a, omega, x, b):
+    x, b = _f64(x).copy(), _f64(b)
+    d, n = _dims(x)
+    tmp = np.empty_like(x)
+    _L().orc_smooth_jacobi_per(d, n, a, omega, _p(x), _p(b), _p(tmp))
+    return x
+
+
+def smooth_rbgs_per(a, x, b):
+    x, b = _f64(x).copy(), _f64(b)
+    d, n = _dims(x)
+    _L().orc_smooth_rbgs_per(d, n, a, _p(x), _p(b))
+    return x
+
+
+def restrict_per(r):
+    r = _f64(r)
+    d, n = _dims(r)
+    rc = np.zeros((n // 2,) * d)
+    _L().orc_restrict_per(d, n, _p(r), _p(rc))
+    return rc
+
+
+def prolong_per(ec, x):
+    ec, x = _f64(ec), _f64(x).copy()
+    d, nc = _dims(ec)
+    assert x.shape[0] == 2 * nc
+    _L().orc_prolong_per(d, nc, _p(ec), _p(x))
+    return x
+
+
+def solve_exact_per(a, b):
+    """(I - a L_h)^{-1} b on the periodic grid by the discrete Fourier transform."""
+    b = _f64(b)
+    d, n = _dims(b)
+    x = np.zeros_like(b)
+    _L().orc_solve_exact_per(d, n, a, _p(b), _p(x))
+    return x
+
+
+def weno5_face(v):
+    """WENO5 face value from the five upwind-biased values v[0..4]."""
+    v = _f64(v)
+    assert v.shape == (5,)
+    return float(_L().orc_weno5_face(_p(v)))
+
+
+def burgers_advection(u):
+    """f^E(u) = -sum_axes (u^2/2)_x by WENO5 with local Lax-Friedrichs splitting (periodic)."""
+    u = _f64(u)
+    d, n = _dims(u)
+    out = np.empty_like(u)
+    _L().orc_burgers_advection(d, n, _p(u), _p(out))
     return out

@@ -40,3 +40,18 @@ def weighting(n):
     """W = I + (h^2/12) L_5 (2D)."""
     h = 1.0 / (n + 1)
     return np.eye(n * n) + h ** 2 / 12.0 * laplacian(2, n)
+
+
+def lap1d_periodic(n, h):
+    """Circulant 1D second difference on n periodic points."""
+    L = np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    L[0, -1] = L[-1, 0] = 1.0
+    return L / h ** 2
+
+
+def laplacian_periodic(d, n):
+    """Periodic L_h on [-1,1)^d with h = 2/n (Kronecker form, x fastest)."""
+    L1, I = lap1d_periodic(n, 2.0 / n), np.eye(n)
+    if d == 2:
+        return np.kron(I, L1) + np.kron(L1, I)
+    return np.kron(I, np.kron(I, L1)) + np.kron(I, np.kron(L1, I)) + np.kron(L1, np.kron(I, I))
