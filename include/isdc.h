@@ -97,6 +97,13 @@ typedef struct {
                              1: the 4th-order compact 9-point Laplacian with the weighting
                              matrix W of Sec. 3 (Eq. 5), 2D, damped-Jacobi smoothing, FP64
                              V-cycles (other combinations: ISDC_ERR_UNSUPPORTED). */
+    int    equation;      /* 0 (default): u_t = nu Lap u + f^E(u) on the unit square / cube, zero
+                             Dirichlet values, sides 2^j - 1 (interior points), h = 1/(n+1).
+                             1: viscous Burgers u_t + sum_axes u u_x = nu Lap u (Sec. 4.1) on the
+                             periodic [-1,1)^ndim, sides 2^j with j >= 3, h = 2/n; the advection is
+                             explicit (5th-order WENO, local Lax-Friedrichs splitting), the
+                             Laplacian implicit (periodic multigrid); FP64 V-cycles; `reaction`
+                             is ignored. */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream
@@ -125,7 +132,8 @@ isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double *tau, do
  * (u and f(u) at t_0 and every node) and the multigrid hierarchy (sides
  * n, (n-1)/2, ... down to 3).
  *   ndim   2 or 3
- *   dims   ndim interior sides; all equal, each 2^j - 1 with j >= 2
+ *   dims   ndim sides, all equal: 2^j - 1 interior points with j >= 2 (equation 0) or
+ *          2^j periodic points with j >= 3 (equation 1)
  *   nu     diffusion coefficient (> 0)
  *   nodes  isdc_node_type (Gauss-Lobatto, Gauss-Radau right or Gauss-Legendre)
  *   M      number of nodes, 2..7

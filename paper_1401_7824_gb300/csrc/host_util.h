@@ -204,5 +204,44 @@ inline void coarse_inverse9(double a, std::vector<double>& inv) {
   }
 }
 
+// Inverse of the dense matrix of I - a L_h on the periodic side-4 grid
+// (h = 1/2; 16 or 64 unknowns, x fastest), row-major.
+inline void coarse_inverse_per(int dim, double a, std::vector<double>& inv) {
+  const int n = 4, Np = dim == 2 ? 16 : 64;
+  const double h = 0.5, c = a / (h * h), d = 1.0 + 2.0 * dim * c;
+  std::vector<double> A(size_t(Np) * Np, 0.0);
+  for (int p = 0; p < Np; ++p) {
+    const int i = p % n, j = (p / n) % n, k = dim == 3 ? p / (n * n) : 0;
+    A[size_t(p) * Np + p] = d;
+    const int nb[6][3] = {{(i + 3) % n, j, k}, {(i + 1) % n, j, k}, {i, (j + 3) % n, k},
+                          {i, (j + 1) % n, k}, {i, j, (k + 3) % n}, {i, j, (k + 1) % n}};
+    for (int q = 0; q < 2 * dim; ++q)
+      A[size_t(p) * Np + (nb[q][0] + n * (nb[q][1] + n * nb[q][2]))] -= c;
+  }
+  inv.assign(size_t(Np) * Np, 0.0);
+  for (int p = 0; p < Np; ++p) inv[size_t(p) * Np + p] = 1.0;
+  for (int col = 0; col < Np; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Np; ++r)
+      if (std::fabs(A[size_t(r) * Np + col]) > std::fabs(A[size_t(piv) * Np + col])) piv = r;
+    if (piv != col)
+      for (int q = 0; q < Np; ++q) {
+        std::swap(A[size_t(col) * Np + q], A[size_t(piv) * Np + q]);
+        std::swap(inv[size_t(col) * Np + q], inv[size_t(piv) * Np + q]);
+      }
+    const double sc = 1.0 / A[size_t(col) * Np + col];
+    for (int q = 0; q < Np; ++q) { A[size_t(col) * Np + q] *= sc; inv[size_t(col) * Np + q] *= sc; }
+    for (int r = 0; r < Np; ++r) {
+      if (r == col) continue;
+      const double f = A[size_t(r) * Np + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < Np; ++q) {
+        A[size_t(r) * Np + q] -= f * A[size_t(col) * Np + q];
+        inv[size_t(r) * Np + q] -= f * inv[size_t(col) * Np + q];
+      }
+    }
+  }
+}
+
 }  // namespace host
 }  // namespace isdc

@@ -24,6 +24,7 @@
 #include "kernels.cuh"
 #include "sdc_kernels.cuh"
 #include "compact_kernels.cuh"
+#include "periodic_kernels.cuh"
 
 #define ISDC_API extern "C" __attribute__((visibility("default")))
 
@@ -99,6 +100,8 @@ struct isdc_ctx {
   int stencil = 0;      // 0: 5/7-point, W = I; 1: 4th-order compact with W (2D)
   double* G = nullptr;  // compact: nu L_9 u per point (P arrays); F holds f~ = W f^E + nu L_9 u
   double* Rs = nullptr; // compact: W-weighted SDC residuals and two Jacobi iterates, 3 (P-1) arrays
+  int equation = 0;     // 0: reaction-diffusion, Dirichlet; 1: viscous Burgers, periodic (h = 2/n)
+  double* FE = nullptr; // Burgers: f^E(u_p) = WENO5 advection per point (P arrays)
   double* b = nullptr;  // right-hand side of the current node solve
   double* u_dev = nullptr;  // device copy of u for isdc_step_host
   Hier<double> h64;
@@ -259,19 +262,27 @@ inline size_t pow_dim(int dim, size_t s) { return dim == 2 ? s * s : s * s * s; 
 // hierarchies hand only the smallest grids to it; FP32 ones go deeper.
 int bottom_threshold(int dim, bool fp64) { return dim == 2 ? (fp64 ? 31 : 63) : (fp64 ? 7 : 15); }
 
+// Entries of one dense coarsest-level inverse: side 3 (9 / 27 unknowns) on the
+// Dirichlet grids, side 4 (16 / 64 unknowns) on the periodic ones.
+inline size_t ainv_slot(const isdc_ctx* ctx) {
+  if (ctx->equation == 1) return ctx->dim == 2 ? 256 : 4096;
+  return ctx->dim == 2 ? 81 : 729;
+}
+
 template <typename T>
 isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   int s = ctx->n, l = 0;
+  const bool periodic = ctx->equation == 1;
   for (;;) {
     H.side[l] = s;
     H.npts[l] = pow_dim(ctx->dim, s);
     ++l;
-    if (s <= 3) break;
-    s = (s - 1) / 2;
+    if (periodic ? s <= 4 : s <= 3) break;
+    s = periodic ? s / 2 : (s - 1) / 2;
   }
   H.nlev = l;
   H.lb = 0;
-  if (ctx->stencil == 1) H.lb = H.nlev - 1;  // compact: grid-wide levels, dense side-3 solve
+  if (ctx->stencil == 1 || periodic) H.lb = H.nlev - 1;  // grid-wide levels, dense coarsest solve
   else
     while (H.side[H.lb] > bottom_threshold(ctx->dim, sizeof(T) == 8)) ++H.lb;
   for (int q = 0; q < H.nlev; ++q) {
@@ -291,7 +302,7 @@ isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   size_t sm = 0;
   for (int q = H.lb; q < H.nlev; ++q) sm += 3 * H.npts[q] * sizeof(T);
   H.bottom_smem = sm;
-  const size_t ainv = size_t(ctx->P) * (ctx->dim == 2 ? 81 : 729) * sizeof(T);
+  const size_t ainv = size_t(ctx->P) * ainv_slot(ctx) * sizeof(T);
   CUDA_TRY(ctx, cudaMalloc(&H.Ainv, ainv));
   return ISDC_OK;
 }
@@ -318,13 +329,16 @@ isdc_status upload_ainv(isdc_ctx* ctx, Hier<T>& H, int slot, double a) {
   if (ctx->stencil == 1) {  // c0 (W - a L_9)^{-1}, c0 = 2/3 + 10 a / (3 h^2), h = 1/4
     coarse_inverse9(a, inv);
     d3 = 2.0 / 3.0 + 10.0 * a * 16.0 / 3.0;
+  } else if (ctx->equation == 1) {  // periodic side 4, h = 1/2
+    coarse_inverse_per(ctx->dim, a, inv);
+    d3 = 1.0 + 2.0 * ctx->dim * a * 4.0;
   } else {
     coarse_inverse(ctx->dim, a, inv);
     d3 = 1.0 + 2.0 * ctx->dim * a * 16.0;  // h = 1/4 on the side-3 grid
   }
   std::vector<T> tv(inv.size());
   for (size_t q = 0; q < inv.size(); ++q) tv[q] = T(d3 * inv[q]);
-  const size_t each = ctx->dim == 2 ? 81 : 729;
+  const size_t each = ainv_slot(ctx);
   CUDA_TRY(ctx, cudaMemcpyAsync(H.Ainv + slot * each, tv.data(), each * sizeof(T), cudaMemcpyHostToDevice,
                                 ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // tv is a host temporary
@@ -876,6 +890,208 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   return ISDC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Viscous Burgers on the periodic grid (Sec. 4.1), FP64: multigrid on
+// (I - a L_h) x = b with periodic kernels, and the sweep with stored f^E.
+// ---------------------------------------------------------------------------
+inline LevelCoef coef_per(int dim, int s, double a) {
+  const double h = 2.0 / s, c = a / (h * h), d = 1.0 + 2.0 * dim * c;
+  return {c, d, c / d};
+}
+inline dim3 pp_grid(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
+inline dim3 prb_grid(int dim, int s) {
+  return dim3((s / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1);
+}
+
+template <int DIM>
+isdc_status smooth_level_per(isdc_ctx* ctx, Hier<double>& H, int l, double a, double*& x, double* home,
+                             const double* b, bool& zero, int sweeps) {
+  const int s = H.side[l];
+  const double kappa = coef_per(DIM, s, a).kappa;
+  const double Np = double(H.npts[l]);
+  for (int it = 0; it < sweeps; ++it) {
+    if (ctx->opt.smoother == ISDC_SMOOTHER_JACOBI) {
+      double* out = (x == H.t[l]) ? home : H.t[l];
+      {
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 2.0 : 3.0) * Np * 8,
+                     (zero ? 1.0 : nb_ops(DIM) + 3.0) * Np, true);
+        k_jacobi_per<double, DIM><<<pp_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, ctx->opt.omega, x, b, out,
+                                                                                zero ? 1 : 0);
+      }
+      LAUNCH_CHECK(ctx);
+      x = out;
+    } else {
+      for (int colour = 0; colour < 2; ++colour) {
+        {
+          const bool z = zero && colour == 0;
+          ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (z ? 1.0 : 1.5) * Np * 8,
+                       (z ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, true);
+          k_rbgs_per<double, DIM><<<prb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, colour, x, b, z ? 1 : 0);
+        }
+        LAUNCH_CHECK(ctx);
+      }
+    }
+    zero = false;
+  }
+  return ISDC_OK;
+}
+
+template <int DIM>
+isdc_status vcycle_per(isdc_ctx* ctx, int slot, double a, double* x0, const double* b0) {
+  Hier<double>& H = ctx->h64;
+  double* xcur[kMaxLevels];
+  isdc_status st;
+  for (int l = 0; l < H.lb; ++l) {
+    double* home = l == 0 ? x0 : H.x[l];
+    double* x = home;
+    const double* b = l == 0 ? b0 : H.b[l];
+    bool zero = l > 0;
+    const int s = H.side[l], sc = H.side[l + 1];
+    if (ctx->opt.nu1 == 0 && zero) {
+      CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(double), ctx->stream));
+      zero = false;
+    }
+    if ((st = smooth_level_per<DIM>(ctx, H, l, a, x, home, b, zero, ctx->opt.nu1)) != ISDC_OK) return st;
+    const LevelCoef lf = coef_per(DIM, s, a);
+    const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+    {
+      ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, 3.0 * Np * 8, (nb_ops(DIM) + 2.0) * Np, true);
+      k_residual_per<double, DIM><<<pp_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, lf.kappa, x, b, H.r[l]);
+    }
+    LAUNCH_CHECK(ctx);
+    {
+      const double ws = lf.d / (coef_per(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0));
+      ProfScope ps(ctx, l == 0 ? PC_RESTRICT0 : PC_RESTRICTC, (Np + Nc) * 8, (DIM == 2 ? 9.0 : 27.0) * Nc, true);
+      k_restrict_per<double, DIM><<<pp_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
+    }
+    LAUNCH_CHECK(ctx);
+    xcur[l] = x;
+  }
+  {  // side-4 level: dense solve
+    const double* bb = H.lb == 0 ? b0 : H.b[H.lb];
+    double* xb = H.lb == 0 ? x0 : H.x[H.lb];
+    const double* G = H.Ainv + size_t(slot) * ainv_slot(ctx);
+    ProfScope ps(ctx, PC_BOTTOM, 2.0 * double(H.npts[H.lb]) * 8, double(H.npts[H.lb] * H.npts[H.lb]), true);
+    if (DIM == 2) k_coarse_dense<double, 16><<<1, 32, 0, ctx->stream>>>(G, bb, xb);
+    else k_coarse_dense<double, 64><<<1, 64, 0, ctx->stream>>>(G, bb, xb);
+    LAUNCH_CHECK(ctx);
+    xcur[H.lb] = xb;
+  }
+  for (int l = H.lb - 1; l >= 0; --l) {
+    const int s = H.side[l], sc = H.side[l + 1];
+    double* home = l == 0 ? x0 : H.x[l];
+    double* x = xcur[l];
+    {
+      const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
+      ProfScope ps(ctx, l == 0 ? PC_PROLONG0 : PC_PROLONGC, (2.0 * Np + Nc) * 8, (DIM == 2 ? 6.0 : 10.0) * Np, true);
+      k_prolong_per<double, DIM><<<pp_grid(DIM, s), kBlock, 0, ctx->stream>>>(sc, xcur[l + 1], x);
+    }
+    LAUNCH_CHECK(ctx);
+    bool zero = false;
+    if ((st = smooth_level_per<DIM>(ctx, H, l, a, x, home, l == 0 ? b0 : H.b[l], zero, ctx->opt.nu2)) != ISDC_OK)
+      return st;
+    xcur[l] = x;
+  }
+  if (xcur[0] != x0)
+    CUDA_TRY(ctx, cudaMemcpyAsync(x0, xcur[0], H.npts[0] * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return ISDC_OK;
+}
+
+template <int DIM>
+isdc_status node_residual_norm_per(isdc_ctx* ctx, double a, const double* x, const double* b, double* out) {
+  const int s = ctx->n;
+  const LevelCoef lf = coef_per(DIM, s, a);
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal + 1, 0, sizeof(unsigned long long), ctx->stream));
+  {
+    ProfScope ps(ctx, PC_RESNORM, 16.0 * double(ctx->N), (nb_ops(DIM) + 3.0) * double(ctx->N), true);
+    k_resnorm_per<DIM><<<pp_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, lf.kappa, lf.d, x, b, ctx->d_scal + 1);
+  }
+  LAUNCH_CHECK(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  unsigned long long bits = ctx->h_scal[1];
+  std::memcpy(out, &bits, sizeof(double));
+  return ISDC_OK;
+}
+
+template <int DIM, int OFF, int P>
+void launch_sweep_end_b_p(isdc_ctx* ctx) {
+  const double nu_h2 = ctx->nu / (ctx->h * ctx->h), inv_h = 1.0 / ctx->h;
+  k_sweep_end_b<DIM, OFF, P><<<pp_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
+      ctx->n, ctx->N, nu_h2, inv_h, ctx->tables, ctx->U, ctx->F, ctx->FE, ctx->C, ctx->d_scal);
+}
+
+// End of a Burgers sweep: f and f^E at the last point, SDC residual, next C_m.
+template <int DIM>
+isdc_status sweep_end_b(isdc_ctx* ctx) {
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
+  {
+    const double M = ctx->M, P = ctx->P, Np = double(ctx->N);
+    // WENO5: per axis 4 face reconstructions of ~45 operations each
+    ProfScope ps(ctx, PC_SWEEP_END, (2.0 * P + 2.0 * (P - 1.0) + 2.0 + (P - 1.0)) * 8.0 * Np,
+                 (DIM * 190.0 + nb_ops(DIM) + 2.0 + (P - 1.0) * M + 2.0 * (P - 1.0) + 4.0 * (P - 1.0)) * Np, true);
+    if (ctx->off) {
+      switch (ctx->P) {
+        case 3: launch_sweep_end_b_p<DIM, 1, 3>(ctx); break;
+        case 4: launch_sweep_end_b_p<DIM, 1, 4>(ctx); break;
+        case 5: launch_sweep_end_b_p<DIM, 1, 5>(ctx); break;
+        case 6: launch_sweep_end_b_p<DIM, 1, 6>(ctx); break;
+        case 7: launch_sweep_end_b_p<DIM, 1, 7>(ctx); break;
+        default: launch_sweep_end_b_p<DIM, 1, 8>(ctx); break;
+      }
+    } else {
+      switch (ctx->P) {
+        case 2: launch_sweep_end_b_p<DIM, 0, 2>(ctx); break;
+        case 3: launch_sweep_end_b_p<DIM, 0, 3>(ctx); break;
+        case 4: launch_sweep_end_b_p<DIM, 0, 4>(ctx); break;
+        case 5: launch_sweep_end_b_p<DIM, 0, 5>(ctx); break;
+        case 6: launch_sweep_end_b_p<DIM, 0, 6>(ctx); break;
+        default: launch_sweep_end_b_p<DIM, 0, 7>(ctx); break;
+      }
+    }
+  }
+  LAUNCH_CHECK(ctx);
+  return ISDC_OK;
+}
+
+// One Burgers sweep (Sec. 2, Eq. 4 with f^E the WENO5 advection).
+template <int DIM>
+isdc_status sweep_once_b(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
+  const int n = ctx->n, P = ctx->P;
+  const size_t N = ctx->N;
+  const double nu_h2 = ctx->nu / (ctx->h * ctx->h), inv_h = 1.0 / ctx->h;
+  isdc_status st;
+  for (int m = 0; m < P - 1; ++m) {
+    const double dtm = ctx->tables.dtm[m], a = dtm * ctx->nu;
+    const double inv_d0 = 1.0 / coef_per(DIM, n, a).d;
+    {
+      ProfScope ps(ctx, PC_RHS, (m >= 1 ? 5.0 : 4.0) * 8.0 * double(N),
+                   (m >= 1 ? DIM * 190.0 + nb_ops(DIM) + 6.0 : 4.0) * double(N), true);
+      k_rhs_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, inv_h, dtm, inv_d0, ctx->U + m * N,
+                                                                ctx->C + m * N, ctx->b, ctx->F + m * N,
+                                                                ctx->FE + m * N, m >= 1 ? 1 : 0);
+    }
+    LAUNCH_CHECK(ctx);
+    double* x = ctx->U + (m + 1) * N;  // initial guess u_{m+1}^k (Sec. 4.3)
+    if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
+      for (int c = 0; c < n_vcycles; ++c)
+        if ((st = vcycle_per<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+      *vcycles += n_vcycles;
+    } else {
+      const int limit = n_vcycles > 0 ? n_vcycles : ctx->opt.mg_max_cycles;
+      for (int c = 0; c < limit; ++c) {
+        double rn;
+        if ((st = node_residual_norm_per<DIM>(ctx, a, x, ctx->b, &rn)) != ISDC_OK) return st;
+        if (!(rn > ctx->opt.mg_tol)) break;
+        if ((st = vcycle_per<DIM>(ctx, m, a, x, ctx->b)) != ISDC_OK) return st;
+        ++*vcycles;
+      }
+    }
+  }
+  return sweep_end_b<DIM>(ctx);
+}
+
 // One SDC sweep with the compact stencil (Sec. 3, Eq. 5): the right-hand
 // sides carry W, the node solves invert W - dt_m nu L_9 (FP64 V-cycles).
 isdc_status sweep_once9(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
@@ -918,6 +1134,7 @@ isdc_status sweep_once9(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
 template <int DIM>
 isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
   if (ctx->stencil == 1) return sweep_once9(ctx, n_vcycles, vcycles);
+  if (ctx->equation == 1) return sweep_once_b<DIM>(ctx, n_vcycles, vcycles);
   const int n = ctx->n, P = ctx->P;
   const size_t N = ctx->N;
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
@@ -1047,6 +1264,29 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
                                                            ctx->G);
     }
     LAUNCH_CHECK(ctx);
+  } else if (ctx->equation == 1) {
+    const double inv_h = 1.0 / ctx->h;
+    if (ctx->nodes_pending) {  // resume: f and f^E at t_0 and every node
+      if (ctx->off)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+      for (int m = 0; m < P; ++m) {
+        {
+          ProfScope ps(ctx, PC_EVAL_F, 24.0 * double(N), (DIM * 190.0 + nb_ops(DIM) + 3.0) * double(N), true);
+          k_eval_f_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, inv_h, ctx->U + m * N,
+                                                                       ctx->F + m * N, ctx->FE + m * N);
+        }
+        LAUNCH_CHECK(ctx);
+      }
+      ctx->nodes_pending = 0;
+    } else {
+      {
+        ProfScope ps(ctx, PC_SPREAD, (1.0 + 3.0 * P) * 8.0 * double(N), (DIM * 190.0 + nb_ops(DIM) + 3.0) * double(N),
+                     true);
+        k_spread_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, inv_h, P, u, ctx->U, ctx->F,
+                                                                     ctx->FE);
+      }
+      LAUNCH_CHECK(ctx);
+    }
   } else if (ctx->nodes_pending) {
     // resume: the nodes were set; t_0 (not a node unless Gauss-Lobatto) is u
     if (ctx->off)
@@ -1070,7 +1310,9 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
   }
   ctx->cprime = ctx->opt.vcycle_fp32 && n_vcycles > 0 && !ctx->opt.vcycle_cap;
   // C_m of the first sweep
-  if ((st = ctx->stencil == 1 ? sweep_end9(ctx) : sweep_end<DIM>(ctx)) != ISDC_OK) return st;
+  if ((st = ctx->stencil == 1 ? sweep_end9(ctx) : ctx->equation == 1 ? sweep_end_b<DIM>(ctx) : sweep_end<DIM>(ctx)) !=
+      ISDC_OK)
+    return st;
 
   const bool until_tol = n_sweeps <= 0;
   const int cap = until_tol ? ctx->opt.max_sweeps : n_sweeps;
@@ -1278,6 +1520,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->use_graphs = 1;
   opt->temporal_blocking = -1;
   opt->stencil = 0;
+  opt->equation = 0;
   opt->stream = nullptr;
   return ISDC_OK;
 }
@@ -1312,6 +1555,7 @@ ISDC_API void isdc_destroy(isdc_ctx* ctx) {
   cudaFree(ctx->C);
   cudaFree(ctx->G);
   cudaFree(ctx->Rs);
+  cudaFree(ctx->FE);
   cudaFree(ctx->b);
   cudaFree(ctx->u_dev);
   free_hier(ctx->h64, false);
@@ -1346,7 +1590,12 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   const int64_t n = dims[0];
   for (int a = 1; a < ndim; ++a)
     if (dims[a] != n) return fail(nullptr, ISDC_ERR_UNSUPPORTED, "only equal sides are implemented");
-  if (n < 3 || ((n + 1) & n) != 0) return fail(nullptr, ISDC_ERR_INVALID_ARG, "side must be 2^j - 1 with j >= 2 (got %lld)", (long long)n);
+  const int equation = opt ? opt->equation : 0;
+  if (equation != 0 && equation != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown equation %d", equation);
+  if (equation == 0 && (n < 3 || ((n + 1) & n) != 0))
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "side must be 2^j - 1 with j >= 2 (got %lld)", (long long)n);
+  if (equation == 1 && (n < 8 || (n & (n - 1)) != 0))
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "periodic side must be 2^j with j >= 3 (got %lld)", (long long)n);
   if ((ndim == 2 && n > 46339) || (ndim == 3 && n > 1289))
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "grid too large for 32-bit point indices");
   if (nodes != ISDC_NODES_GAUSS_LOBATTO && nodes != ISDC_NODES_RADAU_RIGHT && nodes != ISDC_NODES_GAUSS_LEGENDRE)
@@ -1367,9 +1616,11 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   if (o.temporal_blocking < -1 || o.temporal_blocking > 2)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "temporal_blocking must be -1, 0, 1 or 2");
   if (o.stencil != 0 && o.stencil != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown stencil %d", o.stencil);
-  if (o.stencil == 1 && (ndim != 2 || o.smoother != ISDC_SMOOTHER_JACOBI || o.vcycle_fp32))
+  if (o.stencil == 1 && (ndim != 2 || o.smoother != ISDC_SMOOTHER_JACOBI || o.vcycle_fp32 || o.equation != 0))
     return fail(nullptr, ISDC_ERR_UNSUPPORTED,
                 "the compact stencil is implemented in 2D with damped-Jacobi smoothing and FP64 V-cycles");
+  if (o.equation == 1 && o.vcycle_fp32)
+    return fail(nullptr, ISDC_ERR_UNSUPPORTED, "viscous Burgers is implemented with FP64 V-cycles");
 
   isdc_ctx* ctx = new isdc_ctx();
   ctx->dim = ndim;
@@ -1381,7 +1632,8 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   ctx->P = M + ctx->off;
   ctx->nu = nu;
   ctx->dt = dt;
-  ctx->h = 1.0 / double(n + 1);
+  ctx->equation = o.equation;
+  ctx->h = o.equation == 1 ? 2.0 / double(n) : 1.0 / double(n + 1);
   ctx->opt = o;
   ctx->stencil = o.stencil;
   auto bail = [&](isdc_status st) {
@@ -1428,6 +1680,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   CREATE_TRY(cudaMalloc(&ctx->U, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->F, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->C, size_t(P - 1) * N * sizeof(double)));
+  if (ctx->equation == 1) CREATE_TRY(cudaMalloc(&ctx->FE, size_t(P) * N * sizeof(double)));
   if (ctx->stencil == 1) {
     CREATE_TRY(cudaMalloc(&ctx->G, size_t(P) * N * sizeof(double)));
     CREATE_TRY(cudaMalloc(&ctx->Rs, 3 * size_t(P - 1) * N * sizeof(double)));
@@ -1464,7 +1717,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   } else {
     if ((st = alloc_hier(ctx, ctx->h64, false)) != ISDC_OK) return bail(st);
-    if (ctx->stencil == 0) {
+    if (ctx->stencil == 0 && ctx->equation == 0) {
       if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
     }
     for (int m = 0; m < P - 1; ++m)
@@ -1553,6 +1806,15 @@ ISDC_API isdc_status isdc_vcycles(isdc_ctx* ctx, double a, double* x, const doub
   if (ctx->opt.vcycle_fp32) st = upload_ainv(ctx, ctx->h32, ctx->spare_slot, a);
   else st = upload_ainv(ctx, ctx->h64, ctx->spare_slot, a);
   if (st != ISDC_OK) return st;
+  if (ctx->equation == 1) {  // periodic (I - a L_h) x = b, row-scaled by d
+    k_scale<double><<<4 * 152, 256, 0, ctx->stream>>>(ctx->N, 1.0 / coef_per(ctx->dim, ctx->n, a).d, b, ctx->b);
+    LAUNCH_CHECK(ctx);
+    for (int c = 0; c < n_cycles; ++c)
+      if ((st = ctx->dim == 2 ? vcycle_per<2>(ctx, ctx->spare_slot, a, x, ctx->b)
+                              : vcycle_per<3>(ctx, ctx->spare_slot, a, x, ctx->b)) != ISDC_OK)
+        return st;
+    return ISDC_OK;
+  }
   if (ctx->stencil == 1) {  // (W - a L_9) x = b, row-scaled by c0
     k_scale<double><<<4 * 152, 256, 0, ctx->stream>>>(ctx->N, 1.0 / coef9(ctx->n, a).c0, b, ctx->b);
     LAUNCH_CHECK(ctx);

@@ -1,0 +1,314 @@
+// periodic_kernels.cuh -- sm_103a kernels of the viscous Burgers equation of
+// Sec. 4.1 on a periodic grid: u_t + sum_axes u u_x = nu Lap u on [-1,1)^DIM,
+// n = 2^j points per side (h = 2/n), x fastest, indices wrap (n is a power
+// of two, so a wrap is a mask).  The Laplacian is implicit (periodic 5/7-point
+// stencil, multigrid n, n/2, ..., 4 with a dense solve on the side-4 level);
+// the advection is explicit: conservative differences of u^2/2 with the
+// 5th-order WENO scheme of Jiang and Shu and local Lax-Friedrichs splitting
+// (alpha = max |u| over the six points of each face's stencil).
+#pragma once
+#include "sdc_kernels.cuh"
+
+namespace isdc {
+
+template <int DIM>
+__device__ __forceinline__ int plin(int i, int j, int k, int n) {
+  return DIM == 2 ? i + n * j : i + n * (j + n * k);
+}
+
+// Sum of the 2*DIM neighbours of (i,j,k) on the periodic grid.
+template <typename T, int DIM>
+__device__ __forceinline__ T pnbsum(const T* __restrict__ x, int i, int j, int k, int n) {
+  const int w = n - 1;
+  const T sx = x[plin<DIM>((i - 1) & w, j, k, n)] + x[plin<DIM>((i + 1) & w, j, k, n)];
+  const T sy = x[plin<DIM>(i, (j - 1) & w, k, n)] + x[plin<DIM>(i, (j + 1) & w, k, n)];
+  if (DIM == 2) return sx + sy;
+  const T sz = x[plin<DIM>(i, j, (k - 1) & w, n)] + x[plin<DIM>(i, j, (k + 1) & w, n)];
+  return (sx + sy) + sz;
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid on the row-scaled periodic system x - kappa * (neighbour sum) = beta.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_jacobi_per(int n, T kappa, T omega, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ xo,
+                 int zero_guess) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = plin<DIM>(i, j, k, n);
+  if (zero_guess) {
+    xo[p] = omega * beta[p];
+    return;
+  }
+  const T xp = x[p];
+  xo[p] = fma(omega, fma(kappa, pnbsum<T, DIM>(x, i, j, k, n), beta[p]) - xp, xp);
+}
+
+// Red-black half sweep, red = i+j(+k) even (0-based; n even keeps the
+// colouring consistent across the wrap).  Grid over (n/2) x n (x n).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rbgs_per(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+  const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (2 * ih >= n || j >= n) return;
+  const int i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0)) & 1);
+  const int p = plin<DIM>(i, j, k, n);
+  x[p] = zero_guess ? beta[p] : fma(kappa, pnbsum<T, DIM>(x, i, j, k, n), beta[p]);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_residual_per(int n, T kappa, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ r) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = plin<DIM>(i, j, k, n);
+  r[p] = fma(kappa, pnbsum<T, DIM>(x, i, j, k, n), beta[p]) - x[p];
+}
+
+// Full weighting to the coarse periodic grid (nc = n/2 points): coarse I sits
+// on fine 2I; weights [1 2 1] per axis, times wscale = d_f / (2^(2 DIM) d_c).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_restrict_per(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
+  const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y, K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
+  const int n = 2 * nc, w = n - 1;
+  auto row = [&](int j, int k) {
+    const T a = r[plin<DIM>((2 * I - 1) & w, j, k, n)], b = r[plin<DIM>(2 * I, j, k, n)],
+            c = r[plin<DIM>((2 * I + 1) & w, j, k, n)];
+    return (a + c) + T(2) * b;
+  };
+  auto plane = [&](int k) {
+    return (row((2 * J - 1) & w, k) + row((2 * J + 1) & w, k)) + T(2) * row(2 * J, k);
+  };
+  T acc;
+  if (DIM == 2) acc = plane(0);
+  else acc = (plane((2 * K - 1) & w) + plane((2 * K + 1) & w)) + T(2) * plane(2 * K);
+  bc[plin<DIM>(I, J, K, nc)] = acc * wscale;
+}
+
+// x += P e_c: linear interpolation from the coarse periodic grid, one thread
+// per fine point (even index: the coarse point; odd: the mean of two).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_prolong_per(int nc, const T* __restrict__ ec, T* __restrict__ x) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  const int n = 2 * nc, w = nc - 1;
+  if (i >= n || j >= n) return;
+  auto axis = [&](int f, int& c0, int& c1, T& w1) {  // coarse neighbours and the weight of the second
+    c0 = f >> 1;
+    c1 = (c0 + 1) & w;
+    w1 = (f & 1) ? T(0.5) : T(0);
+  };
+  int i0, i1, j0, j1, k0 = 0, k1 = 0;
+  T wi, wj, wk = T(0);
+  axis(i, i0, i1, wi);
+  axis(j, j0, j1, wj);
+  if (DIM == 3) axis(k, k0, k1, wk);
+  auto ev = [&](int kk) {
+    const T a = ec[plin<DIM>(i0, j0, kk, nc)], b = ec[plin<DIM>(i1, j0, kk, nc)];
+    const T c = ec[plin<DIM>(i0, j1, kk, nc)], d = ec[plin<DIM>(i1, j1, kk, nc)];
+    const T lo = a + wi * (b - a), hi = c + wi * (d - c);
+    return lo + wj * (hi - lo);
+  };
+  T v = ev(k0);
+  if (DIM == 3) v = v + wk * (ev(k1) - v);
+  x[plin<DIM>(i, j, k, n)] += v;
+}
+
+// Coarsest level (side 4): x = G beta with G = d (I - a L)^{-1} (NP x NP).
+template <typename T, int NP>
+__global__ void k_coarse_dense(const T* __restrict__ G, const T* __restrict__ beta, T* __restrict__ x) {
+  const int i = threadIdx.x;
+  if (i >= NP) return;
+  T acc = T(0);
+  for (int j = 0; j < NP; ++j) acc = fma(G[i * NP + j], beta[j], acc);
+  x[i] = acc;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_resnorm_per(int n, double kappa, double d, const double* __restrict__ x, const double* __restrict__ beta,
+                  unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  unsigned long long rb = 0;
+  if (i < n && j < n) {
+    const int p = plin<DIM>(i, j, k, n);
+    const double r = d * (fma(kappa, pnbsum<double, DIM>(x, i, j, k, n), beta[p]) - x[p]);
+    rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+  }
+  block_max_atomic(rb, out);
+}
+
+// ---------------------------------------------------------------------------
+// WENO5 advection, FP64.
+// ---------------------------------------------------------------------------
+// Face value from the five upwind-biased values v0..v4 (v2, v3 beside the
+// face): three 3-point candidates, smoothness indicators, nonlinear weights
+// from the linear weights (1/10, 6/10, 3/10), epsilon = 1e-6.
+__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4) {
+  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  const double s0 = v0 - 2.0 * v1 + v2, t0 = v0 - 4.0 * v1 + 3.0 * v2;
+  const double s1 = v1 - 2.0 * v2 + v3, t1 = v1 - v3;
+  const double s2 = v2 - 2.0 * v3 + v4, t2 = 3.0 * v2 - 4.0 * v3 + v4;
+  const double b0 = (13.0 / 12.0) * s0 * s0 + 0.25 * t0 * t0;
+  const double b1 = (13.0 / 12.0) * s1 * s1 + 0.25 * t1 * t1;
+  const double b2 = (13.0 / 12.0) * s2 * s2 + 0.25 * t2 * t2;
+  const double e0 = 1e-6 + b0, e1 = 1e-6 + b1, e2 = 1e-6 + b2;
+  const double a0 = 0.1 / (e0 * e0), a1 = 0.6 / (e1 * e1), a2 = 0.3 / (e2 * e2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// Numerical flux of u^2/2 at the face between w[2] and w[3] from the six
+// values w[0..5] along the axis (local Lax-Friedrichs splitting).
+__device__ __forceinline__ double weno_flux(const double (&w)[6]) {
+  double alpha = 0.0;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) alpha = fmax(alpha, fabs(w[t]));
+  double fp[6], fm[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double f = 0.5 * w[t] * w[t];
+    fp[t] = 0.5 * (f + alpha * w[t]);
+    fm[t] = 0.5 * (f - alpha * w[t]);
+  }
+  return weno5(fp[0], fp[1], fp[2], fp[3], fp[4]) + weno5(fm[5], fm[4], fm[3], fm[2], fm[1]);
+}
+
+// f^E(u) = -sum_axes (F_{i+1/2} - F_{i-1/2}) / h at point (i,j,k).
+template <int DIM>
+__device__ __forceinline__ double burgers_fe(const double* __restrict__ u, int i, int j, int k, int n, double inv_h) {
+  const int w = n - 1;
+  double acc = 0.0;
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    double v[7];  // points -3..+3 along the axis
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      const int o = t - 3;
+      const int ii = ax == 0 ? (i + o) & w : i, jj = ax == 1 ? (j + o) & w : j, kk = ax == 2 ? (k + o) & w : k;
+      v[t] = u[plin<DIM>(ii, jj, kk, n)];
+    }
+    const double wr[6] = {v[1], v[2], v[3], v[4], v[5], v[6]};  // face i+1/2: points i-2..i+3
+    const double wl[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};  // face i-1/2: points i-3..i+2
+    acc -= (weno_flux(wr) - weno_flux(wl)) * inv_h;
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// SDC sweep for Burgers, FP64.  Per point p: U_p, F_p = f(u_p) and the
+// explicit part FE_p = f^E(u_p) (stored: it is a wide stencil, not pointwise).
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ double plap_part(const double* __restrict__ u, int i, int j, int k, int n, int p,
+                                            double nu_h2) {
+  return nu_h2 * (pnbsum<double, DIM>(u, i, j, k, n) - double(2 * DIM) * u[p]);
+}
+
+// Start of a step: every point u_p = u, FE_p = f^E(u), F_p = FE_p + nu L u.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_spread_b(int n, size_t N, double nu_h2, double inv_h, int P, const double* __restrict__ u,
+               double* __restrict__ U, double* __restrict__ F, double* __restrict__ FE) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = plin<DIM>(i, j, k, n);
+  const double fe = burgers_fe<DIM>(u, i, j, k, n, inv_h);
+  const double f = fe + plap_part<DIM>(u, i, j, k, n, p, nu_h2);
+  const double up = u[p];
+  for (int m = 0; m < P; ++m) {
+    U[m * N + p] = up;
+    F[m * N + p] = f;
+    FE[m * N + p] = fe;
+  }
+}
+
+// F and FE of one point's values (resume from given node values).
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_eval_f_b(int n, double nu_h2, double inv_h, const double* __restrict__ u, double* __restrict__ f,
+               double* __restrict__ fe) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = plin<DIM>(i, j, k, n);
+  const double e = burgers_fe<DIM>(u, i, j, k, n, inv_h);
+  fe[p] = e;
+  f[p] = e + plap_part<DIM>(u, i, j, k, n, p, nu_h2);
+}
+
+// Right-hand side of node m's implicit Euler system (Eq. 4), row-scaled:
+//   b = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C_m,
+//   C_m = dt sum_j s_{m,j} f_j^k - dt_m f^E(u_m^k) - dt_m f^I(u_{m+1}^k).
+// For m >= 1 f^E(u_m^{k+1}) is evaluated here and stored with f_m; for m = 0
+// (u_0, fixed during the step) it is the stored value.
+template <int DIM>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rhs_b(int n, double nu_h2, double inv_h, double dtm, double inv_d, const double* __restrict__ Um,
+            const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm,
+            double* __restrict__ FEm, int fresh) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int p = plin<DIM>(i, j, k, n);
+  const double up = Um[p];
+  double fe;
+  if (fresh) {
+    fe = burgers_fe<DIM>(Um, i, j, k, n, inv_h);
+    FEm[p] = fe;
+    Fm[p] = fe + plap_part<DIM>(Um, i, j, k, n, p, nu_h2);
+  } else {
+    fe = FEm[p];
+  }
+  beta[p] = (fma(dtm, fe, up) + Cm[p]) * inv_d;
+}
+
+// End of a sweep: f and f^E at the last point, the max-norm SDC residual
+// (Sec. 3) and the next sweep's C_m.  Node j is point j + OFF.
+template <int DIM, int OFF, int P>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_sweep_end_b(int n, size_t N, double nu_h2, double inv_h, SweepTables tb, const double* __restrict__ U,
+                  double* __restrict__ F, double* __restrict__ FE, double* __restrict__ C,
+                  unsigned long long* __restrict__ Rbits) {
+  constexpr int M = P - OFF;
+  static_assert(M >= 2 && M <= kMaxM && P <= kMaxP, "point count out of range");
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  unsigned long long rb = 0;
+  if (i < n && j < n) {
+    const int p = plin<DIM>(i, j, k, n);
+    double u[P], f[P], fe[P], qf[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) u[m] = U[m * N + p];
+    const double* ul = U + (size_t)(P - 1) * N;
+    fe[P - 1] = burgers_fe<DIM>(ul, i, j, k, n, inv_h);
+    f[P - 1] = fe[P - 1] + plap_part<DIM>(ul, i, j, k, n, p, nu_h2);
+    F[(size_t)(P - 1) * N + p] = f[P - 1];
+    FE[(size_t)(P - 1) * N + p] = fe[P - 1];
+#pragma unroll
+    for (int m = 0; m < P - 1; ++m) {
+      f[m] = F[m * N + p];
+      fe[m] = FE[m * N + p];
+    }
+    qf[0] = 0.0;
+#pragma unroll
+    for (int m = 1; m < P; ++m) {
+      double acc = tb.dtQ[m][0] * f[OFF];
+#pragma unroll
+      for (int jj = 1; jj < M; ++jj) acc = fma(tb.dtQ[m][jj], f[jj + OFF], acc);
+      qf[m] = acc;
+      const unsigned long long bits =
+          (unsigned long long)__double_as_longlong((u[0] - u[m]) + acc) & 0x7fffffffffffffffull;
+      rb = bits > rb ? bits : rb;
+    }
+#pragma unroll
+    for (int m = 0; m < P - 1; ++m) {
+      const double sf = m == 0 ? qf[1] : qf[m + 1] - qf[m];
+      C[m * N + p] = fma(-tb.dtm[m], fe[m] + (f[m + 1] - fe[m + 1]), sf);
+    }
+  }
+  block_max_atomic(rb, Rbits);
+}
+
+}  // namespace isdc

@@ -34,6 +34,8 @@ ISDC_REACTION_NONE = 0
 ISDC_REACTION_ALLEN_CAHN = 1
 ISDC_STENCIL_SECOND_ORDER = 0
 ISDC_STENCIL_COMPACT = 1
+ISDC_EQUATION_REACTION_DIFFUSION = 0
+ISDC_EQUATION_BURGERS = 1
 
 
 class isdc_options(ctypes.Structure):
@@ -41,7 +43,8 @@ class isdc_options(ctypes.Structure):
                 ("omega", ctypes.c_double), ("vcycle_fp32", ctypes.c_int), ("reaction", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_max_cycles", ctypes.c_int), ("vcycle_cap", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("temporal_blocking", ctypes.c_int), ("stencil", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("temporal_blocking", ctypes.c_int), ("stencil", ctypes.c_int),
+                ("equation", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class isdc_kernel_stat(ctypes.Structure):
@@ -420,13 +423,14 @@ class Isdc:
                  omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
                  max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True,
                  temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stencil=ISDC_STENCIL_SECOND_ORDER,
-                 stream=None):
+                 equation=ISDC_EQUATION_REACTION_DIFFUSION, stream=None):
         import torch
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
         o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
         o.mg_tol, o.mg_max_cycles, o.vcycle_cap = mg_tol, mg_max_cycles, int(vcycle_cap)
         o.use_graphs, o.temporal_blocking, o.stencil = int(use_graphs), int(temporal_blocking), int(stencil)
+        o.equation = int(equation)
         s = stream if stream is not None else torch.cuda.current_stream()
         # torch's default stream has handle 0, which the C ABI reads as "create a
         # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.

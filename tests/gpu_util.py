@@ -31,4 +31,6 @@ def make_gpu(p: O.Problem, vcycle_fp32=False, **kw):
                   nodes={O.NODES_LOBATTO: G.ISDC_NODES_GAUSS_LOBATTO, O.NODES_RADAU_RIGHT: G.ISDC_NODES_RADAU_RIGHT,
                          O.NODES_LEGENDRE: G.ISDC_NODES_GAUSS_LEGENDRE}[p.nodes],
                   stencil={O.STENCIL_SECOND_ORDER: G.ISDC_STENCIL_SECOND_ORDER,
-                           O.STENCIL_COMPACT: G.ISDC_STENCIL_COMPACT}[p.stencil], **kw)
+                           O.STENCIL_COMPACT: G.ISDC_STENCIL_COMPACT}[p.stencil],
+                  equation={O.EQUATION_REACTION_DIFFUSION: G.ISDC_EQUATION_REACTION_DIFFUSION,
+                            O.EQUATION_BURGERS: G.ISDC_EQUATION_BURGERS}[p.equation], **kw)
