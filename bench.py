@@ -44,6 +44,10 @@ def workloads():
                                        vcycle_fp32=True, seed=2),
         "3d_n511_M5_mixed": W.workload_3d_511_mixed(),
         "2d_n127_M3_fp64": W.workload_2d_127(),
+        "3d_n255_M5_radau_fp64": W.workload_3d_255_radau(),
+        "3d_n255_M5_legendre_fp64": W.workload_3d_255_legendre(),
+        "2d_n1023_M5_compact_fp64": W.workload_2d_1023_compact(),
+        "2d_n1024_M5_burgers_fp64": W.workload_2d_1024_burgers(),
     }
 
 
@@ -175,8 +179,8 @@ def oracle_sweep_rate(w, n_override=None, sweeps=1):
     import oracle as O
     n = n_override or w.n
     p = O.Problem(w.ndim, n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
-                  reaction=w.reaction)
-    u0 = W.initial_condition(w.ndim, n, w.seed)
+                  reaction=w.reaction, nodes=w.nodes, stencil=w.stencil, equation=w.equation)
+    u0 = W.periodic_bump(w.ndim, n, w.seed) if w.equation == 1 else W.initial_condition(w.ndim, n, w.seed)
     O.build()
     t0 = time.perf_counter()
     O.isdc_step(p, u0, sweeps, w.n_vcycles)
@@ -190,7 +194,7 @@ def run_reference(args):
     if rank != 0:
         return
     w = workloads().get(args.workload, W.workload_3d_255())
-    n_sample = 127 if w.ndim == 3 and w.n > 127 else w.n
+    n_sample = (128 if w.equation == 1 else 127) if w.ndim == 3 and w.n > 127 else w.n
     for _ in range(args.warmup):
         oracle_sweep_rate(w, n_sample)
     total_dof_sweeps, total_t = 0.0, 0.0
@@ -228,10 +232,15 @@ def combine_ranks(times, work, world, device):
 def config_of(w):
     N = w.n ** w.ndim
     state_bytes = (3 * w.M + 2) * N * 8
-    return {"workload": w.name, "ndim": w.ndim, "n": w.n, "dofs": N, "M": w.M, "nodes": "gauss-lobatto",
+    return {"workload": w.name, "ndim": w.ndim, "n": w.n, "dofs": N, "M": w.M,
+            "nodes": ["gauss-lobatto", "gauss-radau-right", "gauss-legendre"][w.nodes],
+            "equation": "viscous Burgers, periodic, WENO5 advection" if w.equation == 1
+            else "u_t = nu Lap u + f^E(u), Dirichlet",
+            "stencil": "4th-order compact with W" if w.stencil == 1 else ("5-point" if w.ndim == 2 else "7-point"),
             "nu": w.nu, "dt": w.dt, "L_vcycles": w.n_vcycles,
             "smoother": ("rbgs" if w.smoother == 1 else "wjacobi") + f" V({w.nu1},{w.nu2})",
-            "reaction": "u-u^3", "tol": w.tol, "vcycle_precision": "fp32" if w.vcycle_fp32 else "fp64",
+            "reaction": "u-u^3" if (w.reaction == 1 and w.equation == 0) else "none",
+            "tol": w.tol, "vcycle_precision": "fp32" if w.vcycle_fp32 else "fp64",
             "l2": f"inputs larger than L2 (node state {state_bytes / 1e9:.2f} GB > {L2_BYTES / 1e6:.0f} MB L2)"
             if state_bytes > L2_BYTES else "inputs fit in L2 (latency-bound case)",
             "parallelism": "replicas (one independent instance per GPU)"}
@@ -255,9 +264,11 @@ def run_ours(args):
 
     w = workloads()[args.workload]
     N = w.n ** w.ndim
-    u0 = W.initial_condition(w.ndim, w.n, w.seed)
+    u0 = W.workload_initial(w)
     g = G.Isdc(w.ndim, w.n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
-               vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200, temporal_blocking=args.temporal_blocking)
+               vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200, temporal_blocking=args.temporal_blocking,
+               nodes=w.nodes, stencil=w.stencil, equation=w.equation,
+               reaction=G.ISDC_REACTION_ALLEN_CAHN if w.reaction == 1 else G.ISDC_REACTION_NONE)
     stream = torch.cuda.current_stream()
     u = torch.from_numpy(u0).cuda()
     for _ in range(args.warmup):
@@ -279,8 +290,7 @@ def run_ours(args):
         gpu_id = None
     clocks = ClockSampler(gpu_id)
     clocks.start()
-    if not args.no_profile:
-        g.profile(True, classes=[dominant])
+    g.profile(True, classes=[])  # launch counts only: no events, no synchronisation
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -294,10 +304,26 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
-    prof = g.profile_read() if not args.no_profile else full_prof
-    g.profile(False)
     elapsed = e0.elapsed_time(e1) / 1e3
+    launches = int(sum(v["launches"] for v in g.profile_read().values()))
+    g.profile(False)
+    # the dominant class's launches timed with CUDA events on the library's
+    # stream over a second timed region of the same length (the event read-back
+    # after every sweep would slow a latency-bound workload's first region)
+    profiled_elapsed = None
+    prof = full_prof
+    if not args.no_profile:
+        g.profile(True, classes=[dominant])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.step(u, 0, w.n_vcycles)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        profiled_elapsed = e0.elapsed_time(e1) / 1e3
+        prof = g.profile_read()
+        g.profile(False)
+    clk = clocks.stop()
     residual = g.residual()
     dof_sweeps = float(N * sum(sweeps))
 
@@ -322,13 +348,15 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if not w.vcycle_fp32 else "f64 (FP32 V-cycles)",
-        "data": "synthetic (seeded sin-mode initial data + N(0, 0.01^2) noise)",
+        "data": "synthetic (seeded " + ("periodic Gaussian" if w.equation == 1 else "sin-mode") +
+                " initial data + N(0, 0.01^2) noise)",
         "config": config_of(w),
         "steps_per_s": world * args.steps / elapsed,
         "sweeps_per_step": sweeps, "vcycles_per_step": vcycles, "residual_last_step": residual,
         "converged": all(s == 0 for s in statuses),
-        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "gpu_launches": launches,
         "roofline": roofline(prof, dominant, w.name, shares),
+        "profiled_region_ms_per_step": profiled_elapsed / args.steps * 1e3 if profiled_elapsed else None,
         "autotune": g.tuning(),
         "clocks": clk,
         "e2e": {"value": e2e_work / e2e_t, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": N * 8,
@@ -339,7 +367,8 @@ def run_ours(args):
         rate, dt, n = oracle_sweep_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "DOF-sweeps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"1 SDC sweep of step 1 of the workload ({n}^{w.ndim} grid, "
-                                          f"{w.M - 1} node solves x {w.n_vcycles} V-cycles + residual), "
+                                          f"{w.M - (1 if w.nodes == 0 else 0)} node solves x {w.n_vcycles} V-cycles"
+                                          f" + residual), "
                                           f"{dt:.1f} s single-threaded"}
     if rank == 0:
         print(json.dumps(line), flush=True)

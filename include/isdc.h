@@ -336,9 +336,12 @@ typedef struct {
 /* enable = 0: off.  Otherwise a bit mask over the kernel classes, in this
  * order: spread, eval_f, rhs, sweep_end, smooth_fine, residual_fine,
  * restrict_fine, prolong_fine, smooth_coarse, residual_coarse,
- * restrict_coarse, prolong_coarse, bottom, defect, update, resnorm (bit 0 =
- * spread).  Launch counts, bytes and ops are kept for every class; only the
- * classes in the mask get events (-1 times them all). */
+ * restrict_coarse, prolong_coarse, bottom, defect, update, resnorm, w_inverse
+ * (bit 0 = spread).  Launch counts, bytes and ops are kept for every class;
+ * only the classes in the mask get events (-1 times them all).  A value with
+ * no class bit but another bit set (e.g. 1 << 30) counts launches, bytes and
+ * ops without events and without the per-sweep synchronisation that reading
+ * graph-replayed events needs. */
 isdc_status isdc_profile_enable(isdc_ctx *ctx, int enable);
 
 /* Synchronise and copy up to cap class records (classes with launches only)

@@ -54,6 +54,9 @@ class Workload:
     tol: float = 1e-10
     vcycle_fp32: bool = False
     seed: int = 1
+    nodes: int = 0          # 0 Gauss-Lobatto, 1 Gauss-Radau (right), 2 Gauss-Legendre
+    stencil: int = 0        # 0 5/7-point, 1 4th-order compact with W (2D)
+    equation: int = 0       # 0 reaction-diffusion (Dirichlet), 1 viscous Burgers (periodic, n = 2^j)
 
     def as_dict(self):
         return asdict(self)
@@ -61,6 +64,30 @@ class Workload:
     @property
     def N(self):
         return self.n ** self.ndim
+
+
+def periodic_grid_coords(n: int) -> np.ndarray:
+    """x_i = -1 + 2 i / n, i = 0..n-1: the periodic grid on [-1, 1)."""
+    return -1.0 + (2.0 / n) * np.arange(n, dtype=np.float64)
+
+
+def periodic_bump(ndim: int, n: int, seed: int, sigma: float = 0.1, noise_std: float = 0.01) -> np.ndarray:
+    """exp(-|x|^2 / sigma^2) on the periodic grid plus seeded N(0, noise_std^2)
+    noise (x fastest): the Burgers initial value of Sec. 4.1 (sigma = 0.1)."""
+    x = periodic_grid_coords(n)
+    g = np.meshgrid(*([x] * ndim), indexing="ij")[::-1]
+    r2 = sum(c ** 2 for c in g)
+    u = np.exp(-r2 / sigma ** 2)
+    if noise_std:
+        u = u + noise_std * np.random.default_rng(seed).standard_normal(u.shape)
+    return np.ascontiguousarray(u)
+
+
+def workload_initial(w: "Workload") -> np.ndarray:
+    """The workload's initial value: periodic bump (Burgers) or sine product + noise."""
+    if w.equation == 1:
+        return periodic_bump(w.ndim, w.n, w.seed)
+    return initial_condition(w.ndim, w.n, w.seed)
 
 
 def _log_uniform(rng, lo, hi):
@@ -119,3 +146,26 @@ def request_stream(count: int = 2000, rate: float = 200.0, seed: int = 5):
         out.append((t, Workload(f"req{r}", ndim, 2 ** j - 1, nu, M, dt, 10, 2, sm, nu1, nu2,
                                 vcycle_fp32=True, seed=seed * 100003 + r)))
     return out
+
+
+def workload_3d_255_radau() -> Workload:
+    """The 3D 255^3 FP64 workload with M = 5 right Gauss-Radau nodes (5 node solves per sweep)."""
+    return Workload("3d_n255_M5_radau_fp64", 3, 255, 0.1, 5, 0.02, 20, 2, 1, 2, 2, seed=2, nodes=1)
+
+
+def workload_3d_255_legendre() -> Workload:
+    """The 3D 255^3 FP64 workload with M = 5 Gauss-Legendre nodes (end-point quadrature)."""
+    return Workload("3d_n255_M5_legendre_fp64", 3, 255, 0.1, 5, 0.02, 20, 2, 1, 2, 2, seed=2, nodes=2)
+
+
+def workload_2d_1023_compact() -> Workload:
+    """2D heat-type problem with the 4th-order compact stencil and W (Sec. 3, Eq. 5):
+    1023^2, nu = 0.1, dt = 0.01, M = 5, damped Jacobi V(2,2), L = 2."""
+    return Workload("2d_n1023_M5_compact_fp64", 2, 1023, 0.1, 5, 0.01, 10, 2, 0, 2, 2, seed=6, stencil=1)
+
+
+def workload_2d_1024_burgers() -> Workload:
+    """Viscous Burgers of Sec. 4.1 on the periodic [-1,1)^2, 1024^2 points, nu = 0.1,
+    dt = 0.0005, M = 5, red-black V(2,2), L = 2 (seeded noise on the Gaussian)."""
+    return Workload("2d_n1024_M5_burgers_fp64", 2, 1024, 0.1, 5, 0.0005, 10, 2, 1, 2, 2, reaction=0, seed=7,
+                    equation=1)

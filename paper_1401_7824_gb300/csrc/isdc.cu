@@ -128,6 +128,7 @@ struct isdc_ctx {
   cudaGraphExec_t sweep_graph = nullptr;
   int graph_vcycles = 0;
   unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
+  bool graph_counted = false;  // captured with the profiler on (per-class launch counts recorded)
   // z-planes per thread of the fine-level red-black smoothers (autotuned)
   int zb64 = 1, zb32 = 1;
   int tb_depth = 0, tb_zc = 32;  // temporal blocking of the split FP32 fine level (sweeps per pass, planes per block)
@@ -894,6 +895,12 @@ isdc_status sweep_end(isdc_ctx* ctx) {
 // Viscous Burgers on the periodic grid (Sec. 4.1), FP64: multigrid on
 // (I - a L_h) x = b with periodic kernels, and the sweep with stored f^E.
 // ---------------------------------------------------------------------------
+// Algorithmic FP64 operations of the WENO5 advection per point and axis: one
+// face flux (u^2/2 and the split fluxes at 6 points: 36; two reconstructions
+// of 50 add/multiply/FMA/divide each) and the difference (the kernels compute
+// every face twice, once from each side).
+constexpr double kWenoOps = 139.0;
+
 inline LevelCoef coef_per(int dim, int s, double a) {
   const double h = 2.0 / s, c = a / (h * h), d = 1.0 + 2.0 * dim * c;
   return {c, d, c / d};
@@ -1028,9 +1035,10 @@ isdc_status sweep_end_b(isdc_ctx* ctx) {
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scal, 0, sizeof(unsigned long long), ctx->stream));
   {
     const double M = ctx->M, P = ctx->P, Np = double(ctx->N);
-    // WENO5: per axis 4 face reconstructions of ~45 operations each
+    // algorithmic FP64 operations: WENO5 advection kWenoOps per axis (one face
+    // flux per point and axis), Laplacian, dt Q f, residual, C_m
     ProfScope ps(ctx, PC_SWEEP_END, (2.0 * P + 2.0 * (P - 1.0) + 2.0 + (P - 1.0)) * 8.0 * Np,
-                 (DIM * 190.0 + nb_ops(DIM) + 2.0 + (P - 1.0) * M + 2.0 * (P - 1.0) + 4.0 * (P - 1.0)) * Np, true);
+                 (DIM * kWenoOps + nb_ops(DIM) + 3.0 + (P - 1.0) * M + 6.0 * (P - 1.0) - 1.0) * Np, true);
     if (ctx->off) {
       switch (ctx->P) {
         case 3: launch_sweep_end_b_p<DIM, 1, 3>(ctx); break;
@@ -1067,7 +1075,7 @@ isdc_status sweep_once_b(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
     const double inv_d0 = 1.0 / coef_per(DIM, n, a).d;
     {
       ProfScope ps(ctx, PC_RHS, (m >= 1 ? 5.0 : 4.0) * 8.0 * double(N),
-                   (m >= 1 ? DIM * 190.0 + nb_ops(DIM) + 6.0 : 4.0) * double(N), true);
+                   (m >= 1 ? DIM * kWenoOps + nb_ops(DIM) + 6.0 : 4.0) * double(N), true);
       k_rhs_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, inv_h, dtm, inv_d0, ctx->U + m * N,
                                                                 ctx->C + m * N, ctx->b, ctx->F + m * N,
                                                                 ctx->FE + m * N, m >= 1 ? 1 : 0);
@@ -1196,7 +1204,8 @@ template <int DIM>
 isdc_status capture_sweep(isdc_ctx* ctx, int n_vcycles) {
   Profiler& P = ctx->prof;
   const unsigned mask = P.on ? P.event_mask : 0u;
-  if (ctx->sweep_graph && ctx->graph_vcycles == n_vcycles && ctx->graph_mask == mask && (mask || !P.on)) {
+  if (ctx->sweep_graph && ctx->graph_vcycles == n_vcycles && ctx->graph_mask == mask &&
+      ctx->graph_counted == P.on) {
     return ISDC_OK;
   }
   if (ctx->sweep_graph) {
@@ -1234,6 +1243,7 @@ isdc_status capture_sweep(isdc_ctx* ctx, int n_vcycles) {
   if (e != cudaSuccess) return fail(ctx, ISDC_ERR_CUDA, "sweep graph: %s", cudaGetErrorString(e));
   ctx->graph_vcycles = n_vcycles;
   ctx->graph_mask = mask;
+  ctx->graph_counted = P.on;
   return ISDC_OK;
 }
 
@@ -1271,7 +1281,7 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
       for (int m = 0; m < P; ++m) {
         {
-          ProfScope ps(ctx, PC_EVAL_F, 24.0 * double(N), (DIM * 190.0 + nb_ops(DIM) + 3.0) * double(N), true);
+          ProfScope ps(ctx, PC_EVAL_F, 24.0 * double(N), (DIM * kWenoOps + nb_ops(DIM) + 3.0) * double(N), true);
           k_eval_f_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, inv_h, ctx->U + m * N,
                                                                        ctx->F + m * N, ctx->FE + m * N);
         }
@@ -1280,7 +1290,7 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
       ctx->nodes_pending = 0;
     } else {
       {
-        ProfScope ps(ctx, PC_SPREAD, (1.0 + 3.0 * P) * 8.0 * double(N), (DIM * 190.0 + nb_ops(DIM) + 3.0) * double(N),
+        ProfScope ps(ctx, PC_SPREAD, (1.0 + 3.0 * P) * 8.0 * double(N), (DIM * kWenoOps + nb_ops(DIM) + 3.0) * double(N),
                      true);
         k_spread_b<DIM><<<pp_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, inv_h, P, u, ctx->U, ctx->F,
                                                                      ctx->FE);
@@ -1330,7 +1340,7 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
       CUDA_TRY(ctx, cudaGraphLaunch(ctx->sweep_graph, ctx->stream));
       vcycles += (long long)n_vcycles * (P - 1);
       if (ctx->prof.on) {  // read the replay's event nodes before the next replay re-records them
-        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->prof.event_mask) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         prof_graph_replayed(ctx);
       }
     } else if ((st = sweep_once<DIM>(ctx, n_vcycles, &vcycles)) != ISDC_OK) {
@@ -1842,7 +1852,7 @@ ISDC_API isdc_status isdc_profile_enable(isdc_ctx* ctx, int enable) {
     std::fill(P.launches, P.launches + PC_COUNT, 0LL);
   }
   P.on = enable != 0;
-  P.event_mask = unsigned(enable);
+  P.event_mask = unsigned(enable) & ((1u << PC_COUNT) - 1u);
   return ISDC_OK;
 }
 

@@ -261,13 +261,14 @@ PROFILE_CLASSES = ["spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "resid
 
 def isdc_profile_enable(ctx, enable, classes=None):
     """enable: False = off; True = time every class with events, or only the
-    named `classes` (counts, bytes and ops are kept for all)."""
+    named `classes` (counts, bytes and ops are kept for all; classes=[] counts
+    only, with no events and no per-sweep synchronisation)."""
     if not enable:
         mask = 0
     elif classes is None:
         mask = -1
     else:
-        mask = 0
+        mask = 1 << 30 if not classes else 0
         for c in classes:
             mask |= 1 << PROFILE_CLASSES.index(c)
     _check(load().isdc_profile_enable(ctx, mask), ctx)

@@ -442,3 +442,33 @@ def test_radau_legendre_graph_replay_is_bitwise_identical(kind):
         outs.append((u.cpu().numpy(), g.stats()))
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
+
+
+def test_profiler_counts_only_and_event_modes_agree():
+    """Counting without events (no per-sweep synchronisation) and timing one
+    class with events give the same launch counts, bytes and ops per class for
+    the same work; only the timed class gets a duration (-1 marks an untimed
+    class); results do not change."""
+    p = O.Problem(3, 31, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2)
+    u0 = initial_condition(3, 31, seed=25)
+    reads, outs = [], []
+    for classes in ([], ["smooth_fine"], None):
+        g = make_gpu(p)
+        u = to_dev(u0)
+        g.step(u, 2, 2)
+        if classes is None:
+            g.step(u, 3, 2)
+        else:
+            g.profile(True, classes=classes)
+            g.step(u, 3, 2)
+            reads.append(g.profile_read())
+            g.profile(False)
+        outs.append(u.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[1], outs[2])
+    a, b = reads
+    assert a.keys() == b.keys() and "smooth_fine" in a
+    for k in a:
+        assert a[k]["launches"] == b[k]["launches"] and a[k]["bytes"] == b[k]["bytes"]
+        assert a[k]["total_ms"] == -1.0                         # not timed
+        assert (b[k]["total_ms"] > 0.0) == (k == "smooth_fine")  # only the named class is timed
