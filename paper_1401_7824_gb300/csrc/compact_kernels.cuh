@@ -70,15 +70,86 @@ __global__ void __launch_bounds__(kBX* kBY)
   block_max_atomic(rb, out);
 }
 
-// Coarsest (side 3) level: x = G beta with G = c0 (W - a L_9)^{-1} (9 x 9).
-template <typename T>
-__global__ void k_coarse9(const T* __restrict__ G, const T* __restrict__ beta, T* __restrict__ x) {
-  const int i = threadIdx.x;
-  if (i >= 9) return;
-  T acc = T(0);
-#pragma unroll
-  for (int j = 0; j < 9; ++j) acc = fma(G[i * 9 + j], beta[j], acc);
-  x[i] = acc;
+// Bottom of the compact V-cycle: every level with side <= the threshold in one
+// block, in shared memory (local levels 0..nlev-1; the last is the side-3 grid
+// solved with the precomputed c0 (W - a L_9)^{-1}).  Damped Jacobi, full
+// weighting, bilinear interpolation: the grid-wide kernels' arithmetic.
+struct BottomParams9 {
+  int nlev;
+  int side[kMaxLevels];
+  double ke[kMaxLevels], kc[kMaxLevels];  // row-scaled edge / corner couplings per level
+  double rscale[kMaxLevels];              // restriction factor c0_l / (16 c0_{l+1})
+  int nu1, nu2;
+  double omega;
+  const double* G;  // c0 (W - a L_9)^{-1} on the side-3 grid, row-major 9 x 9
+};
+
+__device__ void bt9_smooth(const BottomParams9& P, int l, double* x, const double* b, double* t) {
+  const int n = P.side[l], Np = n * n;
+  for (int p = threadIdx.x; p < Np; p += blockDim.x) t[p] = x[p];
+  __syncthreads();
+  for (int p = threadIdx.x; p < Np; p += blockDim.x) {
+    const int i = p % n, j = p / n;
+    const double r =
+        fma(P.ke[l], nbsum<double, 2>(t, i, j, 0, n, p), fma(P.kc[l], corner_sum<double>(t, i, j, n, p), b[p])) - t[p];
+    x[p] = fma(P.omega, r, t[p]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBottomThreads)
+    k_bottom9(BottomParams9 P, const double* __restrict__ b_top, double* __restrict__ x_top, int load_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* base = reinterpret_cast<double*>(smem_raw);
+  double *X[kMaxLevels], *B[kMaxLevels], *Tt[kMaxLevels];
+  int off = 0;
+  for (int l = 0; l < P.nlev; ++l) {
+    const int Np = P.side[l] * P.side[l];
+    X[l] = base + off; off += Np;
+    B[l] = base + off; off += Np;
+    Tt[l] = base + off; off += Np;
+  }
+  {
+    const int Np = P.side[0] * P.side[0];
+    for (int p = threadIdx.x; p < Np; p += blockDim.x) {
+      B[0][p] = b_top[p];
+      X[0][p] = load_x ? x_top[p] : 0.0;  // zero when entered as a coarse-grid correction
+    }
+  }
+  __syncthreads();
+  const int last = P.nlev - 1;
+  for (int l = 0; l < last; ++l) {
+    const int n = P.side[l], nc = P.side[l + 1];
+    for (int s = 0; s < P.nu1; ++s) bt9_smooth(P, l, X[l], B[l], Tt[l]);
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
+      const int i = p % n, j = p / n;
+      Tt[l][p] = fma(P.ke[l], nbsum<double, 2>(X[l], i, j, 0, n, p),
+                     fma(P.kc[l], corner_sum<double>(X[l], i, j, n, p), B[l][p])) - X[l][p];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * nc; q += blockDim.x) {
+      B[l + 1][q] = restrict_point<double, 2, false>(nc, P.rscale[l], Tt[l], q % nc, q / nc, 0);
+      X[l + 1][q] = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < 9; r += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < 9; ++q) acc = fma(P.G[r * 9 + q], B[last][q], acc);
+    X[last][r] = acc;
+  }
+  __syncthreads();
+  for (int l = last - 1; l >= 0; --l) {
+    const int nc = P.side[l + 1];
+    for (int q = threadIdx.x; q < (nc + 1) * (nc + 1); q += blockDim.x)
+      prolong_cell<double, 2, false>(nc, X[l + 1], X[l], q % (nc + 1), q / (nc + 1), 0);
+    __syncthreads();
+    for (int s = 0; s < P.nu2; ++s) bt9_smooth(P, l, X[l], B[l], Tt[l]);
+  }
+  {
+    const int Np = P.side[0] * P.side[0];
+    for (int p = threadIdx.x; p < Np; p += blockDim.x) x_top[p] = X[0][p];
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -283,9 +283,9 @@ isdc_status alloc_hier(isdc_ctx* ctx, Hier<T>& H, bool own_level0) {
   }
   H.nlev = l;
   H.lb = 0;
-  if (ctx->stencil == 1 || periodic) H.lb = H.nlev - 1;  // grid-wide levels, dense coarsest solve
-  else
-    while (H.side[H.lb] > bottom_threshold(ctx->dim, sizeof(T) == 8)) ++H.lb;
+  // levels with side <= the threshold run in one block (compact 2D: 31; periodic: 32 in 2D, 8 in 3D)
+  const int thr = ctx->stencil == 1 ? 31 : periodic ? (ctx->dim == 2 ? 32 : 8) : bottom_threshold(ctx->dim, sizeof(T) == 8);
+  while (H.side[H.lb] > thr) ++H.lb;
   for (int q = 0; q < H.nlev; ++q) {
     const size_t bytes = H.npts[q] * sizeof(T);
     const bool global_level = q < H.lb;
@@ -701,11 +701,25 @@ isdc_status vcycle9(isdc_ctx* ctx, int slot, double a, double* x0, const double*
     LAUNCH_CHECK(ctx);
     xcur[l] = x;
   }
-  {  // side-3 level: dense solve (a one-level grid is the whole hierarchy)
+  {  // the levels with side <= 31 in one block, the side-3 one by the dense inverse
+    BottomParams9 B{};
+    B.nlev = H.nlev - H.lb;
+    for (int q = 0; q < B.nlev; ++q) {
+      const int s = H.side[H.lb + q];
+      const Coef9 k = coef9(s, a);
+      B.side[q] = s;
+      B.ke[q] = k.ke;
+      B.kc[q] = k.kc;
+      B.rscale[q] = q + 1 < B.nlev ? k.c0 / (coef9(H.side[H.lb + q + 1], a).c0 * 16.0) : 0.0;
+    }
+    B.nu1 = ctx->opt.nu1;
+    B.nu2 = ctx->opt.nu2;
+    B.omega = ctx->opt.omega;
+    B.G = H.Ainv + size_t(slot) * 81;
     const double* bb = H.lb == 0 ? b0 : H.b[H.lb];
     double* xb = H.lb == 0 ? x0 : H.x[H.lb];
-    ProfScope ps(ctx, PC_BOTTOM, 18.0 * 8, 81.0, true);
-    k_coarse9<double><<<1, 32, 0, ctx->stream>>>(H.Ainv + size_t(slot) * 81, bb, xb);
+    ProfScope ps(ctx, PC_BOTTOM, 2.0 * double(H.npts[H.lb]) * 8, 0.0, true);
+    k_bottom9<<<1, kBottomThreads, H.bottom_smem, ctx->stream>>>(B, bb, xb, H.lb == 0 ? 1 : 0);
     LAUNCH_CHECK(ctx);
     xcur[H.lb] = xb;
   }
@@ -974,13 +988,25 @@ isdc_status vcycle_per(isdc_ctx* ctx, int slot, double a, double* x0, const doub
     LAUNCH_CHECK(ctx);
     xcur[l] = x;
   }
-  {  // side-4 level: dense solve
+  {  // the levels with side <= 32 (2D) / 8 (3D) in one block, the side-4 one by the dense inverse
+    BottomParamsPer B{};
+    B.nlev = H.nlev - H.lb;
+    for (int q = 0; q < B.nlev; ++q) {
+      const int s = H.side[H.lb + q];
+      const LevelCoef lf = coef_per(DIM, s, a);
+      B.side[q] = s;
+      B.kappa[q] = lf.kappa;
+      B.rscale[q] = q + 1 < B.nlev ? lf.d / (coef_per(DIM, H.side[H.lb + q + 1], a).d * (DIM == 2 ? 16.0 : 64.0)) : 0.0;
+    }
+    B.smoother = ctx->opt.smoother;
+    B.nu1 = ctx->opt.nu1;
+    B.nu2 = ctx->opt.nu2;
+    B.omega = ctx->opt.omega;
+    B.G = H.Ainv + size_t(slot) * ainv_slot(ctx);
     const double* bb = H.lb == 0 ? b0 : H.b[H.lb];
     double* xb = H.lb == 0 ? x0 : H.x[H.lb];
-    const double* G = H.Ainv + size_t(slot) * ainv_slot(ctx);
-    ProfScope ps(ctx, PC_BOTTOM, 2.0 * double(H.npts[H.lb]) * 8, double(H.npts[H.lb] * H.npts[H.lb]), true);
-    if (DIM == 2) k_coarse_dense<double, 16><<<1, 32, 0, ctx->stream>>>(G, bb, xb);
-    else k_coarse_dense<double, 64><<<1, 64, 0, ctx->stream>>>(G, bb, xb);
+    ProfScope ps(ctx, PC_BOTTOM, 2.0 * double(H.npts[H.lb]) * 8, 0.0, true);
+    k_bottom_per<DIM><<<1, kBottomThreads, H.bottom_smem, ctx->stream>>>(B, bb, xb, H.lb == 0 ? 1 : 0);
     LAUNCH_CHECK(ctx);
     xcur[H.lb] = xb;
   }
@@ -1727,7 +1753,14 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
       if ((st = upload_ainv(ctx, ctx->h32, m, ctx->tables.dtm[m] * nu)) != ISDC_OK) return bail(st);
   } else {
     if ((st = alloc_hier(ctx, ctx->h64, false)) != ISDC_OK) return bail(st);
-    if (ctx->stencil == 0 && ctx->equation == 0) {
+    if (ctx->stencil == 1) {
+      cudaFuncSetAttribute(k_bottom9, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->h64.bottom_smem));
+    } else if (ctx->equation == 1) {
+      if (ndim == 2)
+        cudaFuncSetAttribute(k_bottom_per<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->h64.bottom_smem));
+      else
+        cudaFuncSetAttribute(k_bottom_per<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->h64.bottom_smem));
+    } else {
       if (ndim == 2) configure_bottom<double, 2>(ctx->h64); else configure_bottom<double, 3>(ctx->h64);
     }
     for (int m = 0; m < P - 1; ++m)
