@@ -495,6 +495,27 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
   return ISDC_OK;
 }
 
+// One colour pass on the split fine level with zb z-planes per thread.
+// Rows of the split layout hold H = (n+1)/2 slots, a power of two; from
+// H = 4 on the 4-slot form applies.
+template <int DIM>
+void launch_rbgs_split(cudaStream_t st, int zb, int s, float kappa, int colour, float* xc, const float* xo,
+                       const float* bc, bool zero) {
+  const int z = zero ? 1 : 0, H = (s + 1) / 2;
+  const int zbe = DIM == 3 ? zb : 1;
+  if (H % 4 != 0) {
+    const dim3 g = rb_grid(DIM, s, 1);
+    k_rbgs_split<DIM, 1><<<g, kBlock, 0, st>>>(s, kappa, colour, xc, xo, bc, z);
+    return;
+  }
+  const dim3 g(unsigned((H / 4 + kBX - 1) / kBX), unsigned((s + kBY - 1) / kBY),
+               unsigned(DIM == 3 ? (s + zbe - 1) / zbe : 1));
+  if (DIM == 2 || zb <= 1) k_rbgs_split4<DIM, 1><<<g, kBlock, 0, st>>>(s, kappa, colour, xc, xo, bc, z);
+  else if (zb == 2) k_rbgs_split4<DIM, 2><<<g, kBlock, 0, st>>>(s, kappa, colour, xc, xo, bc, z);
+  else if (zb == 4) k_rbgs_split4<DIM, 4><<<g, kBlock, 0, st>>>(s, kappa, colour, xc, xo, bc, z);
+  else k_rbgs_split4<DIM, 8><<<g, kBlock, 0, st>>>(s, kappa, colour, xc, xo, bc, z);
+}
+
 // One blocked pass of `depth` red-black sweeps on the split fine level (3D):
 // black read from xb_in, red written in place, black written to xb_out.
 inline void launch_rbgs_tb(cudaStream_t st, int depth, int zc, int s, float kappa, const float* xb_in, float* xr,
@@ -533,16 +554,15 @@ isdc_status smooth_split(isdc_ctx* ctx, float kappa, int nsw, bool zero, float**
     }
     return ISDC_OK;
   }
-  const dim3 gz = rb_grid(DIM, s, ctx->zb32);
   for (int it = 0; it < nsw; ++it, zero = false) {
     {
       ProfScope ps(ctx, PC_SMOOTH0, (zero ? 1.0 : 1.5) * Np * 4, zero ? 0.0 : pass_ops, false);
-      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 0, x0, *xb, b0, zero ? 1 : 0, ctx->zb32);
+      launch_rbgs_split<DIM>(ctx->stream, ctx->zb32, s, kappa, 0, x0, *xb, b0, zero);
     }
     LAUNCH_CHECK(ctx);
     {
       ProfScope ps(ctx, PC_SMOOTH0, 1.5 * Np * 4, pass_ops, false);
-      k_rbgs_split<DIM><<<gz, kBlock, 0, ctx->stream>>>(s, kappa, 1, *xb, x0, b1, 0, ctx->zb32);
+      launch_rbgs_split<DIM>(ctx->stream, ctx->zb32, s, kappa, 1, *xb, x0, b1, false);
     }
     LAUNCH_CHECK(ctx);
   }
@@ -1436,9 +1456,8 @@ float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0,
   if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { *st = ISDC_ERR_CUDA; return 0.f; }
   for (int colour = 0; colour < 2; ++colour) {
     if (xs0) {
-      k_rbgs_split<3><<<rb_grid(3, s, zb), kBlock, 0, ctx->stream>>>(s, 0.1f, colour, xs0 + colour * hn,
-                                                                     xs0 + (1 - colour) * hn, bs0 + colour * hn, 0,
-                                                                     zb);
+      launch_rbgs_split<3>(ctx->stream, zb, s, 0.1f, colour, xs0 + colour * hn, xs0 + (1 - colour) * hn,
+                           bs0 + colour * hn, false);
     } else {
       k_rbgs<T, 3><<<rb_grid(3, s, zb), kBlock, 0, ctx->stream>>>(s, T(0.1), colour, x, b, 0, zb);
     }

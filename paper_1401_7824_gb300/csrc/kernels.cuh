@@ -337,23 +337,91 @@ __global__ void __launch_bounds__(kBX* kBY)
 }
 
 // Red-black half sweep on the split layout: x_c = beta_c + kappa * (sum of the
-// other colour's neighbours); zero_guess: x_c = beta_c.
-template <int DIM>
+// other colour's neighbours); zero_guess: x_c = beta_c.  Each thread walks
+// ZB z-planes (3D; a compile-time count, so the loop unrolls and the loads of
+// all its planes are in flight together: the colour arrays do not alias).
+template <int DIM, int ZB>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs_split(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
-                 const float* __restrict__ bc, int zero_guess, int zb) {
+                 const float* __restrict__ bc, int zero_guess) {
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int H = (n + 1) >> 1;
   if (j >= n) return;
-  const int nz = DIM == 3 ? zb : 1;
+  constexpr int nz = DIM == 3 ? ZB : 1;
+#pragma unroll
   for (int kk = 0; kk < nz; ++kk) {
-    const int k = DIM == 3 ? blockIdx.z * zb + kk : 0;
-    if (k >= (DIM == 3 ? n : 1)) return;
+    const int k = DIM == 3 ? blockIdx.z * ZB + kk : 0;
     const int i0 = (colour + j + (DIM == 3 ? k : 0) + DIM) & 1;
     const int i = 2 * h + i0;
-    if (i >= n) continue;
-    const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
-    xc[slot] = zero_guess ? bc[slot] : fmaf(kappa, split_nbsum<DIM>(xo, h, i, i0, j, k, n, H), bc[slot]);
+    if (k < (DIM == 3 ? n : 1) && i < n) {
+      const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
+      xc[slot] = zero_guess ? bc[slot] : fmaf(kappa, split_nbsum<DIM>(xo, h, i, i0, j, k, n, H), bc[slot]);
+    }
+  }
+}
+
+// The same with 4 consecutive slots per thread: 16-byte loads of the rhs and of
+// the y/z neighbours and 16-byte stores (a row of H = (n+1)/2 slots is a power
+// of two >= 4, so every row starts 16-byte aligned); the x neighbours are one
+// 16-byte load plus one scalar.  Per lane the same FP32 operations in the same
+// order as k_rbgs_split (bitwise equal).  A slot past the end of a row (odd n,
+// i0 = 1) receives 0, which keeps that padding slot zero.
+template <int DIM, int ZB>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rbgs_split4(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
+                  const float* __restrict__ bc, int zero_guess) {
+  const int h = (blockIdx.x * kBX + threadIdx.x) * 4, j = blockIdx.y * kBY + threadIdx.y;
+  const int H = (n + 1) >> 1;
+  if (j >= n || h >= H) return;
+  constexpr int nz = DIM == 3 ? ZB : 1;
+#pragma unroll
+  for (int kk = 0; kk < nz; ++kk) {
+    const int k = DIM == 3 ? blockIdx.z * ZB + kk : 0;
+    if (k >= (DIM == 3 ? n : 1)) continue;
+    const int i0 = (colour + j + (DIM == 3 ? k : 0) + DIM) & 1;
+    const size_t r = size_t(H) * split_row<DIM>(j, k, n);
+    const float4 b4 = *reinterpret_cast<const float4*>(bc + r + h);
+    float4 v;
+    if (zero_guess) {
+      v = b4;
+    } else {
+      const float* row = xo + r;
+      // other-colour slots h-1+i0 .. h+3+i0 (x neighbours of the 4 lanes)
+      const float4 m4 = *reinterpret_cast<const float4*>(row + h);
+      float e[5];
+      if (i0 == 0) {
+        e[0] = h > 0 ? row[h - 1] : 0.f;
+        e[1] = m4.x; e[2] = m4.y; e[3] = m4.z; e[4] = m4.w;
+      } else {
+        e[0] = m4.x; e[1] = m4.y; e[2] = m4.z; e[3] = m4.w;
+        e[4] = h + 4 < H ? row[h + 4] : 0.f;
+      }
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 yd = j > 0 ? *reinterpret_cast<const float4*>(row + h - H) : zero4;
+      const float4 yu = j < n - 1 ? *reinterpret_cast<const float4*>(row + h + H) : zero4;
+      float4 zd = zero4, zu = zero4;
+      if (DIM == 3) {
+        const size_t hz = size_t(H) * n;
+        if (k > 0) zd = *reinterpret_cast<const float4*>(row + h - hz);
+        if (k < n - 1) zu = *reinterpret_cast<const float4*>(row + h + hz);
+      }
+      const float ydv[4] = {yd.x, yd.y, yd.z, yd.w}, yuv[4] = {yu.x, yu.y, yu.z, yu.w};
+      const float zdv[4] = {zd.x, zd.y, zd.z, zd.w}, zuv[4] = {zu.x, zu.y, zu.z, zu.w};
+      const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+      float out[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 2 * (h + q) + i0;
+        const float sx = (i > 0 ? e[q] : 0.f) + (i < n - 1 ? e[q + 1] : 0.f);
+        const float sy = ydv[q] + yuv[q];
+        float sum = sx + sy;
+        if (DIM == 3) sum = sum + (zdv[q] + zuv[q]);
+        out[q] = i < n ? fmaf(kappa, sum, bv[q]) : 0.f;
+      }
+      v = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    if (zero_guess && i0 == 1 && 2 * (h + 3) + 1 >= n) v.w = 0.f;  // padding slot stays zero
+    *reinterpret_cast<float4*>(xc + r + h) = v;
   }
 }
 
