@@ -348,10 +348,11 @@ isdc_status isdc_profile_enable(isdc_ctx *ctx, int enable);
  * to out; *count receives the number of such classes. */
 isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int *count);
 
-/* Launch shape chosen by the context's autotuner (not from the paper): z-planes
- * per thread of the fine-level red-black smoother in FP64 and in FP32 (3D
- * red-black contexts time 1, 2, 4 and 8 on their own arrays in isdc_create;
- * otherwise 1); for the FP32 fine level also the temporal-blocking depth
+/* Launch shape chosen by the context's autotuner (not from the paper): points
+ * per thread of the fine-level red-black smoother in FP64 (the length of the
+ * thread's diagonal run) and in FP32 (z-planes per thread of the split level);
+ * 3D red-black contexts time 1, 2, 4 and 8 on their own arrays in isdc_create,
+ * otherwise 1; for the FP32 fine level also the temporal-blocking depth
  * (red-black sweeps per pass, 0 = one pass per colour) and the z-planes per
  * block of the blocked pass.  Any output pointer may be NULL. */
 isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32, int *tb_depth, int *tb_planes);

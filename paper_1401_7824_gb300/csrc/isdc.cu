@@ -129,7 +129,8 @@ struct isdc_ctx {
   int graph_vcycles = 0;
   unsigned graph_mask = 0;  // profiler classes with event nodes in the graph
   bool graph_counted = false;  // captured with the profiler on (per-class launch counts recorded)
-  // z-planes per thread of the fine-level red-black smoothers (autotuned)
+  // points per thread of the red-black smoothers (autotuned): the diagonal run
+  // of k_rbgs3 on natural-layout levels, z-planes of the split FP32 level
   int zb64 = 1, zb32 = 1;
   int tb_depth = 0, tb_zc = 32;  // temporal blocking of the split FP32 fine level (sweeps per pass, planes per block)
   float* sp_xb = nullptr;        // second black array of the split level (blocked passes ping-pong into it)
@@ -239,6 +240,10 @@ void prof_graph_replayed(isdc_ctx* ctx) {
 }
 
 inline double nb_ops(int dim) { return dim == 2 ? 3.0 : 5.0; }
+// FP64/FP32 operations per updated point of a natural-layout red-black pass:
+// 3 additions + 1 FMA in 2D; in 3D 4 additions + 1 FMA per step of a diagonal
+// of zb points plus one addition for its first point (k_rbgs3).
+inline double rb_ops(int dim, int zb) { return dim == 2 ? 4.0 : 5.0 + 1.0 / zb; }
 
 // Row scaling of H = I - a L_h on a grid of side s: c = a/h^2, d = 1 + 2 dim c,
 // kappa = c / d.
@@ -379,14 +384,14 @@ isdc_status smooth_level(isdc_ctx* ctx, Hier<T>& H, int l, double a, T*& x, T* h
       const double Np = double(H.npts[l]);
       {
         ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, (zero ? 1.0 : 1.5) * Np * sizeof(T),
-                     (zero ? 0.0 : nb_ops(DIM) + 1.0) * 0.5 * Np, sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s, zb), kBlock, 0, ctx->stream>>>(s, kappa, 0, x, b, zero ? 1 : 0, zb);
+                     (zero ? 0.0 : rb_ops(DIM, zb)) * 0.5 * Np, sizeof(T) == 8);
+        launch_rbgs<T, DIM>(ctx->stream, s, kappa, 0, x, b, zero, zb);
       }
       LAUNCH_CHECK(ctx);
       {
-        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), (nb_ops(DIM) + 1.0) * 0.5 * Np,
+        ProfScope ps(ctx, l == 0 ? PC_SMOOTH0 : PC_SMOOTHC, 1.5 * Np * sizeof(T), rb_ops(DIM, zb) * 0.5 * Np,
                      sizeof(T) == 8);
-        k_rbgs<T, DIM><<<rb_grid(DIM, s, zb), kBlock, 0, ctx->stream>>>(s, kappa, 1, x, b, 0, zb);
+        launch_rbgs<T, DIM>(ctx->stream, s, kappa, 1, x, b, false, zb);
       }
       LAUNCH_CHECK(ctx);
     }
@@ -1446,8 +1451,9 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
 }
 
 // Autotuner for the red-black smoothers (3D): on every grid-wide level with
-// side >= 31, time one red and one black pass with 1, 2, 4 and 8 z-planes per
-// thread on the context's own arrays of that level (zeroed first; the values
+// side >= 31, time one red and one black pass with 1, 2, 4 and 8 points per
+// thread (diagonal runs, or z-planes on the split level) on the context's own
+// arrays of that level (zeroed first; the values
 // do not change the timing) and keep the fastest.  Runs once, in isdc_create.
 template <typename T>
 float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0, float* bs0, size_t hn,
@@ -1459,7 +1465,7 @@ float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0,
       launch_rbgs_split<3>(ctx->stream, zb, s, 0.1f, colour, xs0 + colour * hn, xs0 + (1 - colour) * hn,
                            bs0 + colour * hn, false);
     } else {
-      k_rbgs<T, 3><<<rb_grid(3, s, zb), kBlock, 0, ctx->stream>>>(s, T(0.1), colour, x, b, 0, zb);
+      launch_rbgs<T, 3>(ctx->stream, s, T(0.1), colour, x, b, false, zb);
     }
   }
   float ms = 0.f;

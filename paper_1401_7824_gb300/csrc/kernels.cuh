@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace isdc {
 
 constexpr int kBX = 32;  // threads along x (one warp)
@@ -67,25 +69,88 @@ __global__ void __launch_bounds__(kBX* kBY)
 }
 
 // Red-black Gauss-Seidel half sweep: colour 0 = red = (i+j+k) even in 1-based
-// interior indices.  Each thread owns one point of the colour and solves its
-// row: x_p = beta_p + kappa * (sum of neighbours).  zero_guess (red pass from
-// x == 0): the neighbours are zero.
-// zb: z-planes per thread (3D; blockIdx.z covers planes [zb*blockIdx.z, +zb)),
-// picked by the context's autotuner.
-template <typename T, int DIM>
+// interior indices.  Each thread owns points of the colour and solves their
+// rows: x_p = beta_p + kappa * (sum of neighbours).  zero_guess (red pass from
+// x == 0): the neighbours are zero.  A colour pass reads only the other
+// colour, so every thread issues all its loads before its first store.
+//
+// 2D: one point per thread.
+template <typename T>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_rbgs(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess, int zb) {
+    k_rbgs2(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
   const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (j >= n) return;
-  const int nz = DIM == 3 ? zb : 1;
-  for (int kk = 0; kk < nz; ++kk) {
-    const int k = DIM == 3 ? blockIdx.z * zb + kk : 0;
-    if (k >= (DIM == 3 ? n : 1)) return;
-    // (i+1)+(j+1)+(k+1) parity == colour  <=>  i parity == (colour + j + k + DIM) & 1
-    const int i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0) + DIM) & 1);
-    if (i >= n) continue;
-    const int p = lin<DIM>(i, j, k, n);
-    x[p] = zero_guess ? beta[p] : fma(kappa, nbsum<T, DIM>(x, i, j, k, n, p), beta[p]);
+  // (i+1)+(j+1) parity == colour  <=>  i parity == (colour + j) & 1
+  const int i = 2 * ih + ((colour + j) & 1);
+  if (i >= n) return;
+  const int p = lin<2>(i, j, 0, n);
+  x[p] = zero_guess ? beta[p] : fma(kappa, nbsum<T, 2>(x, i, j, 0, n, p), beta[p]);
+}
+
+// 3D: each thread walks ZB points of the colour along the (0,1,1) diagonal at
+// a fixed i, p_t = (i, jd + t, k0 + t), t < ZB (the colour of a point does not
+// change along that diagonal).  The neighbour sum is built from three pair
+// sums, X = x(i-1) + x(i+1), L = x(j-1) + x(k-1), U = x(j+1) + x(k+1), as
+// (X + L) + U.  U at p_t is the sum of the same two points as L at p_{t+1},
+// so a step loads 4 neighbours and issues 4 additions and one FMA where the
+// plain sum takes 6 and 6.  Addition is commutative in IEEE arithmetic, so a
+// point's value does not depend on ZB or on where its diagonal starts.
+template <typename T, int ZB>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rbgs3(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+  const int ih = blockIdx.x * kBX + threadIdx.x;
+  const int jd = int(blockIdx.y * kBY + threadIdx.y) - (ZB - 1);
+  const int k0 = blockIdx.z * ZB;
+  // (i+1)+(j+1)+(k+1) parity == colour, j + k = jd + k0 + 2t
+  const int i = 2 * ih + ((colour + jd + k0 + 1) & 1);
+  if (i >= n) return;
+  const int nn = n * n;
+  T xs[ZB], us[ZB], bs[ZB], l0 = T(0);
+#pragma unroll
+  for (int t = 0; t < ZB; ++t) {
+    const int j = jd + t, k = k0 + t;
+    if (j < 0 || j >= n || k >= n) continue;
+    const int p = i + n * j + nn * k;
+    bs[t] = beta[p];
+    if (zero_guess) continue;
+    xs[t] = (i > 0 ? x[p - 1] : T(0)) + (i < n - 1 ? x[p + 1] : T(0));
+    us[t] = (j < n - 1 ? x[p + n] : T(0)) + (k < n - 1 ? x[p + nn] : T(0));
+    if (t == 0 || j == 0) l0 = (j > 0 ? x[p - n] : T(0)) + (k > 0 ? x[p - nn] : T(0));  // first point
+  }
+#pragma unroll
+  for (int t = 0; t < ZB; ++t) {
+    const int j = jd + t, k = k0 + t;
+    if (j < 0 || j >= n || k >= n) continue;
+    const int p = i + n * j + nn * k;
+    if (zero_guess) {
+      x[p] = bs[t];
+      continue;
+    }
+    const T lt = (t == 0 || j == 0) ? l0 : us[t > 0 ? t - 1 : 0];
+    x[p] = fma(kappa, (xs[t] + lt) + us[t], bs[t]);
+  }
+}
+
+// One colour pass of the natural-layout red-black smoother; zb in {1, 2, 4, 8}
+// is the 3D diagonal length (the context's autotuner picks it).
+template <typename T, int DIM>
+inline void launch_rbgs(cudaStream_t st, int n, T kappa, int colour, T* x, const T* beta, bool zero_guess, int zb) {
+  const dim3 blk(kBX, kBY, 1);
+  const int gx = ((n + 1) / 2 + kBX - 1) / kBX;
+  if (DIM == 2) {
+    k_rbgs2<T><<<dim3(gx, (n + kBY - 1) / kBY, 1), blk, 0, st>>>(n, kappa, colour, x, beta, zero_guess ? 1 : 0);
+    return;
+  }
+  auto go = [&](auto zbc) {
+    constexpr int ZB = decltype(zbc)::value;
+    const dim3 g(gx, (n + ZB - 1 + kBY - 1) / kBY, (n + ZB - 1) / ZB);
+    k_rbgs3<T, ZB><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zero_guess ? 1 : 0);
+  };
+  switch (zb) {
+    case 8: go(std::integral_constant<int, 8>()); break;
+    case 4: go(std::integral_constant<int, 4>()); break;
+    case 2: go(std::integral_constant<int, 2>()); break;
+    default: go(std::integral_constant<int, 1>()); break;
   }
 }
 

@@ -157,7 +157,6 @@ inline double restrict_scale(int dim, int s, int sc, double a) {
 }
 
 inline dim3 grid_pts(int dim, int s) { return dim3((s + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
-inline dim3 grid_rb(int dim, int s) { return dim3(((s + 1) / 2 + kBX - 1) / kBX, (s + kBY - 1) / kBY, dim == 3 ? s : 1); }
 
 struct Solve {
   int dim, smoother, nu1, nu2;
@@ -180,8 +179,8 @@ isdc_status smooth(const Solve& S, int l, double*& x, double* home, const double
       k_jacobi<double, DIM><<<grid_pts(DIM, s), blk, 0, S.stream>>>(s, kappa, S.omega, x, b, out, zero ? 1 : 0);
       x = out;
     } else {
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 0, x, b, zero ? 1 : 0, 1);
-      k_rbgs<double, DIM><<<grid_rb(DIM, s), blk, 0, S.stream>>>(s, kappa, 1, x, b, 0, 1);
+      launch_rbgs<double, DIM>(S.stream, s, kappa, 0, x, b, zero, 1);
+      launch_rbgs<double, DIM>(S.stream, s, kappa, 1, x, b, false, 1);
     }
     STATIC_TRY(cudaGetLastError());
     zero = false;
