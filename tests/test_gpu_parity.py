@@ -25,6 +25,7 @@ VCYCLE_CASES = [
     (3, 7, RB, 2, 2, 0.3),       # bottom block only
     (2, 3, J, 1, 1, 0.7),        # coarsest grid only: exact solve
     (3, 127, RB, 2, 2, 0.0005),
+    (3, 31, J, 0, 1, 0.02),      # no pre-smoothing, Jacobi: coarse levels start from an explicit zero
 ]
 
 
