@@ -104,6 +104,13 @@ typedef struct {
                              explicit (5th-order WENO, local Lax-Friedrichs splitting), the
                              Laplacian implicit (periodic multigrid); FP64 V-cycles; `reaction`
                              is ignored. */
+    int    rb_run;        /* 3D red-black smoothing of the natural-layout levels (launch shape, not
+                             from the paper): 0 (default) lets the autotuner in isdc_create pick,
+                             per level, the points each thread updates along a diagonal run and how
+                             it issues them; 1, 2, 4, 8, 16 or 32: runs of that many points with
+                             the next point's loads issued before each store; -1, -2, -4 or -8:
+                             runs of that many points with all loads issued first.  Every choice
+                             gives the same result bit for bit. */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream
@@ -351,8 +358,8 @@ isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int
 /* Launch shape chosen by the context's autotuner (not from the paper): points
  * per thread of the fine-level red-black smoother in FP64 (the length of the
  * thread's diagonal run) and in FP32 (z-planes per thread of the split level);
- * 3D red-black contexts time 1, 2, 4 and 8 on their own arrays in isdc_create,
- * otherwise 1; for the FP32 fine level also the temporal-blocking depth
+ * 3D red-black contexts time 1 to 32 points (1 to 8 planes on the split level)
+ * on their own arrays in isdc_create, otherwise 1; for the FP32 fine level also the temporal-blocking depth
  * (red-black sweeps per pass, 0 = one pass per colour) and the z-planes per
  * block of the blocked pass.  Any output pointer may be NULL. */
 isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32, int *tb_depth, int *tb_planes);

@@ -134,7 +134,8 @@ struct isdc_ctx {
   int zb64 = 1, zb32 = 1;
   int tb_depth = 0, tb_zc = 32;  // temporal blocking of the split FP32 fine level (sweeps per pass, planes per block)
   float* sp_xb = nullptr;        // second black array of the split level (blocked passes ping-pong into it)
-  int zbl[kMaxLevels] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // per grid-wide level (natural layout)
+  // per grid-wide level (natural layout): run length, negative for burst runs (launch_rbgs)
+  int zbl[kMaxLevels] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   char err[512] = "";
 };
 
@@ -243,7 +244,7 @@ inline double nb_ops(int dim) { return dim == 2 ? 3.0 : 5.0; }
 // FP64/FP32 operations per updated point of a natural-layout red-black pass:
 // 3 additions + 1 FMA in 2D; in 3D 4 additions + 1 FMA per step of a diagonal
 // of zb points plus one addition for its first point (k_rbgs3).
-inline double rb_ops(int dim, int zb) { return dim == 2 ? 4.0 : 5.0 + 1.0 / zb; }
+inline double rb_ops(int dim, int zb) { return dim == 2 ? 4.0 : 5.0 + 1.0 / (zb < 0 ? -zb : zb); }
 
 // Row scaling of H = I - a L_h on a grid of side s: c = a/h^2, d = 1 + 2 dim c,
 // kappa = c / d.
@@ -1451,16 +1452,18 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
 }
 
 // Autotuner for the red-black smoothers (3D): on every grid-wide level with
-// side >= 31, time one red and one black pass with 1, 2, 4 and 8 points per
-// thread (diagonal runs, or z-planes on the split level) on the context's own
-// arrays of that level (zeroed first; the values
-// do not change the timing) and keep the fastest.  Runs once, in isdc_create.
+// side >= 31, time red and black passes with 1 to 32 points per thread along
+// a diagonal, streamed or in one burst (natural layout; 1, 2, 4 or 8 z-planes
+// on the split level) on the context's own arrays of that level (zeroed
+// first; the values do not change the timing) and keep the fastest.  Runs
+// once, in isdc_create.
 template <typename T>
 float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0, float* bs0, size_t hn,
-                     cudaEvent_t e0, cudaEvent_t e1, isdc_status* st) {
+                     cudaEvent_t e0, cudaEvent_t e1, isdc_status* st, int pairs) {
   *st = ISDC_OK;
   if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { *st = ISDC_ERR_CUDA; return 0.f; }
-  for (int colour = 0; colour < 2; ++colour) {
+  for (int c2 = 0; c2 < 2 * pairs; ++c2) {
+    const int colour = c2 & 1;
     if (xs0) {
       launch_rbgs_split<3>(ctx->stream, zb, s, 0.1f, colour, xs0 + colour * hn, xs0 + (1 - colour) * hn,
                            bs0 + colour * hn, false);
@@ -1477,13 +1480,21 @@ float time_rbgs_pass(isdc_ctx* ctx, int s, int zb, T* x, const T* b, float* xs0,
 
 template <typename T>
 isdc_status tune_levels(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cudaEvent_t e0, cudaEvent_t e1) {
-  const int cand[4] = {1, 2, 4, 8};
+  // natural layout: diagonal runs streamed (2..32 points) or in one burst
+  // (1..8, negative); split FP32 level: 1..8 z-planes
+  const int cand[9] = {-1, -2, -4, -8, 2, 4, 8, 16, 32};
+  const int split_cand[4] = {1, 2, 4, 8};
   for (int l = 0; l < H.lb; ++l) {
     const int s = H.side[l];
     if (s < 31) break;
     T* x = l == 0 ? x0 : H.x[l];
     T* b = l == 0 ? b0 : H.b[l];
     const bool split = l == 0 && split0;
+    if (!split && ctx->opt.rb_run != 0) {  // fixed by the caller
+      ctx->zbl[l] = ctx->opt.rb_run;
+      if (l == 0) (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) = ctx->opt.rb_run < 0 ? -ctx->opt.rb_run : ctx->opt.rb_run;
+      continue;
+    }
     if (split) {
       CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
       CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
@@ -1493,20 +1504,24 @@ isdc_status tune_levels(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cu
     }
     float best = 1e30f;
     int best_zb = 1;
-    for (int rep = 0; rep < 2; ++rep)  // the first round warms up
-      for (int c = 0; c < 4; ++c) {
+    // small levels take a few microseconds a pass: time 16 red-black pairs per
+    // trial there (2 above 1M points) and keep each form's best of two rounds
+    const int pairs = H.npts[l] >= (size_t(1) << 20) ? 2 : 16;
+    for (int rep = 0; rep < 3; ++rep)  // the first round warms up
+      for (int c = 0; c < (split ? 4 : 9); ++c) {
         isdc_status st;
-        const float ms = time_rbgs_pass<T>(ctx, s, cand[c], x, b, split ? ctx->sp_x : nullptr,
-                                           split ? ctx->sp_b : nullptr, ctx->hn, e0, e1, &st);
+        const int zb = split ? split_cand[c] : cand[c];
+        const float ms = time_rbgs_pass<T>(ctx, s, zb, x, b, split ? ctx->sp_x : nullptr,
+                                           split ? ctx->sp_b : nullptr, ctx->hn, e0, e1, &st, pairs);
         if (st != ISDC_OK) return st;
-        if (rep == 1 && ms < best) {
+        if (rep >= 1 && ms < best) {
           best = ms;
-          best_zb = cand[c];
+          best_zb = zb;
         }
       }
     if (split) ctx->zb32 = best_zb;
     else ctx->zbl[l] = best_zb;
-    if (l == 0 && !split) (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) = best_zb;
+    if (l == 0 && !split) (sizeof(T) == 8 ? ctx->zb64 : ctx->zb32) = best_zb < 0 ? -best_zb : best_zb;
   }
   return ISDC_OK;
 }
@@ -1580,6 +1595,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->vcycle_cap = 0;
   opt->use_graphs = 1;
   opt->temporal_blocking = -1;
+  opt->rb_run = 0;
   opt->stencil = 0;
   opt->equation = 0;
   opt->stream = nullptr;
@@ -1676,6 +1692,12 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps and mg_max_cycles must be >= 1");
   if (o.temporal_blocking < -1 || o.temporal_blocking > 2)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "temporal_blocking must be -1, 0, 1 or 2");
+  {
+    const int r = o.rb_run;
+    const bool ok = r == 0 || r == -1 || r == -2 || r == -4 || r == -8 || r == 1 || r == 2 || r == 4 || r == 8 ||
+                    r == 16 || r == 32;
+    if (!ok) return fail(nullptr, ISDC_ERR_INVALID_ARG, "rb_run must be 0, 1, 2, 4, 8, 16, 32, -1, -2, -4 or -8");
+  }
   if (o.stencil != 0 && o.stencil != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown stencil %d", o.stencil);
   if (o.stencil == 1 && (ndim != 2 || o.smoother != ISDC_SMOOTHER_JACOBI || o.vcycle_fp32 || o.equation != 0))
     return fail(nullptr, ISDC_ERR_UNSUPPORTED,

@@ -14,8 +14,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 namespace isdc {
 
 constexpr int kBX = 32;  // threads along x (one warp)
@@ -87,17 +85,64 @@ __global__ void __launch_bounds__(kBX* kBY)
   x[p] = zero_guess ? beta[p] : fma(kappa, nbsum<T, 2>(x, i, j, 0, n, p), beta[p]);
 }
 
-// 3D: each thread walks ZB points of the colour along the (0,1,1) diagonal at
-// a fixed i, p_t = (i, jd + t, k0 + t), t < ZB (the colour of a point does not
+// 3D: each thread walks zb points of the colour along the (0,1,1) diagonal at
+// a fixed i, p_t = (i, jd + t, k0 + t), t < zb (the colour of a point does not
 // change along that diagonal).  The neighbour sum is built from three pair
 // sums, X = x(i-1) + x(i+1), L = x(j-1) + x(k-1), U = x(j+1) + x(k+1), as
 // (X + L) + U.  U at p_t is the sum of the same two points as L at p_{t+1},
 // so a step loads 4 neighbours and issues 4 additions and one FMA where the
-// plain sum takes 6 and 6.  Addition is commutative in IEEE arithmetic, so a
-// point's value does not depend on ZB or on where its diagonal starts.
+// plain sum takes 6 and 6.  The next step's loads are issued before the
+// current store (they read the other colour).  Addition is commutative in
+// IEEE arithmetic, so a point's value does not depend on zb or on where its
+// diagonal starts.
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_rbgs3(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess, int zb) {
+  const int ih = blockIdx.x * kBX + threadIdx.x;
+  const int jd = int(blockIdx.y * kBY + threadIdx.y) - (zb - 1);
+  const int k0 = blockIdx.z * zb;
+  // (i+1)+(j+1)+(k+1) parity == colour, j + k = jd + k0 + 2t
+  const int i = 2 * ih + ((colour + jd + k0 + 1) & 1);
+  if (i >= n) return;
+  const int t0 = jd < 0 ? -jd : 0, t1 = min(zb, min(n - jd, n - k0));
+  if (t0 >= t1) return;
+  const int nn = n * n, step = n + nn;
+  int j = jd + t0, k = k0 + t0, p = i + n * j + nn * k;
+  if (zero_guess) {
+    for (int t = t0; t < t1; ++t, p += step) x[p] = beta[p];
+    return;
+  }
+  const bool xl = i > 0, xr = i < n - 1;
+  T lo = (j > 0 ? x[p - n] : T(0)) + (k > 0 ? x[p - nn] : T(0));
+  T xs = (xl ? x[p - 1] : T(0)) + (xr ? x[p + 1] : T(0));
+  T up = (j < n - 1 ? x[p + n] : T(0)) + (k < n - 1 ? x[p + nn] : T(0));
+  T bp = beta[p];
+  for (int t = t0; t < t1; ++t) {
+    T xs1 = T(0), up1 = T(0), bp1 = T(0);
+    if (t + 1 < t1) {
+      const int q = p + step;
+      xs1 = (xl ? x[q - 1] : T(0)) + (xr ? x[q + 1] : T(0));
+      up1 = (j + 1 < n - 1 ? x[q + n] : T(0)) + (k + 1 < n - 1 ? x[q + nn] : T(0));
+      bp1 = beta[q];
+    }
+    x[p] = fma(kappa, (xs + lo) + up, bp);
+    lo = up;
+    xs = xs1;
+    up = up1;
+    bp = bp1;
+    p += step;
+    ++j;
+    ++k;
+  }
+}
+
+// The same pass with the run length ZB fixed at compile time and all loads of
+// the run issued before its first store (more loads in flight per thread, at
+// more registers): the faster form where the pass is latency bound (small or
+// FP32 levels).
 template <typename T, int ZB>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_rbgs3(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+    k_rbgs3_burst(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
   const int ih = blockIdx.x * kBX + threadIdx.x;
   const int jd = int(blockIdx.y * kBY + threadIdx.y) - (ZB - 1);
   const int k0 = blockIdx.z * ZB;
@@ -131,26 +176,27 @@ __global__ void __launch_bounds__(kBX* kBY)
   }
 }
 
-// One colour pass of the natural-layout red-black smoother; zb in {1, 2, 4, 8}
-// is the 3D diagonal length (the context's autotuner picks it).
+// One colour pass of the natural-layout red-black smoother.  zb: the 3D run
+// length (the context's autotuner picks it); zb > 0 streams runs of zb points
+// (k_rbgs3), zb in {-1, -2, -4, -8} issues runs of -zb points in one burst
+// (k_rbgs3_burst).
 template <typename T, int DIM>
 inline void launch_rbgs(cudaStream_t st, int n, T kappa, int colour, T* x, const T* beta, bool zero_guess, int zb) {
   const dim3 blk(kBX, kBY, 1);
   const int gx = ((n + 1) / 2 + kBX - 1) / kBX;
+  const int zg = zero_guess ? 1 : 0;
   if (DIM == 2) {
-    k_rbgs2<T><<<dim3(gx, (n + kBY - 1) / kBY, 1), blk, 0, st>>>(n, kappa, colour, x, beta, zero_guess ? 1 : 0);
+    k_rbgs2<T><<<dim3(gx, (n + kBY - 1) / kBY, 1), blk, 0, st>>>(n, kappa, colour, x, beta, zg);
     return;
   }
-  auto go = [&](auto zbc) {
-    constexpr int ZB = decltype(zbc)::value;
-    const dim3 g(gx, (n + ZB - 1 + kBY - 1) / kBY, (n + ZB - 1) / ZB);
-    k_rbgs3<T, ZB><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zero_guess ? 1 : 0);
-  };
+  const int run = zb < 0 ? -zb : zb;
+  const dim3 g(gx, (n + run - 1 + kBY - 1) / kBY, (n + run - 1) / run);
   switch (zb) {
-    case 8: go(std::integral_constant<int, 8>()); break;
-    case 4: go(std::integral_constant<int, 4>()); break;
-    case 2: go(std::integral_constant<int, 2>()); break;
-    default: go(std::integral_constant<int, 1>()); break;
+    case -1: k_rbgs3_burst<T, 1><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zg); break;
+    case -2: k_rbgs3_burst<T, 2><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zg); break;
+    case -4: k_rbgs3_burst<T, 4><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zg); break;
+    case -8: k_rbgs3_burst<T, 8><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zg); break;
+    default: k_rbgs3<T><<<g, blk, 0, st>>>(n, kappa, colour, x, beta, zg, run); break;
   }
 }
 

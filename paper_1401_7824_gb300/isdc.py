@@ -44,7 +44,7 @@ class isdc_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_max_cycles", ctypes.c_int), ("vcycle_cap", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("temporal_blocking", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("equation", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("equation", ctypes.c_int), ("rb_run", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class isdc_kernel_stat(ctypes.Structure):
@@ -424,14 +424,14 @@ class Isdc:
                  omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
                  max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True,
                  temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stencil=ISDC_STENCIL_SECOND_ORDER,
-                 equation=ISDC_EQUATION_REACTION_DIFFUSION, stream=None):
+                 equation=ISDC_EQUATION_REACTION_DIFFUSION, rb_run=0, stream=None):
         import torch
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
         o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
         o.mg_tol, o.mg_max_cycles, o.vcycle_cap = mg_tol, mg_max_cycles, int(vcycle_cap)
         o.use_graphs, o.temporal_blocking, o.stencil = int(use_graphs), int(temporal_blocking), int(stencil)
-        o.equation = int(equation)
+        o.equation, o.rb_run = int(equation), int(rb_run)
         s = stream if stream is not None else torch.cuda.current_stream()
         # torch's default stream has handle 0, which the C ABI reads as "create a
         # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.

@@ -350,6 +350,44 @@ def test_temporal_blocking_is_bitwise_identical(nu12):
     assert rel_l2(outs[0][0], ref.per_step_u[0]) <= 1e-9
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_red_black_run_forms_are_bitwise_identical(fp32):
+    """The 3D red-black colour pass of the natural-layout levels walks diagonal
+    runs and shares pair sums between consecutive points; every run length and
+    both issue orders (streamed, or all loads first) form each point's sum as
+    (x-pair + lower pair) + upper pair, so whole steps agree bit for bit.  FP64
+    V-cycles on side 63 (levels 63, 31, 15 in the pass: ragged runs at the
+    grid's edges, several blocks along every axis; checked against the oracle
+    too) and FP32 V-cycles on side 127 (coarse levels 63 and 31 in the pass)."""
+    n = 127 if fp32 else 63
+    p = O.Problem(3, n, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2, max_sweeps=150)
+    u0 = initial_condition(3, n, seed=43)
+    outs = []
+    for run in (1, 2, 4, 8, 16, 32, -1, -2, -4, -8):
+        g = make_gpu(p, vcycle_fp32=fp32, rb_run=run)
+        if not fp32:
+            assert g.tuning()["zb_fp64"] == abs(run)
+        u = to_dev(u0)
+        assert g.step(u, 0, 2) == 0
+        outs.append((u.cpu().numpy(), g.stats(), g.residual()))
+        g.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        assert o[1] == outs[0][1] and o[2] == outs[0][2]
+    if not fp32:
+        ref = O.integrate(p, u0, 1, 0, 2)
+        assert rel_l2(outs[0][0], ref.per_step_u[0]) <= 1e-12
+
+
+def test_red_black_run_option_is_validated():
+    import paper_1401_7824_gb300 as G
+    p = O.Problem(3, 31, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2)
+    for bad in (3, -16, 64):
+        with pytest.raises(G.IsdcError) as e:
+            make_gpu(p, rb_run=bad)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG
+
+
 def test_temporal_blocking_option_is_validated_and_tuned():
     import paper_1401_7824_gb300 as G
     p = O.Problem(3, 63, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2)
