@@ -936,10 +936,10 @@ isdc_status sweep_end(isdc_ctx* ctx) {
 // (I - a L_h) x = b with periodic kernels, and the sweep with stored f^E.
 // ---------------------------------------------------------------------------
 // Algorithmic FP64 operations of the WENO5 advection per point and axis: one
-// face flux (u^2/2 and the split fluxes at 6 points: 36; two reconstructions
-// of 50 add/multiply/FMA/divide each) and the difference (the kernels compute
-// every face twice, once from each side).
-constexpr double kWenoOps = 139.0;
+// face flux (the split fluxes at 6 points: 25; two reconstructions of 42
+// add/multiply/FMA/divide each, one division among them; their sum) and the
+// scaled difference of the point's two faces (2).
+constexpr double kWenoOps = 112.0;
 
 inline LevelCoef coef_per(int dim, int s, double a) {
   const double h = 2.0 / s, c = a / (h * h), d = 1.0 + 2.0 * dim * c;

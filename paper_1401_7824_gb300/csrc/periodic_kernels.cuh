@@ -265,35 +265,46 @@ __global__ void __launch_bounds__(kBottomThreads)
 // WENO5 advection, FP64.
 // ---------------------------------------------------------------------------
 // Face value from the five upwind-biased values v0..v4 (v2, v3 beside the
-// face): three 3-point candidates, smoothness indicators, nonlinear weights
-// from the linear weights (1/10, 6/10, 3/10), epsilon = 1e-6.
+// face): three 3-point candidates q_k, smoothness indicators b_k, nonlinear
+// weights a_k = d_k / (eps + b_k)^2 from the linear weights d = (1/10, 6/10,
+// 3/10), eps = 1e-6, and the value sum a_k q_k / sum a_k.  Computed with one
+// division: multiplying every a_k by the product of the three (eps + b_j)^2
+// leaves d_k times the two other squares.  The candidates are kept as 6 q_k and
+// the indicators as 4 b_k (13/3 s^2 + t^2 instead of 13/12 s^2 + 1/4 t^2, with
+// 4 eps); the factor 4 cancels in the ratio and the 6 is divided out at the end.
 __device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4) {
-  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
-  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
-  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
-  const double s0 = v0 - 2.0 * v1 + v2, t0 = v0 - 4.0 * v1 + 3.0 * v2;
-  const double s1 = v1 - 2.0 * v2 + v3, t1 = v1 - v3;
-  const double s2 = v2 - 2.0 * v3 + v4, t2 = 3.0 * v2 - 4.0 * v3 + v4;
-  const double b0 = (13.0 / 12.0) * s0 * s0 + 0.25 * t0 * t0;
-  const double b1 = (13.0 / 12.0) * s1 * s1 + 0.25 * t1 * t1;
-  const double b2 = (13.0 / 12.0) * s2 * s2 + 0.25 * t2 * t2;
-  const double e0 = 1e-6 + b0, e1 = 1e-6 + b1, e2 = 1e-6 + b2;
-  const double a0 = 0.1 / (e0 * e0), a1 = 0.6 / (e1 * e1), a2 = 0.3 / (e2 * e2);
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  const double q0 = fma(2.0, v0, fma(-7.0, v1, 11.0 * v2));
+  const double q1 = fma(5.0, v2, fma(2.0, v3, -v1));
+  const double q2 = fma(2.0, v2, fma(5.0, v3, -v4));
+  const double s0 = fma(-2.0, v1, v0 + v2), t0 = fma(-4.0, v1, fma(3.0, v2, v0));
+  const double s1 = fma(-2.0, v2, v1 + v3), t1 = v1 - v3;
+  const double s2 = fma(-2.0, v3, v2 + v4), t2 = fma(3.0, v2, fma(-4.0, v3, v4));
+  constexpr double c = 13.0 / 3.0, e4 = 4e-6;
+  const double e0 = fma(c * s0, s0, fma(t0, t0, e4));
+  const double e1 = fma(c * s1, s1, fma(t1, t1, e4));
+  const double e2 = fma(c * s2, s2, fma(t2, t2, e4));
+  const double E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+  const double w0 = E1 * E2, w1 = 6.0 * (E0 * E2), w2 = 3.0 * (E0 * E1);
+  return fma(w0, q0, fma(w1, q1, w2 * q2)) / (6.0 * ((w0 + w1) + w2));
 }
 
 // Numerical flux of u^2/2 at the face between w[2] and w[3] from the six
-// values w[0..5] along the axis (local Lax-Friedrichs splitting).
+// values w[0..5] along the axis (local Lax-Friedrichs splitting with alpha =
+// max |w|, taken on the integer pipe: with the sign bit cleared, doubles order
+// like their bit patterns).  f(+/-) = (w^2/2 +/- alpha w)/2 = w (w/4 +/- alpha/2).
 __device__ __forceinline__ double weno_flux(const double (&w)[6]) {
-  double alpha = 0.0;
+  unsigned long long ab = 0;
 #pragma unroll
-  for (int t = 0; t < 6; ++t) alpha = fmax(alpha, fabs(w[t]));
+  for (int t = 0; t < 6; ++t) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(w[t]) & 0x7fffffffffffffffull;
+    ab = bits > ab ? bits : ab;
+  }
+  const double half_alpha = 0.5 * __longlong_as_double((long long)ab);
   double fp[6], fm[6];
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
-    const double f = 0.5 * w[t] * w[t];
-    fp[t] = 0.5 * (f + alpha * w[t]);
-    fm[t] = 0.5 * (f - alpha * w[t]);
+    fp[t] = w[t] * fma(0.25, w[t], half_alpha);
+    fm[t] = w[t] * fma(0.25, w[t], -half_alpha);
   }
   return weno5(fp[0], fp[1], fp[2], fp[3], fp[4]) + weno5(fm[5], fm[4], fm[3], fm[2], fm[1]);
 }
