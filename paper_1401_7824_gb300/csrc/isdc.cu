@@ -101,7 +101,7 @@ struct isdc_ctx {
   double* G = nullptr;  // compact: nu L_9 u per point (P arrays); F holds f~ = W f^E + nu L_9 u
   double* Rs = nullptr; // compact: W-weighted SDC residuals and two Jacobi iterates, 3 (P-1) arrays
   int equation = 0;     // 0: reaction-diffusion, Dirichlet; 1: viscous Burgers, periodic (h = 2/n)
-  double* FE = nullptr; // Burgers: f^E(u_p) = WENO5 advection per point (P arrays)
+  double* FE = nullptr; // f^E(u_p) per point (P arrays; Burgers: the WENO5 advection); not for the compact stencil
   double* b = nullptr;  // right-hand side of the current node solve
   double* u_dev = nullptr;  // device copy of u for isdc_step_host
   Hier<double> h64;
@@ -888,7 +888,8 @@ inline double bits_to_double(unsigned long long b) {
 template <int DIM, int OFF, int P>
 void launch_sweep_end_p(isdc_ctx* ctx, double nu_h2) {
   k_sweep_end<DIM, OFF, P><<<pt_grid(DIM, ctx->n), kBlock, 0, ctx->stream>>>(
-      ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->C, ctx->d_scal);
+      ctx->n, ctx->N, nu_h2, ctx->opt.reaction, ctx->cprime, ctx->tables, ctx->U, ctx->F, ctx->FE, ctx->C,
+      ctx->d_scal);
 }
 
 template <int DIM>
@@ -920,11 +921,11 @@ isdc_status sweep_end(isdc_ctx* ctx) {
   const double nu_h2 = ctx->nu / (ctx->h * ctx->h);
   {
     const double M = ctx->M, P = ctx->P, Np = double(ctx->N);
-    // reads P u, M-1 f; writes f_{P-1} and P-1 C.  Ops: f_{P-1}: nb+2; f^E: 2P;
-    // dt Q f: (P-1)M; residual: 2(P-1); C: 4(P-1) - 1 (C': 3(P-1) - 1)
-    ProfScope ps(ctx, PC_SWEEP_END, (2.0 * P + M - 1.0) * 8.0 * Np,
-                 (nb_ops(DIM) + 2.0 + 2.0 * P + (P - 1.0) * M + (ctx->cprime ? 5.0 : 6.0) * (P - 1.0) - 1.0) * Np,
-                 true);
+    // reads P u, M-1 f, P-1 f^E; writes f_{P-1} and P-1 C.  Ops: f_{P-1}: nb+2;
+    // f^E of the last point: 2; dt Q f: (P-1)M; residual: 2(P-1); C: 4(P-1) - 1
+    // (C': 3(P-1) - 1)
+    ProfScope ps(ctx, PC_SWEEP_END, (3.0 * P + M - 2.0) * 8.0 * Np,
+                 (nb_ops(DIM) + 4.0 + (P - 1.0) * M + (ctx->cprime ? 5.0 : 6.0) * (P - 1.0) - 1.0) * Np, true);
     launch_sweep_end<DIM>(ctx, nu_h2);
   }
   LAUNCH_CHECK(ctx);
@@ -1206,16 +1207,17 @@ isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
     const double a = dtm * ctx->nu;
     if (ctx->cprime) {  // FP32 V-cycles, fixed count: rhs and defect in one pass
       {
-        ProfScope ps(ctx, PC_RHS, (m >= 1 ? 28.0 : 20.0) * double(N), (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N),
+        ProfScope ps(ctx, PC_RHS, (m >= 1 ? 36.0 : 20.0) * double(N), (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N),
                      true);
         double* Fm = m >= 1 ? ctx->F + m * N : nullptr;
+        double* FEm = ctx->FE + m * N;
         if (ctx->sp_x)
           k_rhs_defect_split<DIM><<<rb_grid(DIM, n), kBlock, 0, ctx->stream>>>(
-              n, nu_h2, ctx->opt.reaction, dtm, inv_d0, ctx->U + m * N, ctx->C + m * N, Fm, ctx->sp_b,
+              n, nu_h2, ctx->opt.reaction, dtm, inv_d0, ctx->U + m * N, ctx->C + m * N, Fm, FEm, ctx->sp_b,
               ctx->sp_b + ctx->hn);
         else
           k_rhs_defect<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
-                                                                         ctx->U + m * N, ctx->C + m * N, Fm,
+                                                                         ctx->U + m * N, ctx->C + m * N, Fm, FEm,
                                                                          ctx->h32.b[0]);
       }
       LAUNCH_CHECK(ctx);
@@ -1224,12 +1226,11 @@ isdc_status sweep_once(isdc_ctx* ctx, int n_vcycles, long long* vcycles) {
       continue;
     }
     {
-      ProfScope ps(ctx, PC_RHS, (m >= 1 ? 4.0 : 3.0) * 8.0 * double(N),
+      ProfScope ps(ctx, PC_RHS, (m >= 1 ? 5.0 : 3.0) * 8.0 * double(N),
                    (m >= 1 ? nb_ops(DIM) + 7.0 : 5.0) * double(N), true);
       k_rhs<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, dtm, inv_d0,
-                                                              ctx->U + m * N,
-                                                              ctx->C + m * N, ctx->b,
-                                                              m >= 1 ? ctx->F + m * N : nullptr);
+                                                              ctx->U + m * N, ctx->C + m * N, ctx->b,
+                                                              m >= 1 ? ctx->F + m * N : nullptr, ctx->FE + m * N);
     }
     LAUNCH_CHECK(ctx);
     if (n_vcycles > 0 && !ctx->opt.vcycle_cap) {
@@ -1353,20 +1354,20 @@ isdc_status run_step(isdc_ctx* ctx, double* u, int n_sweeps, int n_vcycles) {
     // resume: the nodes were set; t_0 (not a node unless Gauss-Lobatto) is u
     if (ctx->off)
       CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U, u, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    for (int m = ctx->off; m < P; ++m) {
+    for (int m = 0; m < P; ++m) {  // f^E of t_0 too (the first C needs it)
       {
-        ProfScope ps(ctx, PC_EVAL_F, 16.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
+        ProfScope ps(ctx, PC_EVAL_F, 24.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
         k_eval_f<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, nu_h2, ctx->opt.reaction, ctx->U + m * N,
-                                                                   ctx->F + m * N);
+                                                                   ctx->F + m * N, ctx->FE + m * N);
       }
       LAUNCH_CHECK(ctx);
     }
     ctx->nodes_pending = 0;
   } else {
     {
-      ProfScope ps(ctx, PC_SPREAD, (1.0 + 2.0 * P) * 8.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
+      ProfScope ps(ctx, PC_SPREAD, (1.0 + 3.0 * P) * 8.0 * double(N), (nb_ops(DIM) + 5.0) * double(N), true);
       k_spread<DIM><<<pt_grid(DIM, n), kBlock, 0, ctx->stream>>>(n, N, nu_h2, ctx->opt.reaction, P, u, ctx->U,
-                                                                 ctx->F);
+                                                                 ctx->F, ctx->FE);
     }
     LAUNCH_CHECK(ctx);
   }
@@ -1763,7 +1764,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   CREATE_TRY(cudaMalloc(&ctx->U, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->F, size_t(P) * N * sizeof(double)));
   CREATE_TRY(cudaMalloc(&ctx->C, size_t(P - 1) * N * sizeof(double)));
-  if (ctx->equation == 1) CREATE_TRY(cudaMalloc(&ctx->FE, size_t(P) * N * sizeof(double)));
+  if (ctx->stencil != 1) CREATE_TRY(cudaMalloc(&ctx->FE, size_t(P) * N * sizeof(double)));
   if (ctx->stencil == 1) {
     CREATE_TRY(cudaMalloc(&ctx->G, size_t(P) * N * sizeof(double)));
     CREATE_TRY(cudaMalloc(&ctx->Rs, 3 * size_t(P - 1) * N * sizeof(double)));

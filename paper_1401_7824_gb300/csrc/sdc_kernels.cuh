@@ -20,35 +20,40 @@ struct SweepTables {
   double dtm[kMaxP];          // dt_m = t_{m+1} - t_m between consecutive points
 };
 
-// Start of a step: every node u_m = u, f_m = f^E(u) + nu L_h u.
+// Start of a step: every point u_m = u, f_m = f^E(u) + nu L_h u, and the
+// explicit part fe_m = f^E(u) (stored so that the sweep end need not
+// re-evaluate it).
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_spread(int n, size_t N, double nu_h2, int reaction, int M, const double* __restrict__ u,
-             double* __restrict__ U, double* __restrict__ F) {
+             double* __restrict__ U, double* __restrict__ F, double* __restrict__ FE) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
   const double up = u[p];
-  const double f = reaction_term(reaction, up) +
-                   nu_h2 * (nbsum<double, DIM>(u, i, j, k, n, p) - double(2 * DIM) * up);
+  const double fe = reaction_term(reaction, up);
+  const double f = fe + nu_h2 * (nbsum<double, DIM>(u, i, j, k, n, p) - double(2 * DIM) * up);
   for (int m = 0; m < M; ++m) {
     U[m * N + p] = up;
     F[m * N + p] = f;
+    FE[m * N + p] = fe;
   }
 }
 
-// f_m = f(u_m) for one node (resume from given node values).
+// f_m = f(u_m) and fe_m = f^E(u_m) for one point (resume from given node values).
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
-    k_eval_f(int n, double nu_h2, int reaction, const double* __restrict__ u, double* __restrict__ f) {
+    k_eval_f(int n, double nu_h2, int reaction, const double* __restrict__ u, double* __restrict__ f,
+             double* __restrict__ fe_out) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
   const double up = u[p];
-  f[p] = reaction_term(reaction, up) +
-         nu_h2 * (nbsum<double, DIM>(u, i, j, k, n, p) - double(2 * DIM) * up);
+  const double fe = reaction_term(reaction, up);
+  fe_out[p] = fe;
+  f[p] = fe + nu_h2 * (nbsum<double, DIM>(u, i, j, k, n, p) - double(2 * DIM) * up);
 }
 
 // Right-hand side of node m's implicit Euler system (Eq. 4, implicit unknown
@@ -56,11 +61,13 @@ __global__ void __launch_bounds__(kBX* kBY)
 //   b = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C_m,
 //   C_m = dt sum_j s_{m,j} f(u_j^k) - dt_m f^E(u_m^k) - dt_m f^I(u_{m+1}^k)
 // (C_m comes from the end of the previous sweep).  For m >= 1 the same pass
-// stores f_m = f(u_m^{k+1}), which the residual and the next sweep need.
+// stores f_m = f(u_m^{k+1}) and fe_m = f^E(u_m^{k+1}), which the residual, the
+// sweep end and the next sweep need.
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rhs(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
-          const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm) {
+          const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm,
+          double* __restrict__ FEm) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -68,7 +75,10 @@ __global__ void __launch_bounds__(kBX* kBY)
   const double up = Um[p];
   const double fe = reaction_term(reaction, up);
   beta[p] = (fma(dtm, fe, up) + Cm[p]) * inv_d;
-  if (Fm) Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
+  if (Fm) {
+    Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
+    FEm[p] = fe;
+  }
 }
 
 // Mixed precision with a fixed V-cycle count: the defect of node m's system at
@@ -79,26 +89,31 @@ __global__ void __launch_bounds__(kBX* kBY)
 // dt_m f^I(u_{m+1}^k)), so
 //   r = b - (I - a L_h) u_{m+1}^k = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C'_m
 // needs no stencil of u_{m+1}^k.  r / d is computed in FP64 and stored in FP32;
-// for m >= 1 the same pass stores f_m = f(u_m^{k+1}).
+// for m >= 1 the same pass stores f_m = f(u_m^{k+1}) and fe_m = f^E(u_m^{k+1}).
 template <int DIM>
 __device__ __forceinline__ float rhs_defect_point(int i, int j, int k, int n, int p, double nu_h2, int reaction,
                                                   double dtm, double inv_d, const double* __restrict__ Um,
-                                                  const double* __restrict__ Cm, double* __restrict__ Fm) {
+                                                  const double* __restrict__ Cm, double* __restrict__ Fm,
+                                                  double* __restrict__ FEm) {
   const double up = Um[p];
   const double fe = reaction_term(reaction, up);
-  if (Fm) Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
+  if (Fm) {
+    Fm[p] = fe + nu_h2 * (nbsum<double, DIM>(Um, i, j, k, n, p) - double(2 * DIM) * up);
+    FEm[p] = fe;
+  }
   return float((fma(dtm, fe, up) + Cm[p]) * inv_d);
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rhs_defect(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
-                 const double* __restrict__ Cm, double* __restrict__ Fm, float* __restrict__ r32) {
+                 const double* __restrict__ Cm, double* __restrict__ Fm, double* __restrict__ FEm,
+                 float* __restrict__ r32) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = lin<DIM>(i, j, k, n);
-  r32[p] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+  r32[p] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm, FEm);
 }
 
 // The same into the colour-split FP32 arrays: one thread per slot pair (points
@@ -106,8 +121,8 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rhs_defect_split(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
-                       const double* __restrict__ Cm, double* __restrict__ Fm, float* __restrict__ r0,
-                       float* __restrict__ r1) {
+                       const double* __restrict__ Cm, double* __restrict__ Fm, double* __restrict__ FEm,
+                       float* __restrict__ r0, float* __restrict__ r1) {
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
@@ -116,9 +131,10 @@ __global__ void __launch_bounds__(kBX* kBY)
   const size_t slot = size_t(h) + size_t(H) * split_row<DIM>(j, k, n);
   const int i = 2 * h;
   const int p = lin<DIM>(i, j, k, n);
-  (c0 ? r1 : r0)[slot] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+  (c0 ? r1 : r0)[slot] = rhs_defect_point<DIM>(i, j, k, n, p, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm, FEm);
   if (i + 1 < n)
-    (c0 ? r0 : r1)[slot] = rhs_defect_point<DIM>(i + 1, j, k, n, p + 1, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm);
+    (c0 ? r0 : r1)[slot] =
+        rhs_defect_point<DIM>(i + 1, j, k, n, p + 1, nu_h2, reaction, dtm, inv_d, Um, Cm, Fm, FEm);
 }
 
 __device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned long long* out) {
@@ -151,8 +167,8 @@ __device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned 
 template <int DIM, int OFF, int P>
 __global__ void __launch_bounds__(kBX* kBY)
     k_sweep_end(int n, size_t N, double nu_h2, int reaction, int cmode, SweepTables tb,
-                const double* __restrict__ U, double* __restrict__ F, double* __restrict__ C,
-                unsigned long long* __restrict__ Rbits) {
+                const double* __restrict__ U, double* __restrict__ F, const double* __restrict__ FE,
+                double* __restrict__ C, unsigned long long* __restrict__ Rbits) {
   constexpr int M = P - OFF;  // nodes; node j is point j + OFF
   static_assert(M >= 2 && M <= kMaxM && P <= kMaxP, "point count out of range");
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
@@ -162,10 +178,11 @@ __global__ void __launch_bounds__(kBX* kBY)
     const int p = lin<DIM>(i, j, k, n);
     double u[P], f[P], fe[P], qf[P];
 #pragma unroll
-    for (int m = 0; m < P; ++m) {
-      u[m] = U[m * N + p];
-      fe[m] = reaction_term(reaction, u[m]);
-    }
+    for (int m = 0; m < P; ++m) u[m] = U[m * N + p];
+    // f^E of the points before the last was stored with their f (spread, right-hand sides)
+#pragma unroll
+    for (int m = 0; m < P - 1; ++m) fe[m] = FE[m * N + p];
+    fe[P - 1] = reaction_term(reaction, u[P - 1]);
     // f at the last point from its stencil; the other nodes' f were stored during the sweep
     const double* ul = U + (size_t)(P - 1) * N;
     const double ulast = u[P - 1];
