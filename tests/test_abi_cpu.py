@@ -76,6 +76,20 @@ def test_host_validation_without_gpu():
         assert "must" in G.isdc_last_error()
     o = G.isdc_default_options()
     assert (o.smoother, o.nu1, o.nu2, o.max_sweeps, o.tol) == (0, 1, 1, 100, 1e-10)
+    assert (o.temporal_blocking, o.rb_run, o.stencil, o.equation) == (-1, 0, 0, 0)
+    # option values outside their sets are refused before any device work
+    for field, bad in [("rb_run", 3), ("rb_run", -16), ("rb_run", 64), ("temporal_blocking", 3),
+                       ("smoother", 2), ("nu1", 17), ("stencil", 2), ("reaction", 5), ("max_sweeps", 0)]:
+        o = G.isdc_default_options()
+        setattr(o, field, bad)
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_create(3, 31, 0.1, 3, 0.05, o)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG, field
+    o = G.isdc_default_options()
+    o.equation = 1
+    with pytest.raises(G.IsdcError) as e:
+        G.isdc_create(2, 31, 0.1, 3, 0.05, o)  # periodic sides are 2^j
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("struct", ["isdc_options", "isdc_problem", "isdc_slot_info", "isdc_batch_info",
