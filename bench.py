@@ -231,7 +231,8 @@ def combine_ranks(times, work, world, device):
 
 def config_of(w):
     N = w.n ** w.ndim
-    state_bytes = (3 * w.M + 2) * N * 8
+    P = w.M if w.nodes == 0 else w.M + 1  # points of a sweep: t_0 and the nodes
+    state_bytes = 4 * P * N * 8  # U, F, f^E (P arrays each), C (P - 1), beta (1), FP64
     return {"workload": w.name, "ndim": w.ndim, "n": w.n, "dofs": N, "M": w.M,
             "nodes": ["gauss-lobatto", "gauss-radau-right", "gauss-legendre"][w.nodes],
             "equation": "viscous Burgers, periodic, WENO5 advection" if w.equation == 1
