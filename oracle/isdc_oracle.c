@@ -944,7 +944,7 @@ void orc_solve_exact9(int n, double a, const double *b, double *x)
 {
     long N = npoints(2, n);
     double h = 1.0 / (n + 1);
-    double *T = (double *)malloc(sizeof(double) * n * n);
+    double *T = (double *)calloc((size_t)n * n, sizeof(double));
     for (int p = 1; p <= n; ++p)
         for (int i = 1; i <= n; ++i)
             T[(p - 1) * n + (i - 1)] = sin(M_PI * (double)i * (double)p / (n + 1));
