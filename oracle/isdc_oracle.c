@@ -45,6 +45,13 @@
  * per level (V-cycle), zero coarse initial guess, exact dense solve on the
  * side-3 grid, and either damped Jacobi or red-black Gauss-Seidel smoothing.
  *
+ * Threads: built once plainly (the pragmas below are ignored) and once with
+ * -fopenmp for the all-core variant.  Only the outermost grid loops of the
+ * stencil, transfer, solve and pointwise steps carry a pragma (each iteration
+ * writes its own points; a red-black colour reads only the other colour), and
+ * the max-norms combine per-thread maxima (max is exact in any order), so both
+ * builds give the same results bit for bit.
+ *
  * Grid layout: interior points only, x fastest.  With 1-based interior
  * indices i,j,k in 1..n the array index is (i-1) + n*((j-1) + n*(k-1)).
  * h = 1/(n+1).  Everything is IEEE double, built with -ffp-contract=off.
@@ -52,6 +59,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_M 16
 
@@ -313,7 +323,9 @@ static double laplacian_at(const double *u, int d, int n, int i, int j, int k)
 /* out = L_h u (5-point in 2D, 7-point in 3D). */
 void orc_laplacian(int d, int n, const double *u, double *out)
 {
-    for (int k = 1; k <= kmax(d, n); ++k)
+    const int km = kmax(d, n);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k <= km; ++k)
         for (int j = 1; j <= n; ++j)
             for (int i = 1; i <= n; ++i)
                 out[idx(d, n, i, j, k)] = laplacian_at(u, d, n, i, j, k);
@@ -322,7 +334,9 @@ void orc_laplacian(int d, int n, const double *u, double *out)
 /* r = b - (I - a L_h) x */
 void orc_residual(int d, int n, double a, const double *x, const double *b, double *r)
 {
-    for (int k = 1; k <= kmax(d, n); ++k)
+    const int km = kmax(d, n);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k <= km; ++k)
         for (int j = 1; j <= n; ++j)
             for (int i = 1; i <= n; ++i) {
                 long p = idx(d, n, i, j, k);
@@ -334,11 +348,45 @@ void orc_residual(int d, int n, double a, const double *x, const double *b, doub
 static double max_abs(const double *v, long N)
 {
     double m = 0.0;
-    for (long p = 0; p < N; ++p) {
-        double a = fabs(v[p]);
-        if (a > m || a != a) m = a; /* a NaN propagates */
+#pragma omp parallel
+    {
+        double mt = 0.0;
+#pragma omp for schedule(static) nowait
+        for (long p = 0; p < N; ++p) {
+            double a = fabs(v[p]);
+            if (a > mt || a != a) mt = a; /* a NaN propagates */
+        }
+#pragma omp critical
+        if (mt > m || mt != mt) m = mt;
     }
     return m;
+}
+
+/* Plain copy of N values (the threaded build splits it over the cores). */
+static void copy_values(double *dst, const double *src, long N)
+{
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < N; ++p) dst[p] = src[p];
+}
+
+/* Threads for the loops of the threaded build (no effect in the plain build). */
+void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* Number of threads the oracle's loops use (1 in the plain build). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */
@@ -355,8 +403,10 @@ void orc_smooth_jacobi(int d, int n, double a, double omega, double *x, const do
 {
     double h = 1.0 / (n + 1);
     double diag = 1.0 + 2.0 * d * a / (h * h);
-    memcpy(old, x, sizeof(double) * npoints(d, n));
-    for (int k = 1; k <= kmax(d, n); ++k)
+    copy_values(old, x, npoints(d, n));
+    const int km = kmax(d, n);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k <= km; ++k)
         for (int j = 1; j <= n; ++j)
             for (int i = 1; i <= n; ++i) {
                 long p = idx(d, n, i, j, k);
@@ -375,8 +425,10 @@ void orc_smooth_rbgs(int d, int n, double a, double *x, const double *b)
 {
     double h = 1.0 / (n + 1);
     double diag = 1.0 + 2.0 * d * a / (h * h);
+    const int km = kmax(d, n);
     for (int colour = 0; colour < 2; ++colour)
-        for (int k = 1; k <= kmax(d, n); ++k)
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 1; k <= km; ++k)
             for (int j = 1; j <= n; ++j)
                 for (int i = 1; i <= n; ++i) {
                     int parity = (d == 3) ? (i + j + k) % 2 : (i + j) % 2;
@@ -403,7 +455,9 @@ static double hat(int i, int I)
 void orc_restrict_fw(int d, int n, const double *r, double *rc)
 {
     int nc = (n - 1) / 2;
-    for (int K = 1; K <= kmax(d, nc); ++K)
+    const int Km = kmax(d, nc);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int K = 1; K <= Km; ++K)
         for (int J = 1; J <= nc; ++J)
             for (int I = 1; I <= nc; ++I) {
                 double acc = 0.0;
@@ -428,7 +482,9 @@ void orc_restrict_fw(int d, int n, const double *r, double *rc)
 void orc_prolong_add(int d, int nc, const double *ec, double *x)
 {
     int n = 2 * nc + 1;
-    for (int k = 1; k <= kmax(d, n); ++k)
+    const int km = kmax(d, n);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k <= km; ++k)
         for (int j = 1; j <= n; ++j)
             for (int i = 1; i <= n; ++i) {
                 double acc = 0.0;
@@ -888,17 +944,21 @@ static void sine_along_axis(int d, int n, int axis, double *u, const double *T)
     long N = npoints(d, n);
     long st = 1;
     for (int a = 0; a < axis; ++a) st *= n;
-    double *line = (double *)malloc(sizeof(double) * n);
-    for (long base = 0; base < N; ++base) {
-        if ((base / st) % n != 0) continue; /* first point of each line */
-        for (int p = 0; p < n; ++p) {
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) acc += T[p * n + i] * u[base + i * st];
-            line[p] = acc;
+#pragma omp parallel
+    {
+        double *line = (double *)malloc(sizeof(double) * n);
+#pragma omp for schedule(static)
+        for (long base = 0; base < N; ++base) {
+            if ((base / st) % n != 0) continue; /* first point of each line */
+            for (int p = 0; p < n; ++p) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += T[p * n + i] * u[base + i * st];
+                line[p] = acc;
+            }
+            for (int p = 0; p < n; ++p) u[base + p * st] = line[p];
         }
-        for (int p = 0; p < n; ++p) u[base + p * st] = line[p];
+        free(line);
     }
-    free(line);
 }
 
 /*
@@ -923,7 +983,9 @@ void orc_solve_exact(int d, int n, double a, const double *b, double *x)
         lam1[p - 1] = -4.0 * s * s / (h * h);
     }
     double scale = pow(2.0 / (n + 1), d);
-    for (int k = 1; k <= kmax(d, n); ++k)
+    const int km = kmax(d, n);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k <= km; ++k)
         for (int j = 1; j <= n; ++j)
             for (int i = 1; i <= n; ++i) {
                 double lam = lam1[i - 1] + lam1[j - 1] + (d == 3 ? lam1[k - 1] : 0.0);
@@ -984,6 +1046,7 @@ static void eval_f(const orc_problem *P, const double *u, double *fE, double *fI
     }
     if (P->stencil == 1) orc_laplacian9(P->n, u, fI);
     else orc_laplacian(P->ndim, P->n, u, fI);
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < N; ++p) {
         fI[p] *= P->nu;
         fE[p] = f_explicit(P, u[p]);
@@ -1073,9 +1136,9 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
     int cap = n_sweeps > 0 ? n_sweeps : P->max_sweeps;
     for (;;) {
         /* keep u^k and F(u^k) for the whole sweep */
-        memcpy(Uold, U, sizeof(double) * NP * N);
-        memcpy(FEold, FE, sizeof(double) * NP * N);
-        memcpy(FIold, FI, sizeof(double) * NP * N);
+        copy_values(Uold, U, NP * N);
+        copy_values(FEold, FE, NP * N);
+        copy_values(FIold, FI, NP * N);
 
         /* point 0 is t_0: u_0^{k+1} = u_0, nothing to solve */
         for (int m = 0; m < NP - 1; ++m) {
@@ -1083,14 +1146,17 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
             double a = dtm * P->nu; /* (I - dt_m A) with A = nu L_h */
             const double *Um_new = U + m * N;
             if (P->equation == 1) orc_burgers_advection(d, n, Um_new, fe_new);
-            else
+            else {
+#pragma omp parallel for schedule(static)
                 for (long p = 0; p < N; ++p) fe_new[p] = f_explicit(P, Um_new[p]);
+            }
             /* Eq. 4 with the implicit unknown moved left:
              * (I - dt_m A) u_{m+1}^{k+1} = u_m^{k+1}
              *     + dt_m [f^E(u_m^{k+1}) - f^E(u_m^k)] - dt_m f^I(u_{m+1}^k)
              *     + S_m^{m+1} F(u^k),   S_m^{m+1}F = dt sum_j s_{m,j} f(u_j^k)
              * (the sum runs over the nodes j, which are points j + off) */
             if (!W9) {
+#pragma omp parallel for schedule(static)
                 for (long p = 0; p < N; ++p) {
                     double sf = 0.0;
                     for (int j = 0; j < M; ++j)
@@ -1114,7 +1180,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
                 }
             }
             /* initial guess for the spatial solver (Sec. 4.3) */
-            if (P->guess == 0) memcpy(x, Uold + (m + 1) * N, sizeof(double) * N);
+            if (P->guess == 0) copy_values(x, Uold + (m + 1) * N, N);
             else if (P->guess == 1) memset(x, 0, sizeof(double) * N);
             else memcpy(x, Um_new, sizeof(double) * N);
 
@@ -1142,7 +1208,7 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
                     ++vcycles;
                 }
             }
-            memcpy(U + (m + 1) * N, x, sizeof(double) * N);
+            copy_values(U + (m + 1) * N, x, N);
         }
         ++k;
 
@@ -1152,12 +1218,19 @@ int orc_isdc_step(const orc_problem *P, double *u, int n_sweeps, int n_vcycles,
         double R = 0.0;
         for (int m = 0; m < M; ++m) {
             if (!W9) {
-                for (long p = 0; p < N; ++p) {
-                    double qf = 0.0;
-                    for (int j = 0; j < M; ++j)
-                        qf += Q[m * M + j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
-                    double r = fabs(u0[p] + P->dt * qf - U[(m + off) * N + p]);
-                    if (r > R || r != r) R = r;
+#pragma omp parallel
+                {
+                    double Rt = 0.0;
+#pragma omp for schedule(static) nowait
+                    for (long p = 0; p < N; ++p) {
+                        double qf = 0.0;
+                        for (int j = 0; j < M; ++j)
+                            qf += Q[m * M + j] * (FE[(j + off) * N + p] + FI[(j + off) * N + p]);
+                        double r = fabs(u0[p] + P->dt * qf - U[(m + off) * N + p]);
+                        if (r > Rt || r != r) Rt = r;
+                    }
+#pragma omp critical
+                    if (Rt > R || Rt != Rt) R = Rt;
                 }
             } else {
                 /* W r_m = W (u_0 - u_m + dt sum_j q_{m,j} f^E_j) + dt sum_j q_{m,j} A u_j:
@@ -1246,11 +1319,18 @@ double orc_sdc_residual(const orc_problem *P, const double *u0, const double *U)
     double R = 0.0;
     for (int m = 0; m < M; ++m) {
         if (P->stencil != 1) {
-            for (long p = 0; p < N; ++p) {
-                double qf = 0.0;
-                for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
-                double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
-                if (r > R || r != r) R = r;
+#pragma omp parallel
+            {
+                double Rt = 0.0;
+#pragma omp for schedule(static) nowait
+                for (long p = 0; p < N; ++p) {
+                    double qf = 0.0;
+                    for (int j = 0; j < M; ++j) qf += Q[m * M + j] * (FE[j * N + p] + FI[j * N + p]);
+                    double r = fabs(u0[p] + P->dt * qf - U[m * N + p]);
+                    if (r > Rt || r != r) Rt = r;
+                }
+#pragma omp critical
+                if (Rt > R || Rt != Rt) R = Rt;
             }
         } else { /* compact stencil: r_m = W^{-1} [W (u_0 - u_m + dt Q f^E) + dt Q A u] */
             for (long p = 0; p < N; ++p) {

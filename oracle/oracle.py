@@ -21,7 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "isdc_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libisdc_oracle.so")
-_lib = None
+_OMP_PATH = os.path.join(_BUILD, "libisdc_oracle_omp.so")
+_libs = {}
+_all_cores = False
 
 SMOOTHER_JACOBI = 0
 SMOOTHER_RBGS = 1
@@ -44,15 +46,50 @@ EQUATION_REACTION_DIFFUSION = 0  # unit square / cube, zero Dirichlet values, n 
 EQUATION_BURGERS = 1             # viscous Burgers, periodic [-1,1)^d, n = 2^j points, WENO5 advection (Sec. 4.1)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FP contraction) if needed."""
+def build(force: bool = False, all_cores: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction) if needed: the plain
+    build, or (all_cores) the same file with -fopenmp, whose pragmas split the
+    outermost grid loops over the host's cores (the same results bit for bit)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    path = _OMP_PATH if all_cores else _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+                               "-D_DEFAULT_SOURCE"] + (["-fopenmp"] if all_cores else ["-Wno-unknown-pragmas"])
+                              + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+def set_all_cores(enabled: bool) -> None:
+    """Route every later call to the OpenMP build (all host cores; OMP_NUM_THREADS
+    bounds it) or back to the plain single-threaded build."""
+    global _all_cores
+    _all_cores = bool(enabled)
+
+
+class all_cores:
+    """Context manager: the oracle runs on all host cores inside the block."""
+
+    def __enter__(self):
+        self._prev = _all_cores
+        set_all_cores(True)
+        return self
+
+    def __exit__(self, *exc):
+        set_all_cores(self._prev)
+        return False
+
+
+def threads() -> int:
+    """Threads the active build's loops use (1 for the plain build)."""
+    return int(_L().orc_threads())
+
+
+def set_threads(t: int) -> None:
+    """Threads for the all-core build's loops (default: OMP_NUM_THREADS or all cores)."""
+    with all_cores():
+        _L().orc_set_threads(int(t))
 
 
 class _Problem(ctypes.Structure):
@@ -106,9 +143,9 @@ class Problem:
 
 
 def _L():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+    key = bool(_all_cores)
+    if key not in _libs:
+        lib = ctypes.CDLL(build(all_cores=key))
         dp = ctypes.POINTER(ctypes.c_double)
         I, D = ctypes.c_int, ctypes.c_double
         lib.orc_lobatto_nodes.argtypes = [I, dp]
@@ -145,11 +182,14 @@ def _L():
                                       ctypes.POINTER(ctypes.c_long), dp, dp, dp]
         lib.orc_sdc_residual.argtypes = [ctypes.POINTER(_Problem), dp, dp]
         lib.orc_sdc_residual.restype = D
+        lib.orc_threads.argtypes = []
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_set_threads.restype = None
         for f in ("orc_lobatto_nodes", "orc_nodes", "orc_end_weights", "orc_q_matrix", "orc_s_matrix",
-                  "orc_vcycle", "orc_isdc_step"):
+                  "orc_vcycle", "orc_isdc_step", "orc_threads"):
             getattr(lib, f).restype = I
-        _lib = lib
-    return _lib
+        _libs[key] = lib
+    return _libs[key]
 
 
 def _p(a: np.ndarray):
