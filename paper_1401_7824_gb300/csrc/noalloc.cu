@@ -59,42 +59,38 @@ isdc_status device_setup(void** addr) {
   return ISDC_OK;
 }
 
-// Dense inverse of I - a L_h on the side-3 grid (Gauss-Jordan, partial
-// pivoting) into a caller-provided array (no heap use).
-void side3_inverse(int dim, double a, double* inv) {
-  const int n = 3, Np = dim == 2 ? 9 : 27;
-  const double h = 1.0 / (n + 1), c = a / (h * h), d = 1.0 + 2.0 * dim * c;
-  double A[27 * 27];
-  for (int q = 0; q < Np * Np; ++q) { A[q] = 0.0; inv[q] = 0.0; }
-  for (int p = 0; p < Np; ++p) {
-    const int i = p % n, j = (p / n) % n, k = dim == 3 ? p / (n * n) : 0;
-    A[p * Np + p] = d;
-    inv[p * Np + p] = 1.0;
-    const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
-    for (int q = 0; q < 2 * dim; ++q) {
-      const int ii = nb[q][0], jj = nb[q][1], kk = nb[q][2];
-      if (ii < 0 || ii >= n || jj < 0 || jj >= n || kk < 0 || kk >= (dim == 3 ? n : 1)) continue;
-      A[p * Np + (ii + n * (jj + n * kk))] = -c;
+// Dense inverse of I - a L_h on the side-3 grid (h = 1/4), times d_3 (the
+// bottom kernels apply it to beta = b / d_3), written by one block straight
+// into the static array.  The operator is diagonalised by the sine basis:
+// with s_q(i) = sqrt(1/2) sin(pi q i / 4) per axis (1-based i, q in {1,2,3},
+// orthonormal), (I - a L_h)^{-1}[i][j] = sum_q prod_axes s_q(i) s_q(j) / mu_q,
+// mu_q = 1 + (4a/h^2) sum_axes sin^2(pi q h / 2).  One thread per entry.
+template <int DIM>
+__global__ void k_side3_inverse(double a, double* __restrict__ inv) {
+  constexpr int Np = DIM == 2 ? 9 : 27;
+  __shared__ double S[3][3], mu[Np];
+  const int t = threadIdx.x;
+  const double c16 = 16.0 * a;  // a / h^2 with h = 1/4
+  if (t < 9) S[t / 3][t % 3] = sqrt(0.5) * sinpi(double((t / 3 + 1) * (t % 3 + 1)) / 4.0);
+  if (t < Np) {
+    double sum = 0.0;
+    for (int ax = 0, q = t; ax < DIM; ++ax, q /= 3) {
+      const double sn = sinpi(double(q % 3 + 1) / 8.0);
+      sum += sn * sn;
     }
+    mu[t] = 1.0 + 4.0 * c16 * sum;
   }
-  for (int col = 0; col < Np; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < Np; ++r)
-      if (std::fabs(A[r * Np + col]) > std::fabs(A[piv * Np + col])) piv = r;
-    if (piv != col)
-      for (int q = 0; q < Np; ++q) {
-        double t = A[col * Np + q]; A[col * Np + q] = A[piv * Np + q]; A[piv * Np + q] = t;
-        t = inv[col * Np + q]; inv[col * Np + q] = inv[piv * Np + q]; inv[piv * Np + q] = t;
-      }
-    const double s = 1.0 / A[col * Np + col];
-    for (int q = 0; q < Np; ++q) { A[col * Np + q] *= s; inv[col * Np + q] *= s; }
-    for (int r = 0; r < Np; ++r) {
-      if (r == col) continue;
-      const double f = A[r * Np + col];
-      if (f == 0.0) continue;
-      for (int q = 0; q < Np; ++q) { A[r * Np + q] -= f * A[col * Np + q]; inv[r * Np + q] -= f * inv[col * Np + q]; }
-    }
+  __syncthreads();
+  if (t >= Np * Np) return;
+  const int row = t / Np, col = t % Np;
+  double acc = 0.0;
+  for (int q = 0; q < Np; ++q) {
+    double w = 1.0;
+    for (int ax = 0, r = row, c = col, qq = q; ax < DIM; ++ax, r /= 3, c /= 3, qq /= 3)
+      w *= S[r % 3][qq % 3] * S[c % 3][qq % 3];
+    acc += w / mu[q];
   }
+  inv[t] = acc * (1.0 + 2.0 * DIM * c16);
 }
 
 // The V-cycle's buffers carved out of the static scratch.
@@ -256,8 +252,13 @@ ISDC_API isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoo
   if (!x || !b || !(a > 0) || !std::isfinite(a) || n_cycles < 0) return ISDC_ERR_INVALID_ARG;
   if (smoother != ISDC_SMOOTHER_JACOBI && smoother != ISDC_SMOOTHER_RBGS) return ISDC_ERR_INVALID_ARG;
   if (nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || nu1 > 16 || nu2 > 16) return ISDC_ERR_INVALID_ARG;
+  if (smoother == ISDC_SMOOTHER_JACOBI && !(omega > 0 && omega <= 1)) return ISDC_ERR_INVALID_ARG;
+  // every level of a grid that fits the array has a slot in Layout; sides with
+  // more levels than Layout holds are far beyond the array anyway
+  int nlev = 1;
+  for (int64_t s = n; s > 3; s = (s - 1) / 2) ++nlev;
+  if (nlev > kMaxLevels || (ndim == 3 && n > 1289)) return ISDC_ERR_SCRATCH_TOO_SMALL;
   Solve S{};
-  if (ndim == 3 && n > 1289) return ISDC_ERR_SCRATCH_TOO_SMALL;
   plan(ndim, int(n), smoother == ISDC_SMOOTHER_JACOBI, S.L);
   if (S.L.bytes > ISDC_STATIC_SCRATCH_BYTES) return ISDC_ERR_SCRATCH_TOO_SMALL;
   void* addr = nullptr;
@@ -271,13 +272,9 @@ ISDC_API isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoo
   S.a = a;
   S.stream = static_cast<cudaStream_t>(stream);
   S.base = static_cast<unsigned char*>(addr);
-  double inv[27 * 27];
-  side3_inverse(ndim, a, inv);
-  const double d3 = 1.0 + 2.0 * ndim * a * 16.0;  // the inverse acts on beta = b / d (h = 1/4)
-  for (int q = 0; q < (ndim == 2 ? 81 : 729); ++q) inv[q] *= d3;
-  // pageable source: the copy is staged before cudaMemcpyAsync returns
-  STATIC_TRY(cudaMemcpyAsync(S.at(S.L.ainv), inv, (ndim == 2 ? 81 : 729) * sizeof(double), cudaMemcpyHostToDevice,
-                             S.stream));
+  if (ndim == 2) k_side3_inverse<2><<<1, 81, 0, S.stream>>>(a, S.at(S.L.ainv));
+  else k_side3_inverse<3><<<1, 729, 0, S.stream>>>(a, S.at(S.L.ainv));
+  STATIC_TRY(cudaGetLastError());
   // the V-cycles act on the row-scaled system x - kappa * (neighbour sum) = b / d
   double* beta = S.at(S.L.beta);
   k_scale<double><<<4 * 152, 256, 0, S.stream>>>(S.L.npts[0], 1.0 / coef(ndim, int(n), a).d, b, beta);
