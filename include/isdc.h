@@ -70,7 +70,7 @@ typedef enum { ISDC_REACTION_NONE = 0, ISDC_REACTION_ALLEN_CAHN = 1 } isdc_react
 typedef struct {
     int    smoother;      /* isdc_smoother: damped Jacobi (default) or red-black Gauss-Seidel */
     int    nu1, nu2;      /* pre/post smoothing sweeps per level (default 1, 1) */
-    double omega;         /* Jacobi damping (default 2/3) */
+    double omega;         /* Jacobi damping (default 2/3; must lie in (0, 1] with the Jacobi smoother) */
     int    vcycle_fp32;   /* 0: V-cycles in FP64.  1: FP32 V-cycles in defect-correction
                              form (FP64 defect b - (I - dt_m A)x, FP32 cycle on the error,
                              FP64 update); node values, S F, residuals stay FP64. */
@@ -111,6 +111,12 @@ typedef struct {
                              the next point's loads issued before each store; -1, -2, -4 or -8:
                              runs of that many points with all loads issued first.  Every choice
                              gives the same result bit for bit. */
+    int    fused_transfer; /* residual + full-weighting restriction on every level above the
+                             single-block bottom (launch form, not from the paper): -1 (default)
+                             lets the autotuner in isdc_create time both forms per level and keep
+                             the faster; 1: one launch, the fine residual kept in shared memory;
+                             0: two launches, the residual written to device memory and read
+                             back.  Every choice gives the same result bit for bit. */
     void  *stream;        /* cudaStream_t to run on.  NULL: the context creates its own
                              non-blocking stream.  To run on the legacy default stream pass
                              cudaStreamLegacy ((void*)1), for the per-thread default stream
@@ -139,8 +145,9 @@ isdc_status isdc_collocation_tables(isdc_node_type nodes, int M, double *tau, do
  * (u and f(u) at t_0 and every node) and the multigrid hierarchy (sides
  * n, (n-1)/2, ... down to 3).
  *   ndim   2 or 3
- *   dims   ndim sides, all equal: 2^j - 1 interior points with j >= 2 (equation 0) or
- *          2^j periodic points with j >= 3 (equation 1)
+ *   dims   ndim sides, all equal: 2^j - 1 interior points with 2 <= j <= 13 (equation 0) or
+ *          2^j periodic points with 3 <= j <= 13 (equation 1), so that the hierarchy has at
+ *          most 12 levels; 3D sides at most 1289 (32-bit point indices)
  *   nu     diffusion coefficient (> 0)
  *   nodes  isdc_node_type (Gauss-Lobatto, Gauss-Radau right or Gauss-Legendre)
  *   M      number of nodes, 2..7
@@ -231,7 +238,8 @@ isdc_status isdc_vcycles(isdc_ctx *ctx, double a, double *x, const double *b, in
  * right-hand side and the side-3 inverse live in one static device array of ISDC_STATIC_SCRATCH_BYTES that
  * every GPU which loads this library keeps until the process exits.  Grids
  * whose buffers exceed it (2D sides above 1023, 3D sides above 127) are
- * rejected with ISDC_ERR_SCRATCH_TOO_SMALL before any GPU work.
+ * rejected with ISDC_ERR_SCRATCH_TOO_SMALL before any GPU work.  With the
+ * Jacobi smoother omega must lie in (0, 1] (else INVALID_ARG).
  *
  * The first call on each device (with that device current) looks up the
  * array's device address and sets the bottom kernels' shared-memory limit;
@@ -252,7 +260,11 @@ isdc_status isdc_vcycles_static(int ndim, int64_t n, double a, int smoother, int
  * of time steps; the smoother, nu1/nu2, L, tol and max_sweeps are the
  * engine's).  Every tick advances every running instance by one SDC sweep:
  * each phase of the sweep is one grid-stride launch over all instances taking
- * part, and the whole tick is one CUDA graph.  V-cycles run in FP32 in
+ * part, and the whole tick is one CUDA graph.  The coarse levels of every
+ * instance (2D sides <= 63, 3D sides <= 15) run in one block per instance in
+ * shared memory; with 2D damped-Jacobi V(1, nu2 <= 1) cycles the sweep of each
+ * grid-wide level is fused into its transfer passes (one pass per leg and
+ * level).  V-cycles run in FP32 in
  * defect-correction form; node values, S F, node residuals and the SDC
  * residual are FP64.  Instances are admitted and their results taken between
  * ticks; device memory for an instance is taken with cudaMallocAsync on
@@ -287,15 +299,26 @@ typedef struct {
     size_t  bytes_in_use;
     int     running;
     int     tuned;              /* 1 once the autotuner has picked the launch shape */
-    int     threads_per_block;  /* launch shape in use (tile = one point per thread) */
+    int     threads_per_block;  /* launch shape in use (tile = one point per thread; the fused 2D
+                                   phases' tile is 32 x threads/32 coarse points) */
     int     blocks_per_sm;      /* persistent blocks per SM */
+    int     fused;              /* 1: the 2D damped-Jacobi smoother is fused into the transfer
+                                   passes (one pass per leg and level); 0: separate phases */
+    int     kernels_per_tick;   /* kernel launches of one tick in the shape in use */
+    double  bytes_last_tick;    /* algorithmic device-memory bytes of the last tick (each phase
+                                   reads each input once and writes each output once) */
 } isdc_batch_info;
 
 /* ndim 2 or 3; max_side: the largest side that will be admitted (sets the
- * number of multigrid phases); max_M <= 7; hbm_budget_bytes: device memory the
+ * number of multigrid phases; 2^j - 1 with 3 <= j <= 13, in 3D at most 1289); max_M <= 7; hbm_budget_bytes: device memory the
  * instances may hold together; n_vcycles: L >= 1; opt as for isdc_create
- * (nu1 >= 1 is required; vcycle_fp32 is implied; stream NULL = own stream).
- * The first ticks try several launch shapes and keep the fastest (autotuner).
+ * (nu1 >= 1 is required; vcycle_fp32 is implied; stream NULL = own stream;
+ * temporal_blocking for 2D damped-Jacobi V(1, nu2 <= 1) engines: -1 or 1 fuse
+ * the sweep into the transfer passes, 0 keeps it a separate phase; other
+ * values INVALID_ARG; the two round differently, so the choice is fixed for
+ * the engine's life).  The first ticks try several launch shapes (tile size,
+ * blocks per SM; all give the same result bit for bit) and keep the fastest
+ * (autotuner).
  * Errors: INVALID_ARG, OOM, CUDA. */
 isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, size_t hbm_budget_bytes, int n_vcycles,
                               const isdc_options *opt, isdc_batch **out);
@@ -363,6 +386,14 @@ isdc_status isdc_profile_read(isdc_ctx *ctx, isdc_kernel_stat *out, int cap, int
  * (red-black sweeps per pass, 0 = one pass per colour) and the z-planes per
  * block of the blocked pass.  Any output pointer may be NULL. */
 isdc_status isdc_tuning(const isdc_ctx *ctx, int *zb_fp64, int *zb_fp32, int *tb_depth, int *tb_planes);
+
+/* The residual + restriction form chosen for each grid-wide multigrid level
+ * l = 0 .. *n_levels - 1 (the levels above the single-block bottom; 0 for the
+ * compact-stencil and periodic configurations): kc[l] = 0 two launches,
+ * kc[l] > 0 one fused launch (3D: kc[l] coarse planes per block).  Fills at
+ * most max_levels entries of kc (host); n_levels may be NULL.
+ * Errors: INVALID_ARG. */
+isdc_status isdc_tuning_transfer(const isdc_ctx *ctx, int *kc, int max_levels, int *n_levels);
 
 /* Message for the last failure of ctx, or of isdc_create when ctx is NULL. */
 const char *isdc_last_error(const isdc_ctx *ctx);

@@ -25,6 +25,7 @@
 #include "sdc_kernels.cuh"
 #include "compact_kernels.cuh"
 #include "periodic_kernels.cuh"
+#include "resrestrict.cuh"
 
 #define ISDC_API extern "C" __attribute__((visibility("default")))
 
@@ -55,12 +56,13 @@ struct Hier {
 // Kernel classes timed by the built-in profiler (isdc_profile_*).
 enum ProfClass {
   PC_SPREAD, PC_EVAL_F, PC_RHS, PC_SWEEP_END, PC_SMOOTH0, PC_RESIDUAL0, PC_RESTRICT0, PC_PROLONG0,
-  PC_SMOOTHC, PC_RESIDUALC, PC_RESTRICTC, PC_PROLONGC, PC_BOTTOM, PC_DEFECT, PC_UPDATE, PC_RESNORM, PC_WINV, PC_COUNT
+  PC_SMOOTHC, PC_RESIDUALC, PC_RESTRICTC, PC_PROLONGC, PC_BOTTOM, PC_DEFECT, PC_UPDATE, PC_RESNORM, PC_WINV,
+  PC_RESRESTRICT0, PC_RESRESTRICTC, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT] = {
     "spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine", "prolong_fine",
     "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse", "bottom", "defect", "update",
-    "resnorm", "w_inverse"};
+    "resnorm", "w_inverse", "resrestrict_fine", "resrestrict_coarse"};
 
 struct Profiler {
   bool on = false;
@@ -136,6 +138,10 @@ struct isdc_ctx {
   float* sp_xb = nullptr;        // second black array of the split level (blocked passes ping-pong into it)
   // per grid-wide level (natural layout): run length, negative for burst runs (launch_rbgs)
   int zbl[kMaxLevels] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  // residual + restriction per grid-wide level of the FP64 / FP32 hierarchy:
+  // 0 two launches, > 0 one fused launch with that many coarse planes per
+  // block (2D: 1); rr_split: the same for the colour-split FP32 fine level
+  int rr64[kMaxLevels] = {}, rr32[kMaxLevels] = {}, rr_split = 0;
   char err[512] = "";
 };
 
@@ -423,6 +429,25 @@ isdc_status vcycle(isdc_ctx* ctx, Hier<T>& H, int slot, double a, T* x0, const T
     const double Np = double(H.npts[l]), Nc = double(H.npts[l + 1]);
     // after a complete red-black sweep only the red rows carry a residual
     const bool red_only = ctx->opt.smoother == ISDC_SMOOTHER_RBGS && ctx->opt.nu1 >= 1;
+    const int kc = (sizeof(T) == 8 ? ctx->rr64 : ctx->rr32)[l];
+    if (kc > 0) {
+      // residual and full weighting in one launch: r stays in shared memory
+      const int sc = H.side[l + 1];
+      const T ws = T(lf.d / (level_coef(DIM, sc, a).d * (DIM == 2 ? 16.0 : 64.0)));
+      const double f = red_only ? 0.5 : 1.0;
+      ProfScope ps(ctx, l == 0 ? PC_RESRESTRICT0 : PC_RESRESTRICTC, ((red_only ? 1.5 : 2.0) * Np + Nc) * sizeof(T),
+                   (nb_ops(DIM) + 2.0) * f * Np +
+                       (red_only ? (DIM == 2 ? 6.0 : 15.0) : (DIM == 2 ? 9.0 : 27.0)) * Nc,
+                   sizeof(T) == 8);
+      const dim3 g = resrestrict_grid(DIM, sc, kc), blk(kRrTX, kRrTY, 1);
+      if (red_only)
+        k_resrestrict<T, DIM, true><<<g, blk, 0, ctx->stream>>>(sc, T(lf.kappa), ws, x, b, H.b[l + 1], kc);
+      else
+        k_resrestrict<T, DIM, false><<<g, blk, 0, ctx->stream>>>(sc, T(lf.kappa), ws, x, b, H.b[l + 1], kc);
+      LAUNCH_CHECK(ctx);
+      xcur[l] = x;
+      continue;
+    }
     {
       const double f = red_only ? 0.5 : 1.0;
       ProfScope ps(ctx, l == 0 ? PC_RESIDUAL0 : PC_RESIDUALC, (red_only ? 2.0 : 3.0) * Np * sizeof(T),
@@ -600,12 +625,18 @@ isdc_status node_solve_split(isdc_ctx* ctx, int slot, double a, double* x, const
   }
   for (int c = 0; c < n_cycles; ++c) {
     if ((st = smooth_split<DIM>(ctx, kappa, ctx->opt.nu1, c == 0, &xb)) != ISDC_OK) return st;
-    {
-      ProfScope ps(ctx, PC_RESIDUAL0, 2.0 * Np * 4, (nb_ops(DIM) + 2.0) * 0.5 * Np, false);
-      k_residual_red_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, x0, xb, b0, ctx->sp_r);
-    }
-    LAUNCH_CHECK(ctx);
-    {
+    if (ctx->rr_split > 0) {
+      const int kc = ctx->rr_split;
+      ProfScope ps(ctx, PC_RESRESTRICT0, (1.5 * Np + Nc) * 4,
+                   (nb_ops(DIM) + 2.0) * 0.5 * Np + (DIM == 2 ? 6.0 : 15.0) * Nc, false);
+      k_resrestrict_red_split<DIM><<<resrestrict_grid(DIM, sc, kc), dim3(kRrTX, kRrTY, 1), 0, ctx->stream>>>(
+          sc, kappa, ws, x0, xb, b0, H.b[1], kc);
+    } else {
+      {
+        ProfScope ps(ctx, PC_RESIDUAL0, 2.0 * Np * 4, (nb_ops(DIM) + 2.0) * 0.5 * Np, false);
+        k_residual_red_split<DIM><<<g, kBlock, 0, ctx->stream>>>(s, kappa, x0, xb, b0, ctx->sp_r);
+      }
+      LAUNCH_CHECK(ctx);
       ProfScope ps(ctx, PC_RESTRICT0, (0.5 * Np + Nc) * 4, (DIM == 2 ? 6.0 : 15.0) * Nc, false);
       k_restrict_red_split<DIM><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, ctx->sp_r, H.b[1]);
     }
@@ -1559,6 +1590,112 @@ isdc_status tune_blocking(isdc_ctx* ctx, cudaEvent_t e0, cudaEvent_t e1) {
   return ISDC_OK;
 }
 
+// Residual + restriction of every grid-wide level: the two-launch form and the
+// fused launch (3D: 4, 8 or 16 coarse planes per block) give the same values
+// bit for bit; time each on the level's own arrays and keep the fastest.
+template <typename T, int DIM>
+isdc_status time_transfer(isdc_ctx* ctx, Hier<T>& H, int l, const T* x, const T* b, bool split, int kc, int reps,
+                          cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  const int s = H.side[l], sc = H.side[l + 1];
+  const T kappa = T(0.1), ws = T(0.01);
+  const bool red_only = ctx->opt.smoother == ISDC_SMOOTHER_RBGS && ctx->opt.nu1 >= 1;
+  const dim3 gf = resrestrict_grid(DIM, sc, kc), bf(kRrTX, kRrTY, 1);
+  CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+  for (int r = 0; r < reps; ++r) {
+    if (split) {
+      const size_t hn = ctx->hn;
+      const float *xr = ctx->sp_x, *xb = ctx->sp_x + hn, *br = ctx->sp_b;
+      if (kc > 0) {
+        k_resrestrict_red_split<DIM><<<gf, bf, 0, ctx->stream>>>(sc, float(kappa), float(ws), xr, xb, br,
+                                                                 reinterpret_cast<float*>(H.b[1]), kc);
+      } else {
+        k_residual_red_split<DIM><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, float(kappa), xr, xb, br,
+                                                                               ctx->sp_r);
+        k_restrict_red_split<DIM><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, float(ws), ctx->sp_r,
+                                                                                reinterpret_cast<float*>(H.b[1]));
+      }
+    } else if (kc > 0) {
+      if (red_only) k_resrestrict<T, DIM, true><<<gf, bf, 0, ctx->stream>>>(sc, kappa, ws, x, b, H.b[l + 1], kc);
+      else k_resrestrict<T, DIM, false><<<gf, bf, 0, ctx->stream>>>(sc, kappa, ws, x, b, H.b[l + 1], kc);
+    } else if (red_only) {
+      k_residual<T, DIM, true><<<rb_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, x, b, H.r[l]);
+      k_restrict<T, DIM, true><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
+    } else {
+      k_residual<T, DIM, false><<<pt_grid(DIM, s), kBlock, 0, ctx->stream>>>(s, kappa, x, b, H.r[l]);
+      k_restrict<T, DIM, false><<<pt_grid(DIM, sc), kBlock, 0, ctx->stream>>>(sc, ws, H.r[l], H.b[l + 1]);
+    }
+  }
+  CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
+  CUDA_TRY(ctx, cudaEventSynchronize(e1));
+  CUDA_TRY(ctx, cudaGetLastError());
+  CUDA_TRY(ctx, cudaEventElapsedTime(ms, e0, e1));
+  return ISDC_OK;
+}
+
+template <typename T, int DIM>
+isdc_status tune_transfer(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cudaEvent_t e0, cudaEvent_t e1) {
+  int* rr = sizeof(T) == 8 ? ctx->rr64 : ctx->rr32;
+  const int cand3[4] = {0, 4, 8, 16}, cand2[2] = {0, 1};
+  for (int l = 0; l < H.lb; ++l) {
+    const bool split = l == 0 && split0;
+    T* x = l == 0 ? x0 : H.x[l];
+    T* b = l == 0 ? b0 : H.b[l];
+    if (split) {
+      CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_x, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+      CUDA_TRY(ctx, cudaMemsetAsync(ctx->sp_b, 0, 2 * ctx->hn * sizeof(float), ctx->stream));
+    } else {
+      CUDA_TRY(ctx, cudaMemsetAsync(x, 0, H.npts[l] * sizeof(T), ctx->stream));
+      CUDA_TRY(ctx, cudaMemsetAsync(b, 0, H.npts[l] * sizeof(T), ctx->stream));
+    }
+    const int reps = H.npts[l] >= (size_t(1) << 20) ? 4 : 32;
+    const int nc = DIM == 3 ? 4 : 2;
+    float best = 1e30f;
+    int pick = 0;
+    for (int round = 0; round < 3; ++round)  // the first round warms up
+      for (int c = 0; c < nc; ++c) {
+        const int kc = DIM == 3 ? cand3[c] : cand2[c];
+        float ms = 0.f;
+        isdc_status st = time_transfer<T, DIM>(ctx, H, l, x, b, split, kc, reps, e0, e1, &ms);
+        if (st != ISDC_OK) return st;
+        if (round >= 1 && ms < best) {
+          best = ms;
+          pick = kc;
+        }
+      }
+    if (split) ctx->rr_split = pick;
+    else rr[l] = pick;
+  }
+  return ISDC_OK;
+}
+
+// Fixed forms (option fused_transfer 0 or 1) or the tuned choice (-1).
+isdc_status setup_transfer(isdc_ctx* ctx) {
+  if (ctx->stencil == 1 || ctx->equation == 1) return ISDC_OK;  // their own transfer kernels
+  const int f = ctx->opt.fused_transfer;
+  const bool fp32 = ctx->opt.vcycle_fp32 != 0;
+  const int lb = fp32 ? ctx->h32.lb : ctx->h64.lb;
+  for (int l = 0; l < lb; ++l) {
+    const int sc = fp32 ? ctx->h32.side[l + 1] : ctx->h64.side[l + 1];
+    const int kc = f == 1 ? (ctx->dim == 3 ? resrestrict_kc(sc) : 1) : 0;
+    (fp32 ? ctx->rr32 : ctx->rr64)[l] = kc;
+  }
+  if (ctx->sp_x) ctx->rr_split = f == 1 ? (ctx->dim == 3 ? resrestrict_kc(ctx->h32.side[1]) : 1) : 0;
+  if (f != -1) return ISDC_OK;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  isdc_status st;
+  if (fp32)
+    st = ctx->dim == 2 ? tune_transfer<float, 2>(ctx, ctx->h32, ctx->h32.x[0], ctx->h32.b[0], ctx->sp_x != nullptr, e0, e1)
+                       : tune_transfer<float, 3>(ctx, ctx->h32, ctx->h32.x[0], ctx->h32.b[0], ctx->sp_x != nullptr, e0, e1);
+  else
+    st = ctx->dim == 2 ? tune_transfer<double, 2>(ctx, ctx->h64, ctx->U, ctx->b, false, e0, e1)
+                       : tune_transfer<double, 3>(ctx, ctx->h64, ctx->U, ctx->b, false, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
 isdc_status tune_smoother(isdc_ctx* ctx) {
   if (ctx->dim != 3 || ctx->opt.smoother != ISDC_SMOOTHER_RBGS) return ISDC_OK;
   cudaEvent_t e0, e1;
@@ -1597,6 +1734,7 @@ ISDC_API isdc_status isdc_default_options(isdc_options* opt) {
   opt->use_graphs = 1;
   opt->temporal_blocking = -1;
   opt->rb_run = 0;
+  opt->fused_transfer = -1;
   opt->stencil = 0;
   opt->equation = 0;
   opt->stream = nullptr;
@@ -1676,6 +1814,13 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "periodic side must be 2^j with j >= 3 (got %lld)", (long long)n);
   if ((ndim == 2 && n > 46339) || (ndim == 3 && n > 1289))
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "grid too large for 32-bit point indices");
+  {
+    int nlev = 1;
+    for (int64_t s = n; equation == 1 ? s > 4 : s > 3; s = equation == 1 ? s / 2 : (s - 1) / 2) ++nlev;
+    if (nlev > kMaxLevels)
+      return fail(nullptr, ISDC_ERR_INVALID_ARG, "side %lld needs %d multigrid levels (at most %d)", (long long)n, nlev,
+                  kMaxLevels);
+  }
   if (nodes != ISDC_NODES_GAUSS_LOBATTO && nodes != ISDC_NODES_RADAU_RIGHT && nodes != ISDC_NODES_GAUSS_LEGENDRE)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown node type %d", int(nodes));
   if (M < 2 || M > kMaxM) return fail(nullptr, ISDC_ERR_INVALID_ARG, "M must be in [2, %d] (got %d)", kMaxM, M);
@@ -1685,6 +1830,8 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   if (opt) o = *opt; else isdc_default_options(&o);
   if (o.smoother != ISDC_SMOOTHER_JACOBI && o.smoother != ISDC_SMOOTHER_RBGS)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown smoother %d", o.smoother);
+  if (o.smoother == ISDC_SMOOTHER_JACOBI && !(o.omega > 0 && o.omega <= 1))
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "the Jacobi damping omega must be in (0, 1]");
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "nu1, nu2 must be in [0, 16] with nu1 + nu2 >= 1");
   if (o.reaction != ISDC_REACTION_NONE && o.reaction != ISDC_REACTION_ALLEN_CAHN)
@@ -1699,6 +1846,8 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
                     r == 16 || r == 32;
     if (!ok) return fail(nullptr, ISDC_ERR_INVALID_ARG, "rb_run must be 0, 1, 2, 4, 8, 16, 32, -1, -2, -4 or -8");
   }
+  if (o.fused_transfer < -1 || o.fused_transfer > 1)
+    return fail(nullptr, ISDC_ERR_INVALID_ARG, "fused_transfer must be -1, 0 or 1");
   if (o.stencil != 0 && o.stencil != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown stencil %d", o.stencil);
   if (o.stencil == 1 && (ndim != 2 || o.smoother != ISDC_SMOOTHER_JACOBI || o.vcycle_fp32 || o.equation != 0))
     return fail(nullptr, ISDC_ERR_UNSUPPORTED,
@@ -1816,6 +1965,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
   }
   ctx->spare_slot = P - 1;
   if ((st = tune_smoother(ctx)) != ISDC_OK) return bail(st);
+  if ((st = setup_transfer(ctx)) != ISDC_OK) return bail(st);
   CREATE_TRY(cudaGetLastError());
 #undef CREATE_TRY
   *out = ctx;
@@ -1967,6 +2117,16 @@ ISDC_API isdc_status isdc_tuning(const isdc_ctx* ctx, int* zb_fp64, int* zb_fp32
   if (zb_fp32) *zb_fp32 = ctx->zb32;
   if (tb_depth) *tb_depth = ctx->tb_depth;
   if (tb_planes) *tb_planes = ctx->tb_zc;
+  return ISDC_OK;
+}
+
+ISDC_API isdc_status isdc_tuning_transfer(const isdc_ctx* ctx, int* kc, int max_levels, int* n_levels) {
+  if (!ctx || (!kc && max_levels > 0) || max_levels < 0) return ISDC_ERR_INVALID_ARG;
+  const bool fp32 = ctx->opt.vcycle_fp32 != 0;
+  const int lb = ctx->stencil == 1 || ctx->equation == 1 ? 0 : (fp32 ? ctx->h32.lb : ctx->h64.lb);
+  for (int l = 0; l < lb && l < max_levels; ++l)
+    kc[l] = (l == 0 && ctx->sp_x) ? ctx->rr_split : (fp32 ? ctx->rr32 : ctx->rr64)[l];
+  if (n_levels) *n_levels = lb;
   return ISDC_OK;
 }
 

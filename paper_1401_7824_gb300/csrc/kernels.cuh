@@ -858,10 +858,11 @@ __device__ void bt_smooth(const BottomParams<T>& P, int l, T* x, const T* b, T* 
   }
 }
 
+// The bottom V-cycle of one grid in one block; smem_raw holds 3 arrays per
+// level (shared by k_bottom and the batched engine's per-instance bottoms).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kBottomThreads)
-    k_bottom(BottomParams<T> P, const T* __restrict__ b_top, T* __restrict__ x_top, int load_x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void bottom_vcycle(const BottomParams<T>& P, const T* __restrict__ b_top,
+                                              T* __restrict__ x_top, int load_x, unsigned char* smem_raw) {
   T* base = reinterpret_cast<T*>(smem_raw);
   T *X[kMaxLevels], *B[kMaxLevels], *Tt[kMaxLevels];
   int off = 0;
@@ -935,6 +936,13 @@ __global__ void __launch_bounds__(kBottomThreads)
     const int Np = DIM == 2 ? n * n : n * n * n;
     for (int p = threadIdx.x; p < Np; p += blockDim.x) x_top[p] = X[0][p];
   }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBottomThreads)
+    k_bottom(BottomParams<T> P, const T* __restrict__ b_top, T* __restrict__ x_top, int load_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bottom_vcycle<T, DIM>(P, b_top, x_top, load_x, smem_raw);
 }
 
 }  // namespace isdc

@@ -44,7 +44,8 @@ class isdc_options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("mg_tol", ctypes.c_double),
                 ("mg_max_cycles", ctypes.c_int), ("vcycle_cap", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("temporal_blocking", ctypes.c_int), ("stencil", ctypes.c_int),
-                ("equation", ctypes.c_int), ("rb_run", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("equation", ctypes.c_int), ("rb_run", ctypes.c_int), ("fused_transfer", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class isdc_kernel_stat(ctypes.Structure):
@@ -66,7 +67,8 @@ class isdc_slot_info(ctypes.Structure):
 class isdc_batch_info(ctypes.Structure):
     _fields_ = [("ticks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
                 ("running", ctypes.c_int),
-                ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+                ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("fused", ctypes.c_int), ("kernels_per_tick", ctypes.c_int), ("bytes_last_tick", ctypes.c_double)]
 
 
 ISDC_SLOT_FREE, ISDC_SLOT_RUNNING, ISDC_SLOT_FINISHED, ISDC_SLOT_FAILED = 0, 1, 2, 3
@@ -85,6 +87,28 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 def library_path() -> str:
     return _build.LIB
+
+
+_probe = None
+
+
+def probe_fp64_rate():
+    """The GPU's FP64 issue rate (FP64 operations per second; one FMA = one
+    operation) measured by libisdc_probe.so, and the best launch's ms."""
+    global _probe
+    if _probe is None:
+        path = _build.build_probe()
+        if not os.path.exists(path):
+            raise RuntimeError(f"probe library {path} is missing; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        lib.isdc_probe_fp64_rate.argtypes = [_dp, _dp]
+        lib.isdc_probe_fp64_rate.restype = ctypes.c_int
+        _probe = lib
+    ops, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = _probe.isdc_probe_fp64_rate(ctypes.byref(ops), ctypes.byref(ms))
+    if st != 0:
+        raise RuntimeError(f"isdc_probe_fp64_rate failed ({st})")
+    return ops.value, ms.value
 
 
 def load(build_if_missing: bool = True):
@@ -124,6 +148,7 @@ def load(build_if_missing: bool = True):
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
         "isdc_tuning": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "isdc_tuning_transfer": (I, [_ctx_p, ctypes.POINTER(I), I, ctypes.POINTER(I)]),
         "isdc_last_error": (ctypes.c_char_p, [_ctx_p]),
         "isdc_destroy": (None, [_ctx_p]),
     }
@@ -256,7 +281,7 @@ def isdc_vcycles_static(ndim, n, a: float, x, b, n_cycles: int, smoother=ISDC_SM
 
 PROFILE_CLASSES = ["spread", "eval_f", "rhs", "sweep_end", "smooth_fine", "residual_fine", "restrict_fine",
                    "prolong_fine", "smooth_coarse", "residual_coarse", "restrict_coarse", "prolong_coarse",
-                   "bottom", "defect", "update", "resnorm", "w_inverse"]
+                   "bottom", "defect", "update", "resnorm", "w_inverse", "resrestrict_fine", "resrestrict_coarse"]
 
 
 def isdc_profile_enable(ctx, enable, classes=None):
@@ -289,7 +314,11 @@ def isdc_profile_read(ctx):
 def isdc_tuning(ctx):
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().isdc_tuning(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), ctx)
-    return {"zb_fp64": a.value, "zb_fp32": b.value, "tb_depth": c.value, "tb_planes": d.value}
+    kc = (ctypes.c_int * 16)()
+    nl = ctypes.c_int()
+    _check(load().isdc_tuning_transfer(ctx, kc, 16, ctypes.byref(nl)), ctx)
+    return {"zb_fp64": a.value, "zb_fp32": b.value, "tb_depth": c.value, "tb_planes": d.value,
+            "transfer_kc": [kc[i] for i in range(min(nl.value, 16))]}
 
 
 def isdc_last_error(ctx=None) -> str:
@@ -373,10 +402,11 @@ class Batch:
 
     def __init__(self, ndim, max_side, max_M=5, hbm_budget_bytes=64 << 30, n_vcycles=2, *,
                  smoother=ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, omega=2.0 / 3.0, reaction=ISDC_REACTION_ALLEN_CAHN,
-                 tol=1e-10, max_sweeps=100):
+                 tol=1e-10, max_sweeps=100, temporal_blocking=-1):
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega, o.reaction = smoother, nu1, nu2, omega, reaction
         o.tol, o.max_sweeps, o.vcycle_fp32 = tol, max_sweeps, 1
+        o.temporal_blocking = int(temporal_blocking)
         self.ndim = ndim
         self.b = isdc_batch_create(ndim, max_side, max_M, hbm_budget_bytes, n_vcycles, o)
         self.sides = {}
@@ -424,14 +454,14 @@ class Isdc:
                  omega=2.0 / 3.0, vcycle_fp32=False, reaction=ISDC_REACTION_ALLEN_CAHN, tol=1e-10,
                  max_sweeps=100, mg_tol=1e-12, mg_max_cycles=50, vcycle_cap=False, use_graphs=True,
                  temporal_blocking=-1, nodes=ISDC_NODES_GAUSS_LOBATTO, stencil=ISDC_STENCIL_SECOND_ORDER,
-                 equation=ISDC_EQUATION_REACTION_DIFFUSION, rb_run=0, stream=None):
+                 equation=ISDC_EQUATION_REACTION_DIFFUSION, rb_run=0, fused_transfer=-1, stream=None):
         import torch
         o = isdc_default_options()
         o.smoother, o.nu1, o.nu2, o.omega = smoother, nu1, nu2, omega
         o.vcycle_fp32, o.reaction, o.tol, o.max_sweeps = int(vcycle_fp32), reaction, tol, max_sweeps
         o.mg_tol, o.mg_max_cycles, o.vcycle_cap = mg_tol, mg_max_cycles, int(vcycle_cap)
         o.use_graphs, o.temporal_blocking, o.stencil = int(use_graphs), int(temporal_blocking), int(stencil)
-        o.equation, o.rb_run = int(equation), int(rb_run)
+        o.equation, o.rb_run, o.fused_transfer = int(equation), int(rb_run), int(fused_transfer)
         s = stream if stream is not None else torch.cuda.current_stream()
         # torch's default stream has handle 0, which the C ABI reads as "create a
         # private stream"; pass cudaStreamLegacy (1) so the work orders with torch.

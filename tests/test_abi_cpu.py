@@ -14,14 +14,22 @@ import oracle as O
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    names = []
-    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if h.endswith(".h"):
-            txt = open(os.path.join(ROOT, "include", h)).read()
-            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names += re.findall(r"\b(isdc_\w+)\s*\(", txt)
-    return sorted(set(names))
+def _declared(header="isdc.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(isdc_\w+)\s*\(", txt)))
+
+
+def test_every_header_is_covered():
+    assert sorted(h for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")) == \
+        ["isdc.h", "isdc_probe.h"]
+
+
+def test_probe_library_exports_its_header():
+    import paper_1401_7824_gb300.build as B
+    path = B.build_probe()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(re.findall(r" T (isdc_\w+)", out)) == set(_declared("isdc_probe.h")) == {"isdc_probe_fp64_rate"}
 
 
 def test_library_exports_every_declared_symbol():
@@ -76,10 +84,11 @@ def test_host_validation_without_gpu():
         assert "must" in G.isdc_last_error()
     o = G.isdc_default_options()
     assert (o.smoother, o.nu1, o.nu2, o.max_sweeps, o.tol) == (0, 1, 1, 100, 1e-10)
-    assert (o.temporal_blocking, o.rb_run, o.stencil, o.equation) == (-1, 0, 0, 0)
+    assert (o.temporal_blocking, o.rb_run, o.stencil, o.equation, o.fused_transfer) == (-1, 0, 0, 0, -1)
     # option values outside their sets are refused before any device work
     for field, bad in [("rb_run", 3), ("rb_run", -16), ("rb_run", 64), ("temporal_blocking", 3),
-                       ("smoother", 2), ("nu1", 17), ("stencil", 2), ("reaction", 5), ("max_sweeps", 0)]:
+                       ("smoother", 2), ("nu1", 17), ("stencil", 2), ("reaction", 5), ("max_sweeps", 0),
+                       ("fused_transfer", 2), ("fused_transfer", -2)]:
         o = G.isdc_default_options()
         setattr(o, field, bad)
         with pytest.raises(G.IsdcError) as e:
@@ -90,6 +99,41 @@ def test_host_validation_without_gpu():
     with pytest.raises(G.IsdcError) as e:
         G.isdc_create(2, 31, 0.1, 3, 0.05, o)  # periodic sides are 2^j
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
+
+
+def test_oversized_grids_and_bad_damping_are_refused_before_device_work():
+    """Sides whose hierarchy would need more than 12 multigrid levels (2D 16383,
+    32767) and Jacobi damping outside (0, 1] are refused by argument checks that
+    run before any CUDA call, so they are exercised here without a GPU."""
+    import paper_1401_7824_gb300 as G
+    lib = G.load()
+    dummy = ctypes.c_void_p(4096)  # never dereferenced: every call below fails its checks first
+    for d, n in [(2, 16383), (2, 32767), (3, 255), (2, 2047), (3, 2047)]:
+        st = lib.isdc_vcycles_static(d, n, 0.01, G.ISDC_SMOOTHER_JACOBI, 1, 1, 2.0 / 3.0, dummy, dummy, 1, None)
+        assert st == G.ISDC_ERR_SCRATCH_TOO_SMALL, (d, n, st)
+    for omega in [0.0, -0.5, 1.5, float("nan"), float("inf")]:
+        st = lib.isdc_vcycles_static(2, 31, 0.01, G.ISDC_SMOOTHER_JACOBI, 1, 1, omega, dummy, dummy, 1, None)
+        assert st == G.ISDC_ERR_INVALID_ARG, omega
+        o = G.isdc_default_options()
+        o.omega = omega
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_create(2, 31, 0.1, 3, 0.05, o)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG and "omega" in G.isdc_last_error()
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_batch_create(2, 31, 3, 1 << 30, 2, o)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG
+    for n in [16383, 32767]:
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_create(2, n, 0.1, 3, 0.05)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG and "levels" in G.isdc_last_error()
+        with pytest.raises(G.IsdcError) as e:
+            G.isdc_batch_create(2, n, 3, 1 << 30, 2)
+        assert e.value.status == G.ISDC_ERR_INVALID_ARG
+    o = G.isdc_default_options()
+    o.equation = 1
+    with pytest.raises(G.IsdcError) as e:
+        G.isdc_create(2, 16384, 0.1, 3, 0.05, o)
+    assert e.value.status == G.ISDC_ERR_INVALID_ARG and "levels" in G.isdc_last_error()
 
 
 @pytest.mark.parametrize("struct", ["isdc_options", "isdc_problem", "isdc_slot_info", "isdc_batch_info",

@@ -379,6 +379,71 @@ def test_red_black_run_forms_are_bitwise_identical(fp32):
         assert rel_l2(outs[0][0], ref.per_step_u[0]) <= 1e-12
 
 
+FUSED_CASES = [
+    # ndim, n, smoother, nu1, nu2, fp32 V-cycles
+    (3, 255, RB, 2, 2, False),   # red-only residual; coarse sides 127, 63, 31, 15 ragged against 32 x 8 tiles
+    (3, 127, J, 1, 1, False),    # full residual (27-term full weighting)
+    (3, 255, RB, 2, 2, True),    # colour-split FP32 fine level, then natural FP32 levels
+    (3, 63, J, 1, 2, True),
+    (2, 1023, RB, 1, 1, False),  # 2D tiles, red-only
+    (2, 511, J, 1, 1, False),
+    (2, 1023, RB, 2, 2, True),
+    (2, 255, J, 1, 1, True),
+]
+
+
+@pytest.mark.parametrize("case", FUSED_CASES)
+def test_fused_residual_restriction_is_bitwise_identical(case):
+    """Residual + full weighting in one launch (the residual kept in shared
+    memory, tiles of 32 x 8 coarse points walking z) against the two-launch form
+    (the residual written to device memory and read back): the same expressions
+    in the same order, so three V-cycles agree bit for bit; the FP64 cases are
+    also checked against the oracle's V-cycles."""
+    d, n, sm, nu1, nu2, fp32 = case
+    p = O.Problem(d, n, 0.1, 3, 0.02, smoother=sm, nu1=nu1, nu2=nu2)
+    rng = np.random.default_rng(n * 13 + d)
+    x0, b = rng.standard_normal(p.shape), rng.standard_normal(p.shape)
+    a = 0.02 if d == 2 else 0.004
+    outs = []
+    for fused in (True, False):
+        g = make_gpu(p, vcycle_fp32=fp32, fused_transfer=fused)
+        x = to_dev(x0)
+        g.vcycles(a, x, to_dev(b), 3)
+        outs.append(x.cpu().numpy())
+        g.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    if not fp32:
+        ref = x0.copy()
+        for _ in range(3):
+            ref = O.vcycle(p, a, ref, b)
+        assert np.abs(outs[0] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_fused_transfer_whole_steps_match_two_launch_form():
+    """Whole until-tolerance steps of the 127^3 FP32-V-cycle workload with the
+    fused and the two-launch transfer agree bit for bit (values, sweep counts
+    and residuals)."""
+    n = 127
+    p = O.Problem(3, n, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2, max_sweeps=150)
+    u0 = initial_condition(3, n, seed=44)
+    outs = []
+    for fused in (True, False):
+        g = make_gpu(p, vcycle_fp32=True, fused_transfer=fused)
+        u = to_dev(u0)
+        assert g.step(u, 0, 2) == 0
+        outs.append((u.cpu().numpy(), g.stats(), g.residual()))
+        g.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+    g = make_gpu(p, vcycle_fp32=True)  # default: each level's form chosen by the autotuner
+    kc = g.tuning()["transfer_kc"]
+    assert len(kc) >= 2 and all(k in (0, 4, 8, 16) for k in kc), kc
+    u = to_dev(u0)
+    assert g.step(u, 0, 2) == 0
+    np.testing.assert_array_equal(u.cpu().numpy(), outs[0][0])
+    g.close()
+
+
 def test_red_black_run_option_is_validated():
     import paper_1401_7824_gb300 as G
     p = O.Problem(3, 31, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2)
