@@ -39,7 +39,7 @@ namespace {
 
 thread_local char g_batch_error[512] = "";
 
-enum ListKind { LK_FULL = 0, LK_HALF = 1, LK_CPTS = 2, LK_CELLS = 3 };
+enum ListKind { LK_FULL = 0, LK_HALF = 1, LK_CPTS = 2, LK_CELLS = 3, LK_TILE = 4, LK_KINDS = 5 };
 
 struct Slot {
   int state = ISDC_SLOT_FREE;
@@ -50,10 +50,16 @@ struct Slot {
   void* mem = nullptr;
 };
 
+// Launch shape of the grid-wide phases: threads per block (the point-wise
+// phases' tile; the fused 2D phases' tile is 32 x threads/32 coarse points),
+// blocks per SM, and whether the whole tick is one persistent cooperative
+// launch (fused 2D mode only; blocks per SM from the occupancy calculator)
+// instead of a graph of one launch per phase.  Every shape gives the same
+// result bit for bit, so the autotuner's trial ticks are real sweeps.
 struct Shape {
-  int threads, blocks_per_sm;
+  int threads, blocks_per_sm, persistent;
 };
-const Shape kShapes[] = {{256, 8}, {128, 16}, {512, 4}, {256, 16}, {512, 8}};
+const Shape kShapes[] = {{256, 8, 0}, {128, 16, 0}, {512, 4, 0}, {256, 16, 0}, {128, 8, 0}, {256, 0, 1}, {512, 0, 1}};
 constexpr int kNumShapes = int(sizeof(kShapes) / sizeof(kShapes[0]));
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -62,6 +68,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct isdc_batch {
   int dim = 0, L = 2, Mmax = 0, Lmax = 0, sms = 0, max_side = 0;
+  int fused = 0;  // 2D damped Jacobi: smoother fused into the transfer passes (temporal-blocking depth 1)
   isdc_options opt{};
   size_t budget = 0, used = 0;
   cudaStream_t stream = nullptr;
@@ -78,11 +85,18 @@ struct isdc_batch {
   int shape = 0;         // shape in use
   int tuned = 0;         // 1 once the autotuner has chosen
   int tune_next = 0;     // next shape to try
+  bool tune_warm = false;  // the first tick (every instance's spread) is run but not scored
   double tune_rate[kNumShapes] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   long long ticks = 0;
   long long kernel_launches = 0;   // kernel nodes executed by all ticks
+  double last_tick_bytes = 0.0;    // algorithmic bytes of the last tick (tick_bytes)
   int kernel_nodes[kNumShapes] = {};  // kernel nodes per tick graph
+  // persistent tick: phase table, grid barrier, resident blocks per SM per shape
+  Phase* d_phases = nullptr;
+  int nphases = 0;
+  GridBarrier *d_gb = nullptr, *h_gb = nullptr;
+  int pers_bps[kNumShapes] = {};
   char err[512] = "";
 };
 
@@ -113,10 +127,24 @@ int levels_of(int n) {
 
 size_t pts(int dim, int n) { return dim == 2 ? size_t(n) * n : size_t(n) * n * n; }
 
-int list_index(const isdc_batch* b, int m, int l, int kind) { return ((m * b->Lmax) + l) * 4 + kind; }
-int list_coarse(const isdc_batch* b, int m) { return (b->Mmax - 1) * b->Lmax * 4 + m; }
-int list_spread(const isdc_batch* b) { return (b->Mmax - 1) * b->Lmax * 4 + (b->Mmax - 1); }
-int list_sweep(const isdc_batch* b) { return list_spread(b) + 1; }
+int list_index(const isdc_batch* b, int m, int l, int kind) { return ((m * b->Lmax) + l) * LK_KINDS + kind; }
+int list_coarse(const isdc_batch* b, int m) { return (b->Mmax - 1) * b->Lmax * LK_KINDS + m; }
+int list_bottom(const isdc_batch* b, int m) { return (b->Mmax - 1) * b->Lmax * LK_KINDS + (b->Mmax - 1) + m; }
+int list_spread(const isdc_batch* b) { return (b->Mmax - 1) * b->Lmax * LK_KINDS + 2 * (b->Mmax - 1); }
+// instances with M nodes (2 <= M <= Mmax): those starting a step, all running ones
+int list_spread_m(const isdc_batch* b, int M) { return list_spread(b) + 1 + (M - 2); }
+int list_sweep_m(const isdc_batch* b, int M) { return list_spread(b) + 1 + (b->Mmax - 1) + (M - 2); }
+int bottom_side(int dim) { return dim == 2 ? kBatchBottom2 : kBatchBottom3; }
+int bottom_level(int dim, int n) {  // first level of side <= the bottom threshold
+  int l = 0;
+  while (n > bottom_side(dim)) { n = (n - 1) / 2; ++l; }
+  return l;
+}
+size_t bottom_smem(int dim) {  // 3 FP32 arrays per level from the threshold side down to 3
+  size_t s = 0;
+  for (int n = bottom_side(dim); n >= 3; n = (n - 1) / 2) s += 3 * pts(dim, n) * 4;
+  return s;
+}
 
 // Bytes of device memory one instance needs (node state FP64, hierarchy FP32).
 size_t instance_bytes(const isdc_batch* b, int n, int M) {
@@ -136,41 +164,116 @@ size_t instance_bytes(const isdc_batch* b, int n, int M) {
   return s;
 }
 
-// Rebuild every work list for the current running set and tile size.
-void build_lists(isdc_batch* b, int tile) {
+enum TickMode { MODE_LEGACY = 0, MODE_FUSED2D = 1, MODE_RB_BOTTOM = 2 };
+
+// How a tick runs its V-cycles.  Fused 2D damped Jacobi (V(1, nu2 <= 1)):
+// one fused pass per leg and grid-wide level, the coarse levels in one block
+// per instance.  Red-black Gauss-Seidel: the separate phases on the grid-wide
+// levels, the coarse levels in one block per instance.  Otherwise (and for
+// the unfused Jacobi shapes): every phase of every level as its own pass.
+int tick_mode(const isdc_batch* b, const Shape&) {
+  const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
+  if (!jac) return MODE_RB_BOTTOM;
+  return b->fused ? MODE_FUSED2D : MODE_LEGACY;
+}
+
+// Rebuild every work list for the current running set and launch shape.
+void build_lists(isdc_batch* b, const Shape& sh) {
+  const int tile = sh.threads, ty = sh.threads / 32;
+  const int mode = tick_mode(b, sh);
   for (int q = 0; q < b->nlists; ++q) {
     b->h_lists[q].count = 0;
     b->h_lists[q].total = 0;
     b->h_lists[q].start[0] = 0;
   }
-  auto add = [&](int li, int inst, size_t domain) {
+  auto add_tiles = [&](int li, int inst, int tiles) {
     List& L = b->h_lists[li];
-    const int tiles = int((domain + tile - 1) / tile);
     L.inst[L.count] = inst;
     L.start[L.count] = L.total;
     L.total += tiles;
     L.count += 1;
     L.start[L.count] = L.total;
   };
+  auto add = [&](int li, int inst, size_t domain) { add_tiles(li, inst, int((domain + tile - 1) / tile)); };
   const int dim = b->dim;
   for (int i = 0; i < kMaxInst; ++i) {
     const Slot& S = b->slots[i];
     if (S.state != ISDC_SLOT_RUNNING) continue;
     const size_t N = pts(dim, S.n);
-    if (S.spread_next) add(list_spread(b), i, N);
-    add(list_sweep(b), i, N);
+    if (S.spread_next) {
+      add(list_spread(b), i, N);
+      add(list_spread_m(b, S.M), i, N);
+    }
+    add(list_sweep_m(b, S.M), i, N);
+    // grid-wide levels: every level above the coarsest (separate phases) or
+    // the levels above the per-instance bottom block
+    const int grid_levels = mode == MODE_LEGACY ? S.nlev - 1 : bottom_level(dim, S.n);
     for (int m = 0; m < S.M - 1; ++m) {
       add(list_coarse(b, m), i, dim == 2 ? 9 : 27);
+      add_tiles(list_bottom(b, m), i, 1);
       int side = S.n;
       for (int l = 0; l < S.nlev - 1; ++l) {
         const int sc = (side - 1) / 2;
-        add(list_index(b, m, l, LK_FULL), i, pts(dim, side));
-        add(list_index(b, m, l, LK_HALF), i, size_t((side + 1) / 2) * (dim == 2 ? side : size_t(side) * side));
-        add(list_index(b, m, l, LK_CPTS), i, pts(dim, sc));
-        add(list_index(b, m, l, LK_CELLS), i, pts(dim, sc + 1));
+        if (l == 0 || l < grid_levels) add(list_index(b, m, l, LK_FULL), i, pts(dim, side));  // level 0: rhs, update
+        if (l < grid_levels) {
+          add(list_index(b, m, l, LK_HALF), i, size_t((side + 1) / 2) * (dim == 2 ? side : size_t(side) * side));
+          add(list_index(b, m, l, LK_CPTS), i, pts(dim, sc));
+          add(list_index(b, m, l, LK_CELLS), i, pts(dim, sc + 1));
+          add_tiles(list_index(b, m, l, LK_TILE), i, ((sc + kFtX - 1) / kFtX) * ((sc + ty - 1) / ty));
+        }
         side = sc;
       }
     }
+  }
+}
+
+// Algorithmic bytes of one tick for the running set (each phase reads each
+// input stream once and writes each output once; FP64 node state, FP32
+// levels).  Used for the engine's roofline.
+double tick_bytes(const isdc_batch* b, const Shape& sh) {
+  const int mode = tick_mode(b, sh), dim = b->dim;
+  const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
+  const int nu1 = b->opt.nu1, nu2 = b->opt.nu2;
+  double total = 0.0;
+  for (int i = 0; i < kMaxInst; ++i) {
+    const Slot& S = b->slots[i];
+    if (S.state != ISDC_SLOT_RUNNING) continue;
+    const double N = double(pts(dim, S.n));
+    const int M = S.M;
+    double t = (3.0 * M - 1.0) * 8.0 * N;                 // sweep end
+    if (S.spread_next) t += 2.0 * M * 8.0 * N;            // spread
+    const int grid_levels = mode == MODE_LEGACY ? S.nlev - 1 : bottom_level(dim, S.n);
+    double cyc = 0.0;                                     // one V-cycle, FP32
+    int side = S.n;
+    for (int l = 0; l < grid_levels; ++l) {
+      const double Nl = double(pts(dim, side)), Nc = double(pts(dim, (side - 1) / 2));
+      if (mode == MODE_FUSED2D) {
+        cyc += 4.0 * (3.0 * Nl + Nc) + (l > 0 ? 0.0 : 4.0 * Nl);  // down: x (not from zero), b, t; b_c
+        cyc += 4.0 * ((nu2 ? 3.0 : 2.0) * Nl + Nc);                // up: t, b, x; e_c
+      } else if (!jac) {
+        cyc += 4.0 * ((nu1 + nu2) * 2.0 * 1.5 * Nl + 2.0 * Nl + (0.5 * Nl + Nc) + (Nl + Nc));
+      } else {
+        cyc += 4.0 * ((nu1 + nu2) * 3.0 * Nl + 3.0 * Nl + (Nl + Nc) + (Nl + Nc));
+      }
+      side = (side - 1) / 2;
+    }
+    if (mode != MODE_LEGACY) cyc += 4.0 * 3.0 * double(pts(dim, side));  // bottom block: b, x in, x out
+    t += (M - 1) * (28.0 * N + 20.0 * N + b->L * cyc);                    // rhs, update, L cycles per node
+    total += t;
+  }
+  return total;
+}
+
+template <int DIM>
+void launch_sweep_end(int M, dim3 grid, dim3 blk, cudaStream_t st, const Inst* I, const List* L, int reaction,
+                      unsigned long long* rbits) {
+  switch (M) {
+    case 2: kb_sweep_end<DIM, 2><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
+    case 3: kb_sweep_end<DIM, 3><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
+    case 4: kb_sweep_end<DIM, 4><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
+    case 5: kb_sweep_end<DIM, 5><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
+    case 6: kb_sweep_end<DIM, 6><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
+    default: kb_sweep_end<DIM, 7><<<grid, blk, 0, st>>>(I, L, reaction, rbits); break;
   }
 }
 
@@ -184,71 +287,181 @@ void record_tick(isdc_batch* b, const Shape& sh) {
   const int reaction = b->opt.reaction;
   const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
   const int nu1 = b->opt.nu1, nu2 = b->opt.nu2;
+  const float omega = float(b->opt.omega);
+  const int mode = tick_mode(b, sh);
+  const int ty = sh.threads / 32;
   const int par = (nu1 + nu2) & 1;  // Jacobi: a level's iterate ends in t after an odd sweep count
   cudaMemsetAsync(b->d_rbits, 0, sizeof(unsigned long long) * kMaxInst, st);
   kb_spread<DIM><<<grid, blk, 0, st>>>(I, Ls + list_spread(b), reaction);
-  kb_sweep_end<DIM><<<grid, blk, 0, st>>>(I, Ls + list_spread(b), reaction, b->d_dummy);
+  for (int M = 2; M <= b->Mmax; ++M)
+    launch_sweep_end<DIM>(M, grid, blk, st, I, Ls + list_spread_m(b, M), reaction, b->d_dummy);
   for (int m = 0; m < b->Mmax - 1; ++m) {
     const List* full0 = Ls + list_index(b, m, 0, LK_FULL);
     kb_rhs<DIM><<<grid, blk, 0, st>>>(I, full0, m, reaction);
     int loc0 = 0;  // level-0 error: in x (0) or t (1)
-    for (int c = 0; c < b->L; ++c) {
-      for (int l = 0; l < b->Lmax - 1; ++l) {
-        const bool zero = l > 0 || c == 0;
-        int loc = l == 0 ? loc0 : 0;
-        for (int s = 0; s < nu1; ++s) {
-          if (jac) {
-            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, float(b->opt.omega),
-                                                 loc, zero && s == 0);
-            loc ^= 1;
+    if (mode != MODE_LEGACY) {
+      const int Lg = bottom_level(DIM, b->max_side);
+      for (int c = 0; c < b->L; ++c) {
+        for (int l = 0; l < Lg; ++l) {
+          const int zero = (l > 0 || c == 0) ? 1 : 0;
+          if (mode == MODE_FUSED2D) {
+            const List* tl = Ls + list_index(b, m, l, LK_TILE);
+            if (ty == 4) kb_down2<4><<<grid, 128, 0, st>>>(I, tl, m, l, omega, zero);
+            else if (ty == 8) kb_down2<8><<<grid, 256, 0, st>>>(I, tl, m, l, omega, zero);
+            else kb_down2<16><<<grid, 512, 0, st>>>(I, tl, m, l, omega, zero);
           } else {
-            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, zero && s == 0);
-            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+            const List* half = Ls + list_index(b, m, l, LK_HALF);
+            for (int s = 0; s < nu1; ++s) {
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 0, zero && s == 0);
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 1, 0);
+            }
+            kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, half, m, l, 0);
+            kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
           }
         }
-        if (!jac)
-          kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0);
-        else
-          kb_residual<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, loc);
-        if (!jac)
-          kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
-        else
-          kb_restrict<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
-      }
-      // every instance's coarsest grid; the result goes where a smoothed level's
-      // iterate would be (t after an odd Jacobi sweep count) so the prolongation
-      // reads one location for all instances
-      kb_coarse<DIM><<<grid, blk, 0, st>>>(I, Ls + list_coarse(b, m), m, jac ? par : 0);
-      for (int l = b->Lmax - 2; l >= 0; --l) {
-        int loc = jac ? ((l == 0 ? loc0 : 0) ^ (nu1 & 1)) : 0;
-        const List* cells = Ls + list_index(b, m, l, LK_CELLS);
-        if (jac)
-          kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, loc, par);
-        else if (nu2 >= 1)  // a red half sweep follows and overwrites the red points
-          kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
-        else
-          kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
-        for (int s = 0; s < nu2; ++s) {
-          if (jac) {
-            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, float(b->opt.omega),
-                                                 loc, 0);
-            loc ^= 1;
+        kb_bottom<DIM><<<kMaxInst, kBottomThreads, bottom_smem(DIM), st>>>(I, Ls + list_bottom(b, m), m, c > 0 ? 1 : 0,
+                                                                          jac ? 0 : 1, nu1, nu2, omega);
+        for (int l = Lg - 1; l >= 0; --l) {
+          if (mode == MODE_FUSED2D) {
+            const List* tl = Ls + list_index(b, m, l, LK_TILE);
+            if (ty == 4) kb_up2<4><<<grid, 128, 0, st>>>(I, tl, m, l, omega, nu2);
+            else if (ty == 8) kb_up2<8><<<grid, 256, 0, st>>>(I, tl, m, l, omega, nu2);
+            else kb_up2<16><<<grid, 512, 0, st>>>(I, tl, m, l, omega, nu2);
           } else {
-            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, 0);
-            kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+            const List* half = Ls + list_index(b, m, l, LK_HALF);
+            const List* cells = Ls + list_index(b, m, l, LK_CELLS);
+            if (nu2 >= 1) kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+            else kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+            for (int s = 0; s < nu2; ++s) {
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 0, 0);
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 1, 0);
+            }
           }
         }
       }
-      if (jac) loc0 ^= par;
+    } else {
+      for (int c = 0; c < b->L; ++c) {
+        for (int l = 0; l < b->Lmax - 1; ++l) {
+          const bool zero = l > 0 || c == 0;
+          int loc = l == 0 ? loc0 : 0;
+          for (int s = 0; s < nu1; ++s) {
+            if (jac) {
+              kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, omega, loc,
+                                                   zero && s == 0);
+              loc ^= 1;
+            } else {
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, zero && s == 0);
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+            }
+          }
+          if (!jac)
+            kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0);
+          else
+            kb_residual<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, loc);
+          if (!jac)
+            kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+          else
+            kb_restrict<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+        }
+        // every instance's coarsest grid; the result goes where a smoothed level's
+        // iterate would be (t after an odd Jacobi sweep count) so the prolongation
+        // reads one location for all instances
+        kb_coarse<DIM><<<grid, blk, 0, st>>>(I, Ls + list_coarse(b, m), m, jac ? par : 0);
+        for (int l = b->Lmax - 2; l >= 0; --l) {
+          int loc = jac ? ((l == 0 ? loc0 : 0) ^ (nu1 & 1)) : 0;
+          const List* cells = Ls + list_index(b, m, l, LK_CELLS);
+          if (jac)
+            kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, loc, par);
+          else if (nu2 >= 1)  // a red half sweep follows and overwrites the red points
+            kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+          else
+            kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+          for (int s = 0; s < nu2; ++s) {
+            if (jac) {
+              kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, omega, loc, 0);
+              loc ^= 1;
+            } else {
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, 0);
+              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
+            }
+          }
+        }
+        if (jac) loc0 ^= par;
+      }
     }
     kb_update<DIM><<<grid, blk, 0, st>>>(I, full0, m, loc0);
   }
-  kb_sweep_end<DIM><<<grid, blk, 0, st>>>(I, Ls + list_sweep(b), reaction, b->d_rbits);
+  for (int M = 2; M <= b->Mmax; ++M)
+    launch_sweep_end<DIM>(M, grid, blk, st, I, Ls + list_sweep_m(b, M), reaction, b->d_rbits);
   cudaMemcpyAsync(b->h_rbits, b->d_rbits, sizeof(unsigned long long) * kMaxInst, cudaMemcpyDeviceToHost, st);
 }
 
+// The fused 2D tick as a phase table for the persistent launch: the same
+// phases, lists and order as record_tick's fused mode.
+isdc_status build_phases(isdc_batch* b) {
+  if (b->d_phases) return ISDC_OK;
+  std::vector<Phase> ph;
+  auto add = [&](int kind, int list, int m, int l, int arg, int arg2) { ph.push_back(Phase{kind, list, m, l, arg, arg2}); };
+  add(PH_SPREAD, list_spread(b), 0, 0, 0, 0);
+  for (int M = 2; M <= b->Mmax; ++M) add(PH_SWEEP_END, list_spread_m(b, M), 0, 0, M, 0);
+  const int Lg = bottom_level(2, b->max_side);
+  for (int m = 0; m < b->Mmax - 1; ++m) {
+    add(PH_RHS, list_index(b, m, 0, LK_FULL), m, 0, 0, 0);
+    for (int c = 0; c < b->L; ++c) {
+      for (int l = 0; l < Lg; ++l) add(PH_DOWN, list_index(b, m, l, LK_TILE), m, l, (l > 0 || c == 0) ? 1 : 0, 0);
+      add(PH_BOTTOM, list_bottom(b, m), m, 0, c > 0 ? 1 : 0, 0);
+      for (int l = Lg - 1; l >= 0; --l) add(PH_UP, list_index(b, m, l, LK_TILE), m, l, 0, 0);
+    }
+    add(PH_UPDATE, list_index(b, m, 0, LK_FULL), m, 0, 0, 0);
+  }
+  for (int M = 2; M <= b->Mmax; ++M) add(PH_SWEEP_END, list_sweep_m(b, M), 0, 0, M, 1);
+  B_TRY(b, cudaMalloc(&b->d_phases, ph.size() * sizeof(Phase)));
+  B_TRY(b, cudaMemcpy(b->d_phases, ph.data(), ph.size() * sizeof(Phase), cudaMemcpyHostToDevice));
+  b->nphases = int(ph.size());
+  return ISDC_OK;
+}
+
+// One tick as one cooperative launch; *unusable when the shape cannot be
+// resident (the tuner then skips it).
+isdc_status launch_persistent(isdc_batch* b, int shape, bool* unusable) {
+  const Shape& sh = kShapes[shape];
+  *unusable = false;
+  isdc_status st = build_phases(b);
+  if (st != ISDC_OK) return st;
+  const void* fn = sh.threads == 512 ? reinterpret_cast<const void*>(kb_tick2<16>)
+                   : sh.threads == 128 ? reinterpret_cast<const void*>(kb_tick2<4>)
+                                       : reinterpret_cast<const void*>(kb_tick2<8>);
+  const size_t smem = bottom_smem(2);
+  if (b->pers_bps[shape] == 0) {
+    int nb = 0;
+    B_TRY(b, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    B_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.threads, smem));
+    b->pers_bps[shape] = nb > 0 ? nb : -1;
+  }
+  if (b->pers_bps[shape] < 0) {
+    *unusable = true;
+    return ISDC_OK;
+  }
+  const dim3 grid(b->pers_bps[shape] * b->sms), blk(sh.threads);
+  const Inst* insts = b->d_insts;
+  const List* lists = b->d_lists;
+  const Phase* phases = b->d_phases;
+  int nph = b->nphases, reaction = b->opt.reaction, nu1 = b->opt.nu1, nu2 = b->opt.nu2;
+  float omega = float(b->opt.omega);
+  unsigned long long *rbits = b->d_rbits, *scratch = b->d_dummy;
+  GridBarrier* gb = b->d_gb;
+  void* args[] = {&insts, &lists, &phases, &nph, &reaction, &omega, &nu1, &nu2, &rbits, &scratch, &gb};
+  B_TRY(b, cudaMemsetAsync(b->d_rbits, 0, sizeof(unsigned long long) * kMaxInst, b->stream));
+  B_TRY(b, cudaMemsetAsync(b->d_gb, 0, sizeof(GridBarrier), b->stream));
+  B_TRY(b, cudaLaunchCooperativeKernel(fn, grid, blk, args, smem, b->stream));
+  B_TRY(b, cudaMemcpyAsync(b->h_rbits, b->d_rbits, sizeof(unsigned long long) * kMaxInst, cudaMemcpyDeviceToHost,
+                           b->stream));
+  B_TRY(b, cudaMemcpyAsync(b->h_gb, b->d_gb, sizeof(GridBarrier), cudaMemcpyDeviceToHost, b->stream));
+  return ISDC_OK;
+}
+
 isdc_status capture(isdc_batch* b, int shape) {
-  if (b->exec[shape]) return ISDC_OK;
+  if (b->exec[shape] || kShapes[shape].persistent) return ISDC_OK;
   cudaGraph_t g = nullptr;
   B_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   if (b->dim == 2) record_tick<2>(b, kShapes[shape]); else record_tick<3>(b, kShapes[shape]);
@@ -279,6 +492,7 @@ void fill_instance(isdc_batch* b, int slot, int n, double nu, int M, double dt, 
   I.n = n;
   I.M = M;
   I.nlev = levels_of(n);
+  I.lb = bottom_level(dim, n);
   I.nu_h2 = nu / (h * h);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -331,7 +545,8 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   if (!out) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (ndim != 2 && ndim != 3) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "ndim must be 2 or 3");
-  if (max_side < 7 || ((max_side + 1) & max_side) != 0 || (ndim == 3 && max_side > 1289) || max_side > 46339)
+  if (max_side < 7 || ((max_side + 1) & max_side) != 0 || (ndim == 3 && max_side > 1289) ||
+      max_side > (int64_t(1) << (kMaxLevels + 1)) - 1)
     return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_side must be 2^j - 1 >= 7 (got %lld)", (long long)max_side);
   if (max_M < 2 || max_M > kMaxM) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_M must be in [2, %d]", kMaxM);
   if (n_vcycles < 1 || n_vcycles > 16) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "n_vcycles must be in [1, 16]");
@@ -339,9 +554,13 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   if (opt) o = *opt; else isdc_default_options(&o);
   if (o.smoother != ISDC_SMOOTHER_JACOBI && o.smoother != ISDC_SMOOTHER_RBGS)
     return bfail(nullptr, ISDC_ERR_INVALID_ARG, "unknown smoother");
+  if (o.smoother == ISDC_SMOOTHER_JACOBI && !(o.omega > 0 && o.omega <= 1))
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "the Jacobi damping omega must be in (0, 1]");
   if (o.nu1 < 1 || o.nu2 < 0 || o.nu1 > 8 || o.nu2 > 8)
     return bfail(nullptr, ISDC_ERR_INVALID_ARG, "the batch engine needs 1 <= nu1 <= 8 and 0 <= nu2 <= 8");
   if (o.max_sweeps < 1) return bfail(nullptr, ISDC_ERR_INVALID_ARG, "max_sweeps must be >= 1");
+  if (o.temporal_blocking < -1 || o.temporal_blocking > 1)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "the batch engine's temporal_blocking must be -1, 0 or 1");
   isdc_batch* b = new isdc_batch();
   b->dim = ndim;
   b->L = n_vcycles;
@@ -350,8 +569,14 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   b->Lmax = levels_of(int(max_side));
   b->opt = o;
   b->opt.vcycle_fp32 = 1;
+  // temporal-blocking depth of the 2D damped-Jacobi V(1, nu2 <= 1) cycles: 1 (the
+  // default, option -1 or 1) fuses the sweep into the transfer passes, 0 keeps
+  // separate phases; the two round differently, so the depth is fixed for the
+  // engine's life
+  b->fused = (ndim == 2 && o.smoother == ISDC_SMOOTHER_JACOBI && o.nu1 == 1 && o.nu2 <= 1 &&
+              o.temporal_blocking != 0) ? 1 : 0;
   b->budget = hbm_budget_bytes;
-  b->nlists = (max_M - 1) * b->Lmax * 4 + (max_M - 1) + 2;
+  b->nlists = (max_M - 1) * b->Lmax * LK_KINDS + 2 * (max_M - 1) + 1 + 2 * (max_M - 1);
   auto bail = [&](isdc_status st) {
     snprintf(g_batch_error, sizeof g_batch_error, "%s", b->err);
     isdc_batch_destroy(b);
@@ -385,6 +610,11 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   CB(cudaMalloc(&b->d_rbits, sizeof(unsigned long long) * kMaxInst));
   CB(cudaMalloc(&b->d_dummy, sizeof(unsigned long long) * kMaxInst));
   CB(cudaMallocHost(&b->h_rbits, sizeof(unsigned long long) * kMaxInst));
+  CB(cudaMalloc(&b->d_gb, sizeof(GridBarrier)));
+  CB(cudaMallocHost(&b->h_gb, sizeof(GridBarrier)));
+  std::memset(b->h_gb, 0, sizeof(GridBarrier));
+  CB(cudaFuncSetAttribute(kb_bottom<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bottom_smem(2))));
+  CB(cudaFuncSetAttribute(kb_bottom<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bottom_smem(3))));
   CB(cudaEventCreate(&b->ev0));
   CB(cudaEventCreate(&b->ev1));
 #undef CB
@@ -407,6 +637,9 @@ ISDC_API void isdc_batch_destroy(isdc_batch* b) {
   cudaFree(b->d_rbits);
   cudaFree(b->d_dummy);
   cudaFreeHost(b->h_rbits);
+  cudaFree(b->d_gb);
+  cudaFreeHost(b->h_gb);
+  cudaFree(b->d_phases);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -476,20 +709,53 @@ ISDC_API isdc_status isdc_batch_tick(isdc_batch* b, int* running_out, int* finis
     }
   int finished = 0;
   if (running) {
-    const int shape = b->tuned ? b->shape : b->tune_next;
+    // the persistent shapes serve the fused 2D mode only; the tuner skips them otherwise
+    while (!b->tuned && kShapes[b->tune_next].persistent && tick_mode(b, kShapes[b->tune_next]) != MODE_FUSED2D) {
+      b->tune_rate[b->tune_next] = 0.0;
+      if (++b->tune_next == kNumShapes) break;
+    }
+    if (!b->tuned && b->tune_next == kNumShapes) {
+      int best = 0;
+      for (int s = 1; s < kNumShapes; ++s)
+        if (b->tune_rate[s] > b->tune_rate[best]) best = s;
+      b->shape = best;
+      b->tuned = 1;
+    }
+    int shape = b->tuned ? b->shape : b->tune_next;
     isdc_status st = capture(b, shape);
     if (st != ISDC_OK) return st;
-    build_lists(b, kShapes[shape].threads);
+    build_lists(b, kShapes[shape]);
+    b->last_tick_bytes = tick_bytes(b, kShapes[shape]);
     B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice, b->stream));
     B_TRY(b, cudaEventRecord(b->ev0, b->stream));
-    B_TRY(b, cudaGraphLaunch(b->exec[shape], b->stream));
-    b->kernel_launches += b->kernel_nodes[shape];
+    bool skip = false;
+    const int tried = shape;
+    if (kShapes[shape].persistent) {
+      if ((st = launch_persistent(b, shape, &skip)) != ISDC_OK) return st;
+      if (skip) {  // cannot be resident: take the first graph shape for this tick
+        shape = 0;
+        if ((st = capture(b, shape)) != ISDC_OK) return st;
+        build_lists(b, kShapes[shape]);
+        B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice,
+                                 b->stream));
+      } else {
+        b->kernel_launches += 1;
+      }
+    }
+    if (!kShapes[shape].persistent) {
+      B_TRY(b, cudaGraphLaunch(b->exec[shape], b->stream));
+      b->kernel_launches += b->kernel_nodes[shape];
+    }
     B_TRY(b, cudaEventRecord(b->ev1, b->stream));
     B_TRY(b, cudaStreamSynchronize(b->stream));
+    if (kShapes[shape].persistent && b->h_gb->err)
+      return bfail(b, ISDC_ERR_CUDA, "a grid barrier of the persistent tick waited longer than its limit");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
-    if (!b->tuned) {  // autotuner: one real tick per launch shape, keep the fastest
-      b->tune_rate[shape] = dofs / std::max(ms, 1e-3f);
+    if (!b->tuned && !b->tune_warm) {
+      b->tune_warm = true;  // warm-up tick: not scored, the same shape is tried again next tick
+    } else if (!b->tuned) {  // autotuner: one real tick per launch shape, keep the fastest
+      b->tune_rate[tried] = skip ? 0.0 : dofs / std::max(ms, 1e-3f);
       if (++b->tune_next == kNumShapes) {
         int best = 0;
         for (int s = 1; s < kNumShapes; ++s)
@@ -576,6 +842,13 @@ ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info
   info->tuned = b->tuned;
   info->threads_per_block = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].threads;
   info->blocks_per_sm = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].blocks_per_sm;
+  info->fused = tick_mode(b, kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes]) == MODE_FUSED2D;
+  {
+    const int sh = b->tuned ? b->shape : b->tune_next % kNumShapes;
+    info->kernels_per_tick = kShapes[sh].persistent ? 1 : b->kernel_nodes[sh];
+    if (kShapes[sh].persistent) info->blocks_per_sm = b->pers_bps[sh];
+  }
+  info->bytes_last_tick = b->last_tick_bytes;
   int r = 0;
   for (int i = 0; i < kMaxInst; ++i) r += b->slots[i].state == ISDC_SLOT_RUNNING;
   info->running = r;

@@ -24,6 +24,7 @@ struct Level {
 // Everything a kernel needs about one instance (device-resident table).
 struct Inst {
   int n, M, nlev;
+  int lb;                             // first level handled by the per-instance bottom block
   double nu_h2;                       // nu / h^2 on the fine grid
   double* U;                          // M node arrays (node-major)
   double* F;                          // f(u_m), M arrays
@@ -91,7 +92,7 @@ __device__ __forceinline__ int npts(int n) { return DIM == 2 ? n * n : n * n * n
 // Start of a step: u = u_{M-1} of the previous step (or the admitted initial
 // value), spread to every node; f_m = f(u).  u_{M-1} itself is only read.
 template <int DIM>
-__global__ void kb_spread(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction) {
+__device__ __forceinline__ void pb_spread(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction) {
   const List& L = *list;
   BATCH_LOOP(L)
     const int n = I.n;
@@ -116,7 +117,8 @@ __global__ void kb_spread(const Inst* __restrict__ insts, const List* __restrict
 // implicit terms of b and of (I - a L_h) u_{m+1}^k cancel:
 //   r = u_m^{k+1} + dt_m f^E(u_m^{k+1}) + C'_m.
 template <int DIM>
-__global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int reaction) {
+__device__ __forceinline__ void pb_rhs(const Inst* __restrict__ insts, const List* __restrict__ list, int m,
+                                       int reaction) {
   const List& L = *list;
   BATCH_LOOP(L)
     const int n = I.n;
@@ -135,7 +137,8 @@ __global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ 
 
 // u_{m+1} += e (FP32 correction from level 0, in x or in t).
 template <int DIM>
-__global__ void kb_update(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int from_t) {
+__device__ __forceinline__ void pb_update(const Inst* __restrict__ insts, const List* __restrict__ list, int m,
+                                          int from_t) {
   const List& L = *list;
   BATCH_LOOP(L)
     const int n = I.n;
@@ -146,54 +149,47 @@ __global__ void kb_update(const Inst* __restrict__ insts, const List* __restrict
 }
 
 // End of a sweep: f_{M-1}, the max-norm SDC residual (Sec. 3) into
-// rbits[instance] and the next sweep's C'_m.
-template <int DIM>
-__global__ void kb_sweep_end(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction,
-                             unsigned long long* __restrict__ rbits) {
+// rbits[instance] and the next sweep's C'_m, for the listed instances with M
+// nodes (one list and one compiled kernel per node count).
+template <int DIM, int M>
+__device__ __forceinline__ void pb_sweep_end(const Inst* __restrict__ insts, const List* __restrict__ list,
+                                             int reaction, unsigned long long* __restrict__ rbits) {
+  static_assert(M >= 2 && M <= kMaxM, "node count out of range");
   const List& L = *list;
   BATCH_LOOP(L)
-    const int n = I.n, M = I.M;
+    const int n = I.n;
     unsigned long long rb = 0;
     if (q < npts<DIM>(n)) {
       int i, j, k;
       decode<DIM>(q, n, i, j, k);
       const size_t N = size_t(npts<DIM>(n));
-      double u[kMaxM], f[kMaxM], fe[kMaxM], qf[kMaxM];
+      double u[M], f[M], qf[M];
 #pragma unroll
-      for (int mm = 0; mm < kMaxM; ++mm)
-        if (mm < M) {
-          u[mm] = I.U[mm * N + q];
-          fe[mm] = reaction_term(reaction, u[mm]);
-        }
+      for (int mm = 0; mm < M; ++mm) u[mm] = I.U[mm * N + q];
+#pragma unroll
+      for (int mm = 0; mm < M - 1; ++mm) f[mm] = I.F[mm * N + q];
       const double* ul = I.U + size_t(M - 1) * N;
-      const double flast = fma(I.nu_h2, fma(-double(2 * DIM), ul[q], nbsum<double, DIM>(ul, i, j, k, n, q)),
-                               reaction_term(reaction, ul[q]));
+      const double flast = fma(I.nu_h2, fma(-double(2 * DIM), u[M - 1], nbsum<double, DIM>(ul, i, j, k, n, q)),
+                               reaction_term(reaction, u[M - 1]));
       I.F[size_t(M - 1) * N + q] = flast;
+      f[M - 1] = flast;
 #pragma unroll
-      for (int mm = 0; mm < kMaxM; ++mm) {
-        if (mm < M - 1) f[mm] = I.F[mm * N + q];
-        else if (mm == M - 1) f[mm] = flast;
+      for (int mm = 1; mm < M; ++mm) {
+        double acc = I.dtQ[mm][0] * f[0];
+#pragma unroll
+        for (int jj = 1; jj < M; ++jj) acc = fma(I.dtQ[mm][jj], f[jj], acc);
+        qf[mm] = acc;
+        const unsigned long long bits =
+            (unsigned long long)__double_as_longlong((u[0] - u[mm]) + acc) & 0x7fffffffffffffffull;
+        rb = bits > rb ? bits : rb;
       }
 #pragma unroll
-      for (int mm = 1; mm < kMaxM; ++mm)
-        if (mm < M) {
-          double acc = I.dtQ[mm][0] * f[0];
-#pragma unroll
-          for (int jj = 1; jj < kMaxM; ++jj)
-            if (jj < M) acc = fma(I.dtQ[mm][jj], f[jj], acc);
-          qf[mm] = acc;
-          const unsigned long long bits =
-              (unsigned long long)__double_as_longlong((u[0] - u[mm]) + acc) & 0x7fffffffffffffffull;
-          rb = bits > rb ? bits : rb;
-        }
-#pragma unroll
-      for (int mm = 0; mm < kMaxM - 1; ++mm)
-        if (mm < M - 1) {
-          const double sf = mm == 0 ? qf[1] : qf[mm + 1] - qf[mm];
-          I.C[mm * N + q] = fma(-I.dtm[mm], fe[mm], sf) - u[mm + 1];
-        }
+      for (int mm = 0; mm < M - 1; ++mm) {
+        const double sf = mm == 0 ? qf[1] : qf[mm + 1] - qf[mm];
+        I.C[mm * N + q] = fma(-I.dtm[mm], reaction_term(reaction, u[mm]), sf) - u[mm + 1];
+      }
     }
-    // all threads of the block work on the same instance: block max, one atomic
+    // all threads of the block work on the same instance: warp max, one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long w = __shfl_xor_sync(0xffffffffu, rb, o);
@@ -301,6 +297,395 @@ __global__ void kb_coarse(const Inst* __restrict__ insts, const List* __restrict
     for (int c = 0; c < Np; ++c) acc = fmaf(A[q * Np + c], V.b[c], acc);
     (dst_t ? V.t : V.x)[q] = acc;
   BATCH_END
+}
+
+// ---------------------------------------------------------------------------
+// Coarse levels of every listed instance in one block each: the bottom of the
+// V-cycle (sides <= kBatchBottom2 in 2D, <= kBatchBottom3 in 3D) on the
+// instance's own level arrays, with the single-instance path's shared-memory
+// V-cycle (bottom_vcycle).  One tile = one instance; blockDim = kBottomThreads.
+// ---------------------------------------------------------------------------
+constexpr int kBatchBottom2 = 63, kBatchBottom3 = 15;
+
+template <int DIM>
+__device__ __forceinline__ void pb_bottom(const Inst* __restrict__ insts, const List* __restrict__ list, int m,
+                                          int load_x, int smoother, int nu1, int nu2, float omega,
+                                          unsigned char* smem_raw) {
+  const List& L = *list;
+  for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
+    const Inst& I = insts[L.inst[find_entry(L, g)]];
+    BottomParams<float> P;
+    P.nlev = I.nlev - I.lb;
+    for (int q = 0; q < P.nlev; ++q) {
+      P.side[q] = I.lev[I.lb + q].n;
+      P.kappa[q] = I.kappa[m][I.lb + q];
+      P.rscale[q] = q + 1 < P.nlev ? I.wscale[m][I.lb + q] : 0.f;
+    }
+    P.smoother = smoother;
+    P.nu1 = nu1;
+    P.nu2 = nu2;
+    P.omega = omega;
+    P.Ainv = I.ainv + size_t(m) * (DIM == 2 ? 81 : 729);
+    const Level& V = I.lev[I.lb];
+    bottom_vcycle<float, DIM>(P, V.b, V.x, load_x && I.lb == 0, smem_raw);
+    __syncthreads();  // shared memory is reused by the block's next instance
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2D damped-Jacobi V(1, nu2 <= 1) cycles with the smoother fused into the
+// transfer passes.  A tile is kFtX x TY coarse points of level l+1 and owns
+// the fine points [2 I0, 2 I0 + 2 kFtX) x [2 J0, 2 J0 + 2 TY) of level l (the
+// tiles of a level cover its grid, whose side is 2 nc + 1).
+//   down (l): t_l = J(x_l) (one sweep, x_l = 0 on zero guesses) on the tile
+//     and a ring of one, the residual of t_l on the fine points that full
+//     weighting needs, b_{l+1} = FW(r) on the tile's coarse points; writes t_l
+//     on the owned points and b_{l+1}: one pass over level l where the
+//     separate phases make three.
+//   up (l): v = t_l + P e_{l+1} on the tile and a ring of one (e_{l+1} in
+//     x_{l+1}), x_l = J(v) on the owned points (nu2 = 1) or x_l = v (nu2 = 0).
+// Every value is formed by the same expressions as the separate phases.
+// ---------------------------------------------------------------------------
+constexpr int kFtX = 32;
+
+__device__ __forceinline__ void fused_tile_origin(int q, int nc, int ty, int& I0, int& J0) {
+  const int ntx = (nc + kFtX - 1) / kFtX;
+  I0 = (q % ntx) * kFtX;
+  J0 = (q / ntx) * ty;
+}
+
+// Tile loads: a thread loads its share of the tile's input region into
+// registers (K = COUNT / NTH values, all issued before the first is stored)
+// and then stores them to shared memory.  (Issuing the next tile's loads
+// during the current tile's compute was measured slower: these passes are
+// bound by instruction issue, not by load latency.)
+template <int COUNT, int NTH, class Get>
+__device__ __forceinline__ void tile_load(float (&v)[(COUNT + NTH - 1) / NTH], int tid, const Get& get) {
+#pragma unroll
+  for (int k = 0; k < (COUNT + NTH - 1) / NTH; ++k) {
+    const int p = tid + k * NTH;
+    v[k] = p < COUNT ? get(p) : 0.f;
+  }
+}
+template <int COUNT, int NTH>
+__device__ __forceinline__ void tile_store(float* __restrict__ dst, const float (&v)[(COUNT + NTH - 1) / NTH],
+                                           int tid) {
+#pragma unroll
+  for (int k = 0; k < (COUNT + NTH - 1) / NTH; ++k) {
+    const int p = tid + k * NTH;
+    if (p < COUNT) dst[p] = v[k];
+  }
+}
+
+// Geometry of work-list tile g of level l (coarse side nc = side of level l+1).
+struct FTile {
+  const Inst* I;
+  int n, nc, I0, J0;
+};
+__device__ __forceinline__ FTile fused_tile(const Inst* __restrict__ insts, const List& L, int g, int l, int ty) {
+  const int e = find_entry(L, g);
+  FTile t;
+  t.I = &insts[L.inst[e]];
+  t.n = t.I->lev[l].n;
+  t.nc = t.I->lev[l + 1].n;
+  fused_tile_origin(g - L.start[e], t.nc, ty, t.I0, t.J0);
+  return t;
+}
+
+template <int TY>
+__device__ __forceinline__ void pb_down2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l,
+                                         float omega, int zero) {
+  constexpr int NTH = 32 * TY;
+  constexpr int FX = 2 * kFtX, FY = 2 * TY;
+  constexpr int XW = FX + 5, XH = FY + 5;  // x on fine offsets [-2, FX + 2]
+  constexpr int SW = FX + 3, SH = FY + 3;  // b and the smoothed iterate on [-1, FX + 1]
+  constexpr int RW = FX + 1, RH = FY + 1;  // residual on [0, FX]
+  __shared__ float sx[XH][XW], sb[SH][SW], st[SH][SW], sr[RH][RW];
+  const List& L = *list;
+  const int tid = threadIdx.x;
+  float vx[(XH * XW + NTH - 1) / NTH], vb[(SH * SW + NTH - 1) / NTH];
+  auto load = [&](int g) {
+    const FTile t = fused_tile(insts, L, g, l, TY);
+    const int n = t.n, fi0 = 2 * t.I0, fj0 = 2 * t.J0;
+    const float* __restrict__ fx = t.I->lev[l].x;
+    const float* __restrict__ fb = t.I->lev[l].b;
+    if (!zero)
+      tile_load<XH * XW, NTH>(vx, tid, [&](int p) {
+        const int r = p / XW, c = p - r * XW, i = fi0 - 2 + c, j = fj0 - 2 + r;
+        return (i >= 0 && i < n && j >= 0 && j < n) ? fx[i + n * j] : 0.f;
+      });
+    tile_load<SH * SW, NTH>(vb, tid, [&](int p) {
+      const int r = p / SW, c = p - r * SW, i = fi0 - 1 + c, j = fj0 - 1 + r;
+      return (i >= 0 && i < n && j >= 0 && j < n) ? fb[i + n * j] : 0.f;
+    });
+  };
+  for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
+    load(g);
+    const FTile t = fused_tile(insts, L, g, l, TY);
+    const Inst& I = *t.I;
+    const int n = t.n, nc = t.nc, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
+    const float kappa = I.kappa[m][l], ws = I.wscale[m][l];
+    float* __restrict__ gt = I.lev[l].t;
+    float* __restrict__ gbc = I.lev[l + 1].b;
+    if (!zero) tile_store<XH * XW, NTH>(&sx[0][0], vx, tid);
+    tile_store<SH * SW, NTH>(&sb[0][0], vb, tid);
+    __syncthreads();
+    auto inside = [&](int i, int j) { return i >= 0 && i < n && j >= 0 && j < n; };
+#pragma unroll
+    for (int k = 0; k < (SH * SW + NTH - 1) / NTH; ++k) {
+      const int p = tid + k * NTH;
+      if (p < SH * SW) {
+        const int r = p / SW, c = p - r * SW, i = fi0 - 1 + c, j = fj0 - 1 + r;
+        float v = 0.f;
+        if (inside(i, j)) {
+          if (zero) {
+            v = omega * sb[r][c];
+          } else {
+            const float xp = sx[r + 1][c + 1];
+            const float nb = (sx[r + 1][c] + sx[r + 1][c + 2]) + (sx[r][c + 1] + sx[r + 2][c + 1]);
+            v = fmaf(omega, fmaf(kappa, nb, sb[r][c]) - xp, xp);
+          }
+        }
+        st[r][c] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < (RH * RW + NTH - 1) / NTH; ++k) {
+      const int p = tid + k * NTH;
+      if (p < RH * RW) {
+        const int r = p / RW, c = p - r * RW, i = fi0 + c, j = fj0 + r;
+        float res = 0.f;
+        if (inside(i, j)) {
+          const float tp = st[r + 1][c + 1];
+          const float nb = (st[r + 1][c] + st[r + 1][c + 2]) + (st[r][c + 1] + st[r + 2][c + 1]);
+          res = fmaf(kappa, nb, sb[r + 1][c + 1]) - tp;
+          if (c < FX && r < FY) gt[i + n * j] = tp;
+        }
+        sr[r][c] = res;
+      }
+    }
+    __syncthreads();
+    for (int p = tid; p < kFtX * TY; p += NTH) {
+      const int ly = p / kFtX, lx = p - ly * kFtX, Ic = I0 + lx, Jc = J0 + ly;
+      if (Ic < nc && Jc < nc) {
+        const int li = 2 * lx + 1, lj = 2 * ly + 1;
+        float row[3];
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+          row[dj + 1] = (sr[lj + dj][li - 1] + sr[lj + dj][li + 1]) + 2.f * sr[lj + dj][li];
+        gbc[Ic + nc * Jc] = ((row[0] + row[2]) + 2.f * row[1]) * ws;
+      }
+    }
+    __syncthreads();  // shared memory is refilled for the block's next tile
+  }
+}
+
+template <int TY>
+__device__ __forceinline__ void pb_up2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l,
+                                       float omega, int nu2) {
+  constexpr int NTH = 32 * TY;
+  constexpr int FX = 2 * kFtX, FY = 2 * TY;
+  constexpr int VW = FX + 2, VH = FY + 2;     // corrected iterate on fine offsets [-1, FX]
+  constexpr int EW = kFtX + 2, EH = TY + 2;   // coarse error on [I0 - 1, I0 + kFtX] x [J0 - 1, J0 + TY]
+  constexpr int KO = FX * FY / NTH;           // owned points per thread
+  __shared__ float sv[VH][VW], se[EH][EW];
+  const List& L = *list;
+  const int tid = threadIdx.x;
+  float vt[(VH * VW + NTH - 1) / NTH], ve[(EH * EW + NTH - 1) / NTH], bo[KO];
+  auto load = [&](int g) {
+    const FTile t = fused_tile(insts, L, g, l, TY);
+    const int n = t.n, nc = t.nc, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
+    const float* __restrict__ ft = t.I->lev[l].t;
+    const float* __restrict__ fb = t.I->lev[l].b;
+    const float* __restrict__ cx = t.I->lev[l + 1].x;
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int p = tid + k * NTH, r = p / FX, c = p - r * FX, i = fi0 + c, j = fj0 + r;
+      bo[k] = (nu2 && i < n && j < n) ? fb[i + n * j] : 0.f;
+    }
+    tile_load<EH * EW, NTH>(ve, tid, [&](int p) {
+      const int r = p / EW, c = p - r * EW, ci = I0 - 1 + c, cj = J0 - 1 + r;
+      return (ci >= 0 && ci < nc && cj >= 0 && cj < nc) ? cx[ci + nc * cj] : 0.f;
+    });
+    tile_load<VH * VW, NTH>(vt, tid, [&](int p) {
+      const int r = p / VW, c = p - r * VW, i = fi0 - 1 + c, j = fj0 - 1 + r;
+      return (i >= 0 && i < n && j >= 0 && j < n) ? ft[i + n * j] : 0.f;
+    });
+  };
+  for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
+    load(g);
+    const FTile t = fused_tile(insts, L, g, l, TY);
+    const Inst& I = *t.I;
+    const int n = t.n, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
+    const float kappa = I.kappa[m][l];
+    float* __restrict__ gx = I.lev[l].x;
+    tile_store<EH * EW, NTH>(&se[0][0], ve, tid);
+    tile_store<VH * VW, NTH>(&sv[0][0], vt, tid);
+    __syncthreads();
+    // + P e: coarse ci sits on fine 2 ci + 1, so an odd fine index takes one
+    // coarse value and an even one the mean of its two neighbours (zero ghosts)
+#pragma unroll
+    for (int k = 0; k < (VH * VW + NTH - 1) / NTH; ++k) {
+      const int p = tid + k * NTH;
+      if (p < VH * VW) {
+        const int r = p / VW, c = p - r * VW, i = fi0 - 1 + c, j = fj0 - 1 + r;
+        if (i >= 0 && i < n && j >= 0 && j < n) {
+          const int ex = (i & 1) ? (i - 1) / 2 - (I0 - 1) : i / 2 - 1 - (I0 - 1);
+          const int ey = (j & 1) ? (j - 1) / 2 - (J0 - 1) : j / 2 - 1 - (J0 - 1);
+          float pe;
+          if (i & 1) pe = (j & 1) ? se[ey][ex] : 0.5f * (se[ey][ex] + se[ey + 1][ex]);
+          else pe = (j & 1) ? 0.5f * (se[ey][ex] + se[ey][ex + 1])
+                            : 0.25f * ((se[ey][ex] + se[ey][ex + 1]) + (se[ey + 1][ex] + se[ey + 1][ex + 1]));
+          sv[r][c] += pe;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int p = tid + k * NTH, r = p / FX, c = p - r * FX, i = fi0 + c, j = fj0 + r;
+      if (i < n && j < n) {
+        const float vp = sv[r + 1][c + 1];
+        float out = vp;
+        if (nu2) {
+          const float nb = (sv[r + 1][c] + sv[r + 1][c + 2]) + (sv[r][c + 1] + sv[r + 2][c + 1]);
+          out = fmaf(omega, fmaf(kappa, nb, bo[k]) - vp, vp);
+        }
+        gx[i + n * j] = out;
+      }
+    }
+    __syncthreads();  // shared memory is refilled for the block's next tile
+  }
+}
+
+// Kernels of the phases (one launch each in the tick's graph).
+template <int DIM>
+__global__ void kb_spread(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction) {
+  pb_spread<DIM>(insts, list, reaction);
+}
+template <int DIM>
+__global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int reaction) {
+  pb_rhs<DIM>(insts, list, m, reaction);
+}
+template <int DIM>
+__global__ void kb_update(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int from_t) {
+  pb_update<DIM>(insts, list, m, from_t);
+}
+template <int DIM, int M>
+__global__ void kb_sweep_end(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction,
+                             unsigned long long* __restrict__ rbits) {
+  pb_sweep_end<DIM, M>(insts, list, reaction, rbits);
+}
+template <int DIM>
+__global__ void __launch_bounds__(kBottomThreads)
+    kb_bottom(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int load_x, int smoother,
+              int nu1, int nu2, float omega) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pb_bottom<DIM>(insts, list, m, load_x, smoother, nu1, nu2, omega, smem_raw);
+}
+template <int TY>
+__global__ void __launch_bounds__(32 * TY)
+    kb_down2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int zero) {
+  pb_down2<TY>(insts, list, m, l, omega, zero);
+}
+template <int TY>
+__global__ void __launch_bounds__(32 * TY)
+    kb_up2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int nu2) {
+  pb_up2<TY>(insts, list, m, l, omega, nu2);
+}
+
+// ---------------------------------------------------------------------------
+// The whole tick as one persistent cooperative launch (fused 2D mode): the
+// blocks walk the tick's phase table, and a grid barrier separates phases.
+// The launch is cooperative, so every block is resident and the barrier cannot
+// wait for a block that has not started; still, every wait is bounded: a block
+// that waits longer than kBarrierNs sets the error flag, every block leaves at
+// its next barrier, and the host reports the tick as failed.  Each phase runs
+// the same device function as its graph-node kernel, so both forms give the
+// same result bit for bit.
+// ---------------------------------------------------------------------------
+enum PhaseKind { PH_SPREAD = 0, PH_SWEEP_END = 1, PH_RHS = 2, PH_DOWN = 3, PH_BOTTOM = 4, PH_UP = 5, PH_UPDATE = 6 };
+
+struct Phase {
+  int kind, list, m, l, arg;  // arg: M (sweep end), 1 = rbits / 0 = scratch (sweep end), zero guess, load_x
+  int arg2;
+};
+
+struct GridBarrier {
+  unsigned int count, gen;
+  int err, pad;
+};
+
+constexpr unsigned long long kBarrierNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Returns false when the tick has failed (a wait ran out here or elsewhere).
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &gb->gen;
+    volatile int* verr = &gb->err;
+    const unsigned int g0 = *vgen;  // read before arriving: the generation cannot move until we arrive
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g0 && !*verr) {
+        if (global_ns() - t0 > kBarrierNs) {
+          atomicExch(&gb->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = *verr == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int TY>
+__global__ void __launch_bounds__(32 * TY)
+    kb_tick2(const Inst* __restrict__ insts, const List* __restrict__ lists, const Phase* __restrict__ phases,
+             int nphases, int reaction, float omega, int nu1, int nu2, unsigned long long* __restrict__ rbits,
+             unsigned long long* __restrict__ scratch, GridBarrier* gb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int q = 0; q < nphases; ++q) {
+    const Phase P = phases[q];
+    const List* L = lists + P.list;
+    switch (P.kind) {
+      case PH_SPREAD: pb_spread<2>(insts, L, reaction); break;
+      case PH_SWEEP_END: {
+        unsigned long long* out = P.arg2 ? rbits : scratch;
+        switch (P.arg) {
+          case 2: pb_sweep_end<2, 2>(insts, L, reaction, out); break;
+          case 3: pb_sweep_end<2, 3>(insts, L, reaction, out); break;
+          case 4: pb_sweep_end<2, 4>(insts, L, reaction, out); break;
+          case 5: pb_sweep_end<2, 5>(insts, L, reaction, out); break;
+          case 6: pb_sweep_end<2, 6>(insts, L, reaction, out); break;
+          default: pb_sweep_end<2, 7>(insts, L, reaction, out); break;
+        }
+        break;
+      }
+      case PH_RHS: pb_rhs<2>(insts, L, P.m, reaction); break;
+      case PH_DOWN: pb_down2<TY>(insts, L, P.m, P.l, omega, P.arg); break;
+      case PH_BOTTOM: pb_bottom<2>(insts, L, P.m, P.arg, 0, nu1, nu2, omega, smem_raw); break;
+      case PH_UP: pb_up2<TY>(insts, L, P.m, P.l, omega, nu2); break;
+      default: pb_update<2>(insts, L, P.m, 0); break;
+    }
+    if (q + 1 < nphases && !grid_barrier(gb)) return;
+  }
 }
 
 #undef BATCH_LOOP

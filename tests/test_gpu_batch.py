@@ -66,6 +66,75 @@ def test_batch_matches_fp64_oracle(ndim, probs):
     eng.close()
 
 
+@pytest.mark.parametrize("depth", [-1, 0])
+def test_batch_temporal_blocking_depths_match_fp64_oracle(depth):
+    """2D damped-Jacobi V(1,1) engines with the sweep fused into the transfer
+    passes (depth 1, the default) and with separate phases (depth 0), on sides
+    with up to three grid-wide levels above the per-instance bottom block (511:
+    levels 511, 255, 127, then 63 and below in one block) and bottom-only
+    sides, against the FP64 oracle."""
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    probs = [(511, 0.05, 3, 0.02, 1), (255, 0.5, 5, 0.05, 1), (127, 0.02, 5, 0.1, 1), (63, 0.3, 3, 0.05, 2),
+             (15, 1.0, 3, 0.01, 1)]
+    eng = G.Batch(2, 511, 5, 16 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150,
+                  temporal_blocking=depth)
+    got = _run(eng, probs, 2, 110)
+    info = eng.stats()
+    assert info.fused == (1 if depth == -1 else 0) and info.bytes_last_tick > 0
+    eng.close()
+    for q, (n, nu, M, dt, steps) in enumerate(probs):
+        p = O.Problem(2, n, nu, M, dt, smoother=O.SMOOTHER_JACOBI, max_sweeps=150)
+        with O.all_cores():
+            ref = O.integrate(p, initial_condition(2, n, 110 + q), steps, 0, 2)
+        assert all(s == 0 for s in ref.status)
+        assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
+
+
+def test_batch_launch_shapes_give_identical_results():
+    """An instance admitted into a fresh engine sweeps through the autotuner's
+    trial ticks (every graph shape, then the persistent one-launch ticks), the
+    same instance admitted after tuning sweeps in the chosen shape only: the
+    results agree bit for bit, so no launch form changes the arithmetic."""
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    prob = (255, 0.1, 5, 0.02, 1)
+
+    def engine():
+        return G.Batch(2, 255, 5, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+
+    fresh = engine()
+    r_fresh = _run(fresh, [prob], 2, 150)
+    fresh.close()
+    tuned = engine()
+    warm = tuned.admit(63, 0.5, 3, 0.05, 50, initial_condition(2, 63, 9))
+    for _ in range(20):
+        tuned.tick()
+        if tuned.stats().tuned:
+            break
+    assert tuned.stats().tuned == 1
+    r_tuned = _run_keep(tuned, [prob], 2, 150, ignore=[warm])
+    tuned.close()
+    np.testing.assert_array_equal(r_fresh[0][0], r_tuned[0][0])
+    assert r_fresh[0][1] == r_tuned[0][1]
+
+
+def _run_keep(eng, probs, ndim, seed0, ignore=()):
+    slots = [eng.admit(n, nu, M, dt, steps, initial_condition(ndim, n, seed0 + q))
+             for q, (n, nu, M, dt, steps) in enumerate(probs)]
+    assert all(s is not None for s in slots)
+    for _ in range(10000):
+        eng.tick()
+        if all(eng.query(s).state != 1 for s in slots):
+            break
+    out = []
+    for s in slots:
+        info = eng.query(s)
+        assert info.state == 2, info.state
+        out.append((eng.take(s), info.total_sweeps))
+    return out
+
+
 def test_batch_alone_equals_in_the_mix():
     mix = _engine(2)
     together = _run(mix, PROBS_2D, 2, 70)
