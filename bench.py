@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 import isdc_inputs as W  # noqa: E402
 
-FP64_OPS_PER_SM_CLK = 2      # DFMA/DADD issue per SM per clock on GB300 (measured 0.598 T DFMA/s at ~1.98 GHz)
+FP64_OPS_PER_SM_CLK = 2      # nominal FP64 issue per SM per clock (used only when the probe cannot run)
 FP32_OPS_PER_SM_CLK = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -130,9 +130,10 @@ def traffic_for(workload: str, cls: str):
     return None
 
 
-def roofline(prof: dict, dom: str, workload: str, shares: dict):
+def roofline(prof: dict, dom: str, workload: str, shares: dict, peak: dict | None = None):
     """Roofline of kernel class `dom`: algorithmic bytes / ops per launch over
-    its event-timed average launch duration in the timed region."""
+    its event-timed average launch duration in the timed region.  FP64-bound
+    classes are reported against the FP64 issue rate measured in this run."""
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
@@ -141,7 +142,7 @@ def roofline(prof: dict, dom: str, workload: str, shares: dict):
     bytes_l = r["bytes"] / r["launches"]
     dp_l = r["fp64_ops"] / r["launches"]
     sp_l = r["fp32_ops"] / r["launches"]
-    dp_peak = SMS * FP64_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    dp_peak = peak["ops_per_s"] if peak else SMS * FP64_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6
     sp_peak = SMS * FP32_OPS_PER_SM_CLK * SM_MAX_MHZ * 1e6
     t_hbm = bytes_l / (hbm * 1e9)
     t_dp = dp_l / dp_peak
@@ -155,7 +156,8 @@ def roofline(prof: dict, dom: str, workload: str, shares: dict):
     elif t_dp >= t_sp:
         ach = dp_l / per_launch_s / 1e12
         out.update(bound="alu", achieved=ach, peak=dp_peak / 1e12, unit="T FP64-op/s", frac=ach / (dp_peak / 1e12),
-                   peak_source="derived: 152 SMs x 2 FP64 add/mul/FMA per SM-clock x 2070 MHz",
+                   peak_source=("measured in this run: FP64 FMA issue probe (libisdc_probe.so)" if peak else
+                                "derived: 152 SMs x 2 FP64 add/mul/FMA per SM-clock x 2070 MHz"),
                    hbm_frac=bytes_l / per_launch_s / 1e9 / hbm)
     else:
         ach = sp_l / per_launch_s / 1e12
@@ -189,27 +191,34 @@ def oracle_sweep_rate(w, n_override=None, sweeps=1):
 
 
 def run_reference(args):
+    """The oracle as it stands (its all-core build, every host core) on the
+    workload's own grid: each step one SDC sweep of step 1 of the workload."""
+    import oracle as O
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     w = workloads().get(args.workload, W.workload_3d_255())
-    n_sample = (128 if w.equation == 1 else 127) if w.ndim == 3 and w.n > 127 else w.n
-    for _ in range(args.warmup):
-        oracle_sweep_rate(w, n_sample)
-    total_dof_sweeps, total_t = 0.0, 0.0
-    for _ in range(args.steps):
-        rate, dt, n = oracle_sweep_rate(w, n_sample)
-        total_dof_sweeps += n ** w.ndim
-        total_t += dt
+    with O.all_cores():
+        cores = O.threads()
+        for _ in range(args.warmup):
+            oracle_sweep_rate(w)
+        total_dof_sweeps, total_t = 0.0, 0.0
+        for _ in range(args.steps):
+            rate, dt, n = oracle_sweep_rate(w)
+            total_dof_sweeps += n ** w.ndim
+            total_t += dt
     value = total_dof_sweeps / total_t
-    sample = (f"each step: 1 SDC sweep ({w.M - 1} node solves x {w.n_vcycles} V-cycles + residual) of the "
-              f"workload's equation and parameters on a {n_sample}^{w.ndim} grid, from its seeded initial state")
+    solves = w.M - (1 if w.nodes == 0 else 0)
+    sample = (f"each step: 1 SDC sweep ({solves} node solves x {w.n_vcycles} V-cycles + residual) of step 1 of "
+              f"the workload on its own {w.n}^{w.ndim} grid, from its seeded initial state, all-core oracle "
+              f"build on {cores} threads")
     line = {"metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(w),
-            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -247,33 +256,40 @@ def config_of(w):
             "parallelism": "replicas (one independent instance per GPU)"}
 
 
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
+def fp64_peak():
+    """The GPU's FP64 issue rate measured in this run (libisdc_probe.so: independent
+    FMA chains on every SM; one FMA = one FP64 operation), in operations per second."""
     import paper_1401_7824_gb300 as G
+    ops, ms = G.probe_fp64_rate()
+    return {"ops_per_s": ops, "probe_ms": ms,
+            "per_sm_clock_at_max": ops / (SMS * SM_MAX_MHZ * 1e6)}
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+def latency_record(prof_full, shares, dom, elapsed, sweeps_total, launches):
+    """Roofline record of a workload whose node state fits in L2: the time per
+    sweep and the launches per sweep (no bandwidth or ALU bound applies)."""
+    us = elapsed / max(1, sweeps_total) * 1e6
+    return {"bound": "latency", "achieved": us, "unit": "us/sweep", "peak": None, "frac": None,
+            "launches_per_sweep": launches / max(1, sweeps_total), "us_per_sweep": us,
+            "kernel": dom, "traffic": None, "shares": shares}
 
-    w = workloads()[args.workload]
+
+def measure(w, args, world, barrier, peak):
+    """Time K until-tolerance steps of workload w on this rank (inputs resident
+    on the device), then the same through the host-buffer entry point."""
+    import torch
+    import paper_1401_7824_gb300 as G
     N = w.n ** w.ndim
     u0 = W.workload_initial(w)
     g = G.Isdc(w.ndim, w.n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
                vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200, temporal_blocking=args.temporal_blocking,
+               fused_transfer=args.fused_transfer, rb_run=args.rb_run,
                nodes=w.nodes, stencil=w.stencil, equation=w.equation,
                reaction=G.ISDC_REACTION_ALLEN_CAHN if w.reaction == 1 else G.ISDC_REACTION_NONE)
     stream = torch.cuda.current_stream()
     u = torch.from_numpy(u0).cuda()
     for _ in range(args.warmup):
-        st = g.step(u, 0, w.n_vcycles)
+        g.step(u, 0, w.n_vcycles)
     torch.cuda.synchronize()
     # one untimed step with every kernel class event-timed: the per-class shares
     # and the dominant class (timed alone inside the measured region below)
@@ -286,7 +302,7 @@ def run_ours(args):
 
     gpu_id = None
     try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
     except Exception:
         gpu_id = None
     clocks = ClockSampler(gpu_id)
@@ -339,38 +355,99 @@ def run_ours(args):
         e2e_sweeps += g.stats()[0]
     e2e_t = time.perf_counter() - t0
     barrier()
+    tuning = g.tuning()
+    g.close()
+    del u, uh
+    torch.cuda.empty_cache()
 
     (elapsed, e2e_t), (dof_sweeps, e2e_work) = combine_ranks([elapsed, e2e_t], [dof_sweeps, float(N * e2e_sweeps)],
                                                              world, "cuda")
+    cfg = config_of(w)
+    if cfg["l2"].startswith("inputs fit"):
+        roof = latency_record(full_prof, shares, dominant, elapsed, world * sum(sweeps), world * launches)
+    else:
+        roof = roofline(prof, dominant, w.name, shares, peak)
+    return {
+        "value": dof_sweeps / elapsed, "elapsed": elapsed, "config": cfg,
+        "ms_per_step": elapsed / args.steps * 1e3, "steps_per_s": world * args.steps / elapsed,
+        "sweeps_per_step": sweeps, "vcycles_per_step": vcycles, "residual_last_step": residual,
+        "converged": all(s == 0 for s in statuses), "gpu_launches": launches, "roofline": roof,
+        "profiled_region_ms_per_step": profiled_elapsed / args.steps * 1e3 if profiled_elapsed else None,
+        "autotune": tuning, "clocks": clk,
+        "e2e": {"value": e2e_work / e2e_t, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": N * 8},
+    }
 
-    value = dof_sweeps / elapsed
+
+def cpu_baseline(w):
+    """The oracle as it stands, on one SDC sweep of step 1 of the workload: its
+    all-core build (every host core) and its plain single-threaded build."""
+    import oracle as O
+    with O.all_cores():
+        rate_all, dt_all, n = oracle_sweep_rate(w)
+        cores = O.threads()
+    rate_1, dt_1, _ = oracle_sweep_rate(w)
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines() if ln.startswith("Model name")), "")
+    except Exception:
+        pass
+    solves = w.M - (1 if w.nodes == 0 else 0)
+    return {"value": rate_all, "unit": "DOF-sweeps/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 SDC sweep of step 1 of the workload ({n}^{w.ndim} grid, {solves} node solves x "
+                      f"{w.n_vcycles} V-cycles + residual): {dt_all:.2f} s on {cores} threads (all-core build), "
+                      f"{dt_1:.1f} s single-threaded (plain build)",
+            "single_core_value": rate_1, "nproc": os.cpu_count(), "cpu_model": model}
+
+
+def run_ours(args):
+    import dataclasses
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    peak = fp64_peak()
+    w = workloads()[args.workload]
+    m = measure(w, args, world, barrier, peak)
     line = {
-        "metric": "DOF-sweeps/s", "value": value, "unit": "DOF-sweeps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "metric": "DOF-sweeps/s", "value": m["value"], "unit": "DOF-sweeps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if not w.vcycle_fp32 else "f64 (FP32 V-cycles)",
         "data": "synthetic (seeded " + ("periodic Gaussian" if w.equation == 1 else "sin-mode") +
                 " initial data + N(0, 0.01^2) noise)",
-        "config": config_of(w),
-        "steps_per_s": world * args.steps / elapsed,
-        "sweeps_per_step": sweeps, "vcycles_per_step": vcycles, "residual_last_step": residual,
-        "converged": all(s == 0 for s in statuses),
-        "gpu_launches": launches,
-        "roofline": roofline(prof, dominant, w.name, shares),
-        "profiled_region_ms_per_step": profiled_elapsed / args.steps * 1e3 if profiled_elapsed else None,
-        "autotune": g.tuning(),
-        "clocks": clk,
-        "e2e": {"value": e2e_work / e2e_t, "unit": "DOF-sweeps/s", "h2d_bytes_per_step": N * 8,
-                "d2h_bytes_per_step": N * 8},
+        "config": m["config"],
     }
-    g.close()
+    for k in ("steps_per_s", "sweeps_per_step", "vcycles_per_step", "residual_last_step", "converged",
+              "gpu_launches", "roofline", "profiled_region_ms_per_step", "autotune", "clocks", "e2e"):
+        line[k] = m[k]
+    line["fp64_peak_probe"] = peak
+    # the FP32-V-cycle forms of the workload (and the largest single-GPU one),
+    # timed the same way, beside the FP64 headline
+    if world == 1 and not args.no_extras and w.name == "3d_n255_M5_fp64":
+        extras = {"fp32_vcycles": dataclasses.replace(w, name="3d_n255_M5_mixed", vcycle_fp32=True),
+                  "n511_fp32_vcycles": W.workload_3d_511_mixed()}
+        for key, we in extras.items():
+            me = measure(we, args, world, barrier, peak)
+            line[key] = {"workload": we.name, "value": me["value"], "unit": "DOF-sweeps/s",
+                         "vs_headline": me["value"] / m["value"], "ms_per_step": me["ms_per_step"],
+                         "steps": args.steps, "sweeps_per_step": me["sweeps_per_step"],
+                         "residual_last_step": me["residual_last_step"], "converged": me["converged"],
+                         "gpu_launches": me["gpu_launches"], "e2e": me["e2e"], "roofline": me["roofline"],
+                         "clocks": me["clocks"], "config": me["config"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, n = oracle_sweep_rate(w)
-        line["cpu_baseline"] = {"value": rate, "unit": "DOF-sweeps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"1 SDC sweep of step 1 of the workload ({n}^{w.ndim} grid, "
-                                          f"{w.M - (1 if w.nodes == 0 else 0)} node solves x {w.n_vcycles} V-cycles"
-                                          f" + residual), "
-                                          f"{dt:.1f} s single-threaded"}
+        line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -387,10 +464,11 @@ def run_batch(args):
     import paper_1401_7824_gb300 as G
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    insts = W.batch_instances(256, seed=4)
+    insts = W.batch_instances(args.instances, seed=4)
     stream = torch.cuda.Stream()
     o = G.isdc_default_options()
     o.smoother, o.nu1, o.nu2, o.vcycle_fp32, o.tol, o.max_sweeps = G.ISDC_SMOOTHER_JACOBI, 1, 1, 1, 1e-10, 150
+    o.temporal_blocking = -1 if args.temporal_blocking < 0 else min(args.temporal_blocking, 1)
     import ctypes
     o.stream = ctypes.c_void_p(stream.cuda_stream)
     eng = G.isdc_batch_create(2, 1023, 5, 200 << 30, 2, o)
@@ -409,11 +487,13 @@ def run_batch(args):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dofs = 0.0
+    tick_bytes = 0.0
     e0.record(stream)
     for _ in range(args.steps):
         live = [s for s in sides if G.isdc_batch_query(eng, s).state == G.ISDC_SLOT_RUNNING]
         dofs += sum(float(sides[s] ** 2) for s in live)
         G.isdc_batch_tick(eng)
+        tick_bytes += G.isdc_batch_stats(eng).bytes_last_tick  # host-side counter, no device work
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -425,7 +505,8 @@ def run_batch(args):
             "steps": args.steps, "warmup": warm, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 V-cycles)",
             "data": "synthetic (seeded)",
-            "config": {"workload": "batch_2d_256", "instances": len(insts),
+            "config": {"workload": "batch_2d_256" if len(insts) == 256 else f"batch_2d_{len(insts)}",
+                       "instances": len(insts),
                        "dofs_total": int(sum(w.n ** 2 for w in insts)),
                        "sides": "2^j - 1, j uniform in 6..10", "smoother": "wjacobi V(1,1)", "L_vcycles": 2,
                        "vcycle_precision": "fp32", "tol": 1e-10,
@@ -434,6 +515,19 @@ def run_batch(args):
                                         "blocks_per_sm": info.blocks_per_sm, "tuned": info.tuned}},
             "gpu_launches": int(launches),
             "clocks": clk}
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach = tick_bytes / elapsed / 1e9
+    line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": None, "kernel": "whole tick",
+                        "algorithmic_bytes_per_tick": tick_bytes / args.steps,
+                        "peak_source": ("measured" if "hbm_gbs" in peaks else "fallback") +
+                                       " HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                        "note": "algorithmic bytes of every phase of the tick (each input read once, each output "
+                                "written once) over the tick time; the FP64 phases (right-hand sides, sweep end) "
+                                "are bound by FP64 issue, so the whole tick stays below the HBM bound"}
+    line["config"]["fused_smoother"] = int(info.fused)
+    line["config"]["kernels_per_tick"] = int(info.kernels_per_tick)
     if args.compare_fp64:
         # the same instances one at a time through the FP64 single-instance path
         tot_dofs, tot_t = 0.0, 0.0
@@ -492,19 +586,35 @@ def main():
     ap.add_argument("--workload", default="3d_n255_M5_fp64",
                     choices=sorted(workloads()) + ["batch_2d_256", "serve_poisson"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the FP32-V-cycle 255^3 and 511^3 lines")
+    ap.add_argument("--probe-fp64", action="store_true", help="print the FP64 issue-rate probe and exit")
     ap.add_argument("--no-profile", action="store_true",
                     help="no per-launch events in the timed region (sweeps replay CUDA graphs); the roofline then "
                          "comes from the untimed fully profiled step")
     ap.add_argument("--compare-fp64", type=int, default=0, help="batch: also time N instances on the FP64 path")
+    ap.add_argument("--instances", type=int, default=256,
+                    help="batch: number of instances (the first K of the seeded 256; smaller for profiling)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--fused-transfer", type=int, default=-1, choices=[-1, 0, 1],
+                    help="residual + restriction: -1 tuned per level, 0 two launches, 1 one fused launch")
+    ap.add_argument("--rb-run", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32, -1, -2, -4, -8],
+                    help="3D red-black run form of the natural-layout levels: 0 tuned")
     ap.add_argument("--temporal-blocking", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="3D FP32 red-black fine level: -1 autotuned, 0 one pass per colour, "
                          "1/2 red-black sweeps per blocked pass")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.probe_fp64:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks = ClockSampler(None)
+        clocks.start()
+        r = [fp64_peak() for _ in range(5)]
+        print(json.dumps({"fp64_probe": r, "clocks": clocks.stop()}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch_2d_256":
         run_batch(args)

@@ -29,6 +29,23 @@ def nvcc():
     return "nvcc"
 
 
+PROBE_LIB = os.path.join(PKG, "libisdc_probe.so")
+PROBE_SRC = os.path.join(PKG, "csrc", "probe", "fp64_rate.cu")
+
+
+def build_probe(force: bool = False) -> str:
+    """libisdc_probe.so: the FP64 issue-rate measurement (include/isdc_probe.h)."""
+    deps_p = [PROBE_SRC, os.path.join(ROOT, "include", "isdc_probe.h")]
+    if not force and os.path.exists(PROBE_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(PROBE_LIB)
+                                                       for d in deps_p):
+        return PROBE_LIB
+    tmp = f"{PROBE_LIB}.tmp{os.getpid()}"
+    subprocess.check_call([nvcc(), ARCH, "-O3", "-lineinfo", "-shared", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+                           "-o", tmp, PROBE_SRC])
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
@@ -47,3 +64,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_probe(force=True))
