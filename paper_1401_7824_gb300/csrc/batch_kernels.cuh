@@ -354,29 +354,6 @@ __device__ __forceinline__ void fused_tile_origin(int q, int nc, int ty, int& I0
   J0 = (q / ntx) * ty;
 }
 
-// Tile loads: a thread loads its share of the tile's input region into
-// registers (K = COUNT / NTH values, all issued before the first is stored)
-// and then stores them to shared memory.  (Issuing the next tile's loads
-// during the current tile's compute was measured slower: these passes are
-// bound by instruction issue, not by load latency.)
-template <int COUNT, int NTH, class Get>
-__device__ __forceinline__ void tile_load(float (&v)[(COUNT + NTH - 1) / NTH], int tid, const Get& get) {
-#pragma unroll
-  for (int k = 0; k < (COUNT + NTH - 1) / NTH; ++k) {
-    const int p = tid + k * NTH;
-    v[k] = p < COUNT ? get(p) : 0.f;
-  }
-}
-template <int COUNT, int NTH>
-__device__ __forceinline__ void tile_store(float* __restrict__ dst, const float (&v)[(COUNT + NTH - 1) / NTH],
-                                           int tid) {
-#pragma unroll
-  for (int k = 0; k < (COUNT + NTH - 1) / NTH; ++k) {
-    const int p = tid + k * NTH;
-    if (p < COUNT) dst[p] = v[k];
-  }
-}
-
 // Geometry of work-list tile g of level l (coarse side nc = side of level l+1).
 struct FTile {
   const Inst* I;
@@ -392,84 +369,88 @@ __device__ __forceinline__ FTile fused_tile(const Inst* __restrict__ insts, cons
   return t;
 }
 
+// Row-structured access to a tile region: warp w takes rows w, w + NW, ...
+// and lane l columns l, l + 32, l + 64 of each, so a row's base address and
+// validity are formed once per row and no index is divided.  Every loop has a
+// compile-time trip count and is unrolled, so a thread's loads of several
+// rows are in flight together.
+template <int H, int W, int NW, class Body>
+__device__ __forceinline__ void for_rows(int warp, int lane, const Body& body) {
+#pragma unroll
+  for (int t = 0; t < (H + NW - 1) / NW; ++t) {
+    const int r = warp + NW * t;
+    if (r < H) {
+#pragma unroll
+      for (int k = 0; k < (W + 31) / 32; ++k) {
+        const int c = lane + 32 * k;
+        if (c < W) body(r, c);
+      }
+    }
+  }
+}
+
 template <int TY>
 __device__ __forceinline__ void pb_down2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l,
                                          float omega, int zero) {
-  constexpr int NTH = 32 * TY;
+  constexpr int NW = TY;  // warps per block
   constexpr int FX = 2 * kFtX, FY = 2 * TY;
   constexpr int XW = FX + 5, XH = FY + 5;  // x on fine offsets [-2, FX + 2]
   constexpr int SW = FX + 3, SH = FY + 3;  // b and the smoothed iterate on [-1, FX + 1]
   constexpr int RW = FX + 1, RH = FY + 1;  // residual on [0, FX]
   __shared__ float sx[XH][XW], sb[SH][SW], st[SH][SW], sr[RH][RW];
   const List& L = *list;
-  const int tid = threadIdx.x;
-  float vx[(XH * XW + NTH - 1) / NTH], vb[(SH * SW + NTH - 1) / NTH];
-  auto load = [&](int g) {
-    const FTile t = fused_tile(insts, L, g, l, TY);
-    const int n = t.n, fi0 = 2 * t.I0, fj0 = 2 * t.J0;
-    const float* __restrict__ fx = t.I->lev[l].x;
-    const float* __restrict__ fb = t.I->lev[l].b;
-    if (!zero)
-      tile_load<XH * XW, NTH>(vx, tid, [&](int p) {
-        const int r = p / XW, c = p - r * XW, i = fi0 - 2 + c, j = fj0 - 2 + r;
-        return (i >= 0 && i < n && j >= 0 && j < n) ? fx[i + n * j] : 0.f;
-      });
-    tile_load<SH * SW, NTH>(vb, tid, [&](int p) {
-      const int r = p / SW, c = p - r * SW, i = fi0 - 1 + c, j = fj0 - 1 + r;
-      return (i >= 0 && i < n && j >= 0 && j < n) ? fb[i + n * j] : 0.f;
-    });
-  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
-    load(g);
     const FTile t = fused_tile(insts, L, g, l, TY);
     const Inst& I = *t.I;
     const int n = t.n, nc = t.nc, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
     const float kappa = I.kappa[m][l], ws = I.wscale[m][l];
+    const float* __restrict__ fx = I.lev[l].x;
+    const float* __restrict__ fb = I.lev[l].b;
     float* __restrict__ gt = I.lev[l].t;
     float* __restrict__ gbc = I.lev[l + 1].b;
-    if (!zero) tile_store<XH * XW, NTH>(&sx[0][0], vx, tid);
-    tile_store<SH * SW, NTH>(&sb[0][0], vb, tid);
+    const unsigned un = unsigned(n);
+    if (!zero)
+      for_rows<XH, XW, NW>(warp, lane, [&](int r, int c) {
+        const int i = fi0 - 2 + c, j = fj0 - 2 + r;
+        sx[r][c] = (unsigned(i) < un && unsigned(j) < un) ? fx[i + n * j] : 0.f;
+      });
+    for_rows<SH, SW, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 - 1 + c, j = fj0 - 1 + r;
+      sb[r][c] = (unsigned(i) < un && unsigned(j) < un) ? fb[i + n * j] : 0.f;
+    });
     __syncthreads();
-    auto inside = [&](int i, int j) { return i >= 0 && i < n && j >= 0 && j < n; };
-#pragma unroll
-    for (int k = 0; k < (SH * SW + NTH - 1) / NTH; ++k) {
-      const int p = tid + k * NTH;
-      if (p < SH * SW) {
-        const int r = p / SW, c = p - r * SW, i = fi0 - 1 + c, j = fj0 - 1 + r;
-        float v = 0.f;
-        if (inside(i, j)) {
-          if (zero) {
-            v = omega * sb[r][c];
-          } else {
-            const float xp = sx[r + 1][c + 1];
-            const float nb = (sx[r + 1][c] + sx[r + 1][c + 2]) + (sx[r][c + 1] + sx[r + 2][c + 1]);
-            v = fmaf(omega, fmaf(kappa, nb, sb[r][c]) - xp, xp);
-          }
+    for_rows<SH, SW, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 - 1 + c, j = fj0 - 1 + r;
+      float v = 0.f;
+      if (unsigned(i) < un && unsigned(j) < un) {
+        if (zero) {
+          v = omega * sb[r][c];
+        } else {
+          const float xp = sx[r + 1][c + 1];
+          const float nb = (sx[r + 1][c] + sx[r + 1][c + 2]) + (sx[r][c + 1] + sx[r + 2][c + 1]);
+          v = fmaf(omega, fmaf(kappa, nb, sb[r][c]) - xp, xp);
         }
-        st[r][c] = v;
       }
-    }
+      st[r][c] = v;
+    });
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < (RH * RW + NTH - 1) / NTH; ++k) {
-      const int p = tid + k * NTH;
-      if (p < RH * RW) {
-        const int r = p / RW, c = p - r * RW, i = fi0 + c, j = fj0 + r;
-        float res = 0.f;
-        if (inside(i, j)) {
-          const float tp = st[r + 1][c + 1];
-          const float nb = (st[r + 1][c] + st[r + 1][c + 2]) + (st[r][c + 1] + st[r + 2][c + 1]);
-          res = fmaf(kappa, nb, sb[r + 1][c + 1]) - tp;
-          if (c < FX && r < FY) gt[i + n * j] = tp;
-        }
-        sr[r][c] = res;
+    for_rows<RH, RW, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 + c, j = fj0 + r;
+      float res = 0.f;
+      if (unsigned(i) < un && unsigned(j) < un) {
+        const float tp = st[r + 1][c + 1];
+        const float nb = (st[r + 1][c] + st[r + 1][c + 2]) + (st[r][c + 1] + st[r + 2][c + 1]);
+        res = fmaf(kappa, nb, sb[r + 1][c + 1]) - tp;
+        if (c < FX && r < FY) gt[i + n * j] = tp;
       }
-    }
+      sr[r][c] = res;
+    });
     __syncthreads();
-    for (int p = tid; p < kFtX * TY; p += NTH) {
-      const int ly = p / kFtX, lx = p - ly * kFtX, Ic = I0 + lx, Jc = J0 + ly;
+    {  // one coarse point per thread: (I0 + lane, J0 + warp)
+      const int Ic = I0 + lane, Jc = J0 + warp;
       if (Ic < nc && Jc < nc) {
-        const int li = 2 * lx + 1, lj = 2 * ly + 1;
+        const int li = 2 * lane + 1, lj = 2 * warp + 1;
         float row[3];
 #pragma unroll
         for (int dj = -1; dj <= 1; ++dj)
@@ -484,77 +465,60 @@ __device__ __forceinline__ void pb_down2(const Inst* __restrict__ insts, const L
 template <int TY>
 __device__ __forceinline__ void pb_up2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l,
                                        float omega, int nu2) {
-  constexpr int NTH = 32 * TY;
+  constexpr int NW = TY;
   constexpr int FX = 2 * kFtX, FY = 2 * TY;
   constexpr int VW = FX + 2, VH = FY + 2;     // corrected iterate on fine offsets [-1, FX]
   constexpr int EW = kFtX + 2, EH = TY + 2;   // coarse error on [I0 - 1, I0 + kFtX] x [J0 - 1, J0 + TY]
-  constexpr int KO = FX * FY / NTH;           // owned points per thread
   __shared__ float sv[VH][VW], se[EH][EW];
   const List& L = *list;
-  const int tid = threadIdx.x;
-  float vt[(VH * VW + NTH - 1) / NTH], ve[(EH * EW + NTH - 1) / NTH], bo[KO];
-  auto load = [&](int g) {
-    const FTile t = fused_tile(insts, L, g, l, TY);
-    const int n = t.n, nc = t.nc, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
-    const float* __restrict__ ft = t.I->lev[l].t;
-    const float* __restrict__ fb = t.I->lev[l].b;
-    const float* __restrict__ cx = t.I->lev[l + 1].x;
-#pragma unroll
-    for (int k = 0; k < KO; ++k) {
-      const int p = tid + k * NTH, r = p / FX, c = p - r * FX, i = fi0 + c, j = fj0 + r;
-      bo[k] = (nu2 && i < n && j < n) ? fb[i + n * j] : 0.f;
-    }
-    tile_load<EH * EW, NTH>(ve, tid, [&](int p) {
-      const int r = p / EW, c = p - r * EW, ci = I0 - 1 + c, cj = J0 - 1 + r;
-      return (ci >= 0 && ci < nc && cj >= 0 && cj < nc) ? cx[ci + nc * cj] : 0.f;
-    });
-    tile_load<VH * VW, NTH>(vt, tid, [&](int p) {
-      const int r = p / VW, c = p - r * VW, i = fi0 - 1 + c, j = fj0 - 1 + r;
-      return (i >= 0 && i < n && j >= 0 && j < n) ? ft[i + n * j] : 0.f;
-    });
-  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
-    load(g);
     const FTile t = fused_tile(insts, L, g, l, TY);
     const Inst& I = *t.I;
-    const int n = t.n, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
+    const int n = t.n, nc = t.nc, I0 = t.I0, J0 = t.J0, fi0 = 2 * I0, fj0 = 2 * J0;
     const float kappa = I.kappa[m][l];
+    const float* __restrict__ ft = I.lev[l].t;
+    const float* __restrict__ fb = I.lev[l].b;
+    const float* __restrict__ cx = I.lev[l + 1].x;
     float* __restrict__ gx = I.lev[l].x;
-    tile_store<EH * EW, NTH>(&se[0][0], ve, tid);
-    tile_store<VH * VW, NTH>(&sv[0][0], vt, tid);
+    const unsigned un = unsigned(n), unc = unsigned(nc);
+    for_rows<EH, EW, NW>(warp, lane, [&](int r, int c) {
+      const int ci = I0 - 1 + c, cj = J0 - 1 + r;
+      se[r][c] = (unsigned(ci) < unc && unsigned(cj) < unc) ? cx[ci + nc * cj] : 0.f;
+    });
+    for_rows<VH, VW, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 - 1 + c, j = fj0 - 1 + r;
+      sv[r][c] = (unsigned(i) < un && unsigned(j) < un) ? ft[i + n * j] : 0.f;
+    });
     __syncthreads();
     // + P e: coarse ci sits on fine 2 ci + 1, so an odd fine index takes one
-    // coarse value and an even one the mean of its two neighbours (zero ghosts)
-#pragma unroll
-    for (int k = 0; k < (VH * VW + NTH - 1) / NTH; ++k) {
-      const int p = tid + k * NTH;
-      if (p < VH * VW) {
-        const int r = p / VW, c = p - r * VW, i = fi0 - 1 + c, j = fj0 - 1 + r;
-        if (i >= 0 && i < n && j >= 0 && j < n) {
-          const int ex = (i & 1) ? (i - 1) / 2 - (I0 - 1) : i / 2 - 1 - (I0 - 1);
-          const int ey = (j & 1) ? (j - 1) / 2 - (J0 - 1) : j / 2 - 1 - (J0 - 1);
-          float pe;
-          if (i & 1) pe = (j & 1) ? se[ey][ex] : 0.5f * (se[ey][ex] + se[ey + 1][ex]);
-          else pe = (j & 1) ? 0.5f * (se[ey][ex] + se[ey][ex + 1])
-                            : 0.25f * ((se[ey][ex] + se[ey][ex + 1]) + (se[ey + 1][ex] + se[ey + 1][ex + 1]));
-          sv[r][c] += pe;
-        }
+    // coarse value and an even one the mean of its two neighbours (zero ghosts);
+    // fine offset c (index fi0 - 1 + c) has its coarse neighbours at se column
+    // c / 2 (and c / 2 + 1 for an even index)
+    for_rows<VH, VW, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 - 1 + c, j = fj0 - 1 + r;
+      if (unsigned(i) < un && unsigned(j) < un) {
+        const int ex = c >> 1, ey = r >> 1;
+        float pe;
+        if (i & 1) pe = (j & 1) ? se[ey][ex] : 0.5f * (se[ey][ex] + se[ey + 1][ex]);
+        else pe = (j & 1) ? 0.5f * (se[ey][ex] + se[ey][ex + 1])
+                          : 0.25f * ((se[ey][ex] + se[ey][ex + 1]) + (se[ey + 1][ex] + se[ey + 1][ex + 1]));
+        sv[r][c] += pe;
       }
-    }
+    });
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KO; ++k) {
-      const int p = tid + k * NTH, r = p / FX, c = p - r * FX, i = fi0 + c, j = fj0 + r;
-      if (i < n && j < n) {
+    for_rows<FY, FX, NW>(warp, lane, [&](int r, int c) {
+      const int i = fi0 + c, j = fj0 + r;
+      if (unsigned(i) < un && unsigned(j) < un) {
         const float vp = sv[r + 1][c + 1];
         float out = vp;
         if (nu2) {
           const float nb = (sv[r + 1][c] + sv[r + 1][c + 2]) + (sv[r][c + 1] + sv[r + 2][c + 1]);
-          out = fmaf(omega, fmaf(kappa, nb, bo[k]) - vp, vp);
+          out = fmaf(omega, fmaf(kappa, nb, fb[i + n * j]) - vp, vp);
         }
         gx[i + n * j] = out;
       }
-    }
+    });
     __syncthreads();  // shared memory is refilled for the block's next tile
   }
 }

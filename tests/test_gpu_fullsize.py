@@ -94,6 +94,31 @@ def test_511_fp32_vcycles_first_step():
     assert R < 1e-10 and err <= 1e-9
 
 
+def test_511_fp32_vcycles_all_steps_satisfy_the_collocation_equations():
+    """All 10 steps of the 511^3 FP32-V-cycle workload: after every step the
+    oracle recomputes, in FP64 on all host cores, the SDC residual of the GPU's
+    node values (the collocation equations of Sec. 2 evaluated at them; an
+    element-wise oracle run of every step would take over an hour on the host).
+    Each must be below the 1e-10 stopping tolerance and agree with the GPU's own
+    residual to 1e-13 absolute; step 1 is compared element by element above."""
+    w = workload_3d_511_mixed()
+    p = O.Problem(3, w.n, w.nu, w.M, w.dt, smoother=RB, nu1=w.nu1, nu2=w.nu2, max_sweeps=200)
+    g = make_gpu(p, vcycle_fp32=True)
+    u = to_dev(initial_condition(3, w.n, w.seed))
+    for step in range(w.steps):
+        assert g.step(u, 0, w.n_vcycles) == 0
+        R = g.residual()
+        sweeps, _ = g.stats()
+        nodes = g.nodes().cpu().numpy()
+        with O.all_cores():
+            R_oracle = O.sdc_residual(p, nodes)
+        del nodes
+        print(f"511^3 FP32 V-cycles step {step + 1}: {sweeps} sweeps, R GPU {R:.3e}, R oracle {R_oracle:.3e}")
+        assert R < 1e-10 and R_oracle < 1e-10 and abs(R_oracle - R) <= 1e-13, (step, R, R_oracle)
+    assert bool(np.isfinite(u.cpu().numpy()).all())
+    g.close()
+
+
 def test_largest_batch_instance_against_the_oracle():
     """The 256-instance batch (one step each) at full size; its largest
     instance (side 1023) and its median one against the FP64 oracle."""
