@@ -283,7 +283,7 @@ def measure(w, args, world, barrier, peak):
     u0 = W.workload_initial(w)
     g = G.Isdc(w.ndim, w.n, w.nu, w.M, w.dt, smoother=w.smoother, nu1=w.nu1, nu2=w.nu2, omega=w.omega,
                vcycle_fp32=w.vcycle_fp32, tol=w.tol, max_sweeps=200, temporal_blocking=args.temporal_blocking,
-               fused_transfer=args.fused_transfer, rb_run=args.rb_run,
+               fused_transfer=args.fused_transfer, rb_run=args.rb_run, use_graphs=args.use_graphs,
                nodes=w.nodes, stencil=w.stencil, equation=w.equation,
                reaction=G.ISDC_REACTION_ALLEN_CAHN if w.reaction == 1 else G.ISDC_REACTION_NONE)
     stream = torch.cuda.current_stream()
@@ -599,6 +599,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--fused-transfer", type=int, default=-1, choices=[-1, 0, 1],
                     help="residual + restriction: -1 tuned per level, 0 two launches, 1 one fused launch")
+    ap.add_argument("--use-graphs", type=int, default=1, choices=[0, 1, 2],
+                    help="sweeps replayed from CUDA graphs: 1 with programmatic dependencies, 2 ordinary, 0 none")
     ap.add_argument("--rb-run", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32, -1, -2, -4, -8],
                     help="3D red-black run form of the natural-layout levels: 0 tuned")
     ap.add_argument("--temporal-blocking", type=int, default=-1, choices=[-1, 0, 1, 2],

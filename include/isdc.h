@@ -84,8 +84,12 @@ typedef struct {
                              cap and a node solve stops early once its max-norm residual is
                              <= mg_tol (one residual check, and host synchronisation, per cycle) */
     int    use_graphs;    /* 1 (default): a sweep with a fixed V-cycle count is captured once as a
-                             CUDA graph and replayed (same kernels, same order); 0: launch one by
-                             one.  With the profiler on, the graph carries its event nodes and the
+                             CUDA graph and replayed (same kernels, same order), each kernel
+                             launched as soon as every block of the one before it has started and
+                             waiting at entry for that kernel to complete (programmatic
+                             dependencies); 2: the same graph with ordinary dependencies; 0:
+                             launch one by one.  Every choice gives the same result bit for bit.
+                             With the profiler on, the graph carries its event nodes and the
                              stream is synchronised after every replay to read them. */
     int    temporal_blocking; /* 3D, FP32 V-cycles, red-black: smoothing of the fine level.
                              -1 (default): chosen by the autotuner in isdc_create.  0: one pass

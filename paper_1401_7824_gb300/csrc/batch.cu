@@ -477,6 +477,10 @@ isdc_status capture(isdc_batch* b, int shape) {
           ++b->kernel_nodes[shape];
       }
   }
+  if ((e = host::programmatic_edges(g)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return bfail(b, ISDC_ERR_CUDA, "tick graph edges: %s", cudaGetErrorString(e));
+  }
   e = cudaGraphInstantiate(&b->exec[shape], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));

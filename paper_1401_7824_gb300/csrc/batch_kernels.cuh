@@ -205,6 +205,7 @@ __device__ __forceinline__ void pb_sweep_end(const Inst* __restrict__ insts, con
 template <int DIM>
 __global__ void kb_jacobi(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega,
                           int src_t, int zero) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& V = I.lev[l];
@@ -226,6 +227,7 @@ __global__ void kb_jacobi(const Inst* __restrict__ insts, const List* __restrict
 template <int DIM>
 __global__ void kb_rbgs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, int colour,
                         int zero) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& V = I.lev[l];
@@ -239,6 +241,7 @@ __global__ void kb_rbgs(const Inst* __restrict__ insts, const List* __restrict__
 // Scaled residual of level l (red points only after a red-black sweep).
 template <int DIM, bool RED_ONLY>
 __global__ void kb_residual(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, int src_t) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& V = I.lev[l];
@@ -257,6 +260,7 @@ __global__ void kb_residual(const Inst* __restrict__ insts, const List* __restri
 
 template <int DIM, bool RED_ONLY>
 __global__ void kb_restrict(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& C = I.lev[l + 1];
@@ -271,6 +275,7 @@ __global__ void kb_restrict(const Inst* __restrict__ insts, const List* __restri
 template <int DIM, bool BLACK_ONLY>
 __global__ void kb_prolong(const Inst* __restrict__ insts, const List* __restrict__ list, int l, int dst_t,
                            int src_t) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& C = I.lev[l + 1];
@@ -287,6 +292,7 @@ __global__ void kb_prolong(const Inst* __restrict__ insts, const List* __restric
 // iterate) so that the prolongation reads one location for every instance.
 template <int DIM>
 __global__ void kb_coarse(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int dst_t) {
+  grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& V = I.lev[I.nlev - 1];
@@ -526,36 +532,43 @@ __device__ __forceinline__ void pb_up2(const Inst* __restrict__ insts, const Lis
 // Kernels of the phases (one launch each in the tick's graph).
 template <int DIM>
 __global__ void kb_spread(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction) {
+  grid_dep_wait();
   pb_spread<DIM>(insts, list, reaction);
 }
 template <int DIM>
 __global__ void kb_rhs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int reaction) {
+  grid_dep_wait();
   pb_rhs<DIM>(insts, list, m, reaction);
 }
 template <int DIM>
 __global__ void kb_update(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int from_t) {
+  grid_dep_wait();
   pb_update<DIM>(insts, list, m, from_t);
 }
 template <int DIM, int M>
 __global__ void kb_sweep_end(const Inst* __restrict__ insts, const List* __restrict__ list, int reaction,
                              unsigned long long* __restrict__ rbits) {
+  grid_dep_wait();
   pb_sweep_end<DIM, M>(insts, list, reaction, rbits);
 }
 template <int DIM>
 __global__ void __launch_bounds__(kBottomThreads)
     kb_bottom(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int load_x, int smoother,
               int nu1, int nu2, float omega) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pb_bottom<DIM>(insts, list, m, load_x, smoother, nu1, nu2, omega, smem_raw);
 }
 template <int TY>
 __global__ void __launch_bounds__(32 * TY)
     kb_down2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int zero) {
+  grid_dep_wait();
   pb_down2<TY>(insts, list, m, l, omega, zero);
 }
 template <int TY>
 __global__ void __launch_bounds__(32 * TY)
     kb_up2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int nu2) {
+  grid_dep_wait();
   pb_up2<TY>(insts, list, m, l, omega, nu2);
 }
 
@@ -624,6 +637,7 @@ __global__ void __launch_bounds__(32 * TY)
     kb_tick2(const Inst* __restrict__ insts, const List* __restrict__ lists, const Phase* __restrict__ phases,
              int nphases, int reaction, float omega, int nu1, int nu2, unsigned long long* __restrict__ rbits,
              unsigned long long* __restrict__ scratch, GridBarrier* gb) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int q = 0; q < nphases; ++q) {
     const Phase P = phases[q];

@@ -33,6 +33,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBX* kBY)
     k_jacobi9(int n, T ke, T kc, T omega, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ xo,
               int zero_guess) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY)
     k_residual9(int n, T ke, T kc, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ r) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -59,6 +61,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 __global__ void __launch_bounds__(kBX* kBY)
     k_resnorm9(int n, double ke, double kc, double c0, const double* __restrict__ x, const double* __restrict__ beta,
                unsigned long long* __restrict__ out) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   unsigned long long rb = 0;
   if (i < n && j < n) {
@@ -99,6 +102,7 @@ __device__ void bt9_smooth(const BottomParams9& P, int l, double* x, const doubl
 
 __global__ void __launch_bounds__(kBottomThreads)
     k_bottom9(BottomParams9 P, const double* __restrict__ b_top, double* __restrict__ x_top, int load_x) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* base = reinterpret_cast<double*>(smem_raw);
   double *X[kMaxLevels], *B[kMaxLevels], *Tt[kMaxLevels];
@@ -175,6 +179,7 @@ __device__ __forceinline__ void ftilde_at(const double* __restrict__ u, int i, i
 __global__ void __launch_bounds__(kBX* kBY)
     k_spread9(int n, size_t N, double nu6, int reaction, int P, const double* __restrict__ u, double* __restrict__ U,
               double* __restrict__ Ft, double* __restrict__ G) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 __global__ void __launch_bounds__(kBX* kBY)
     k_eval_f9(int n, double nu6, int reaction, const double* __restrict__ u, double* __restrict__ ft,
               double* __restrict__ g) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_rhs9(int n, double nu6, int reaction, double dtm, double inv_c0, const double* __restrict__ Um,
            const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Ftm,
            double* __restrict__ Gm) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -236,6 +243,7 @@ template <int OFF, int P>
 __global__ void __launch_bounds__(kBX* kBY)
     k_sweep_end9(int n, size_t N, double nu6, int reaction, SweepTables tb, const double* __restrict__ U,
                  double* __restrict__ Ft, double* __restrict__ G, double* __restrict__ C, double* __restrict__ Rho) {
+  grid_dep_wait();
   constexpr int M = P - OFF;
   static_assert(M >= 2 && M <= kMaxM && P <= kMaxP, "point count out of range");
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
@@ -284,6 +292,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 __global__ void __launch_bounds__(kBX* kBY)
     k_winv_jacobi(int n, size_t N, const double* __restrict__ rho, const double* __restrict__ rin,
                   double* __restrict__ rout) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const size_t base = size_t(blockIdx.z) * N;
@@ -295,6 +304,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 // Max-norm over total values (grid-stride), integer max of the bit patterns.
 __global__ void __launch_bounds__(256) k_maxabs(size_t total, const double* __restrict__ v,
                                                 unsigned long long* __restrict__ out) {
+  grid_dep_wait();
   unsigned long long rb = 0;
   for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < total; q += size_t(gridDim.x) * blockDim.x) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]) & 0x7fffffffffffffffull;
@@ -312,6 +322,7 @@ __global__ void __launch_bounds__(256) k_maxabs(size_t total, const double* __re
 // (the W^{-1} of it follows by k_winv_jacobi), part 2 below.
 __global__ void __launch_bounds__(kBX* kBY)
     k_gauss_end9_sum(int n, size_t N, EndWeights ew, const double* __restrict__ G, double* __restrict__ y) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;
@@ -326,6 +337,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 __global__ void __launch_bounds__(kBX* kBY)
     k_gauss_end9(int n, size_t N, EndWeights ew, int reaction, const double* __restrict__ U,
                  const double* __restrict__ winv_y, double* __restrict__ u) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n || j >= n) return;
   const int p = i + n * j;

@@ -3,8 +3,11 @@
 // Gauss-Radau and Gauss-Legendre nodes, Q, full-step weights) and the dense
 // inverse of the side-3 multigrid operator.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace isdc {
@@ -241,6 +244,42 @@ inline void coarse_inverse_per(int dim, double a, std::vector<double>& inv) {
       }
     }
   }
+}
+
+// Rewrite the kernel-to-kernel edges of a captured graph as programmatic
+// dependencies on the upstream kernel's launch-completion port: a downstream
+// kernel may be launched once every block of the upstream one has started, and
+// its blocks wait at entry (grid_dep_wait) until the upstream kernel has
+// completed and its writes are visible.  Launch processing of each kernel then
+// overlaps the kernel before it; the order of all memory effects is unchanged.
+// Edges that touch non-kernel nodes (copies, memsets, events) stay ordinary.
+inline cudaError_t programmatic_edges(cudaGraph_t g) {
+  size_t ne = 0;
+  cudaError_t e = cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne);
+  if (e != cudaSuccess || ne == 0) return e;
+  std::vector<cudaGraphNode_t> from(ne), to(ne);
+  std::vector<cudaGraphEdgeData> data(ne);
+  if ((e = cudaGraphGetEdges(g, from.data(), to.data(), data.data(), &ne)) != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> f, t;
+  for (size_t q = 0; q < ne; ++q) {
+    cudaGraphNodeType a, b;
+    if (cudaGraphNodeGetType(from[q], &a) != cudaSuccess || cudaGraphNodeGetType(to[q], &b) != cudaSuccess) continue;
+    if (a == cudaGraphNodeTypeKernel && b == cudaGraphNodeTypeKernel && data[q].type == cudaGraphDependencyTypeDefault &&
+        data[q].from_port == cudaGraphKernelNodePortDefault) {
+      f.push_back(from[q]);
+      t.push_back(to[q]);
+    }
+  }
+  if (f.empty()) return cudaSuccess;
+  std::vector<cudaGraphEdgeData> plain(f.size()), prog(f.size());
+  std::memset(plain.data(), 0, plain.size() * sizeof(cudaGraphEdgeData));
+  std::memset(prog.data(), 0, prog.size() * sizeof(cudaGraphEdgeData));
+  for (auto& d : prog) {
+    d.from_port = cudaGraphKernelNodePortLaunchCompletion;
+    d.type = cudaGraphDependencyTypeProgrammatic;
+  }
+  if ((e = cudaGraphRemoveDependencies(g, f.data(), t.data(), plain.data(), f.size())) != cudaSuccess) return e;
+  return cudaGraphAddDependencies(g, f.data(), t.data(), prog.data(), f.size());
 }
 
 }  // namespace host

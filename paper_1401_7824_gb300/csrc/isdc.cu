@@ -1322,6 +1322,10 @@ isdc_status capture_sweep(isdc_ctx* ctx, int n_vcycles) {
     return st;
   }
   if (e != cudaSuccess) return fail(ctx, ISDC_ERR_CUDA, "sweep capture: %s", cudaGetErrorString(e));
+  if (ctx->opt.use_graphs == 1 && (e = host::programmatic_edges(g)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(ctx, ISDC_ERR_CUDA, "sweep graph edges: %s", cudaGetErrorString(e));
+  }
   e = cudaGraphInstantiate(&ctx->sweep_graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(ctx, ISDC_ERR_CUDA, "sweep graph: %s", cudaGetErrorString(e));
@@ -1636,6 +1640,9 @@ template <typename T, int DIM>
 isdc_status tune_transfer(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, cudaEvent_t e0, cudaEvent_t e1) {
   int* rr = sizeof(T) == 8 ? ctx->rr64 : ctx->rr32;
   const int cand3[4] = {0, 4, 8, 16}, cand2[2] = {0, 1};
+  int dev = 0, sms = 0;
+  CUDA_TRY(ctx, cudaGetDevice(&dev));
+  CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   for (int l = 0; l < H.lb; ++l) {
     const bool split = l == 0 && split0;
     T* x = l == 0 ? x0 : H.x[l];
@@ -1654,6 +1661,14 @@ isdc_status tune_transfer(isdc_ctx* ctx, Hier<T>& H, T* x0, T* b0, bool split0, 
     for (int round = 0; round < 3; ++round)  // the first round warms up
       for (int c = 0; c < nc; ++c) {
         const int kc = DIM == 3 ? cand3[c] : cand2[c];
+        if (kc > 0) {
+          // a fused launch with fewer than two blocks per SM loses to the two
+          // launches inside the replayed sweep (measured on the 127^2 workload:
+          // 181.7 against 160 us per sweep) while winning a back-to-back timing
+          // loop, so it is not a candidate there
+          const dim3 gf = resrestrict_grid(DIM, H.side[l + 1], kc);
+          if (size_t(gf.x) * gf.y * gf.z < size_t(2) * sms) continue;
+        }
         float ms = 0.f;
         isdc_status st = time_transfer<T, DIM>(ctx, H, l, x, b, split, kc, reps, e0, e1, &ms);
         if (st != ISDC_OK) return st;
@@ -1846,6 +1861,7 @@ ISDC_API isdc_status isdc_create(int ndim, const int64_t* dims, double nu, isdc_
                     r == 16 || r == 32;
     if (!ok) return fail(nullptr, ISDC_ERR_INVALID_ARG, "rb_run must be 0, 1, 2, 4, 8, 16, 32, -1, -2, -4 or -8");
   }
+  if (o.use_graphs < 0 || o.use_graphs > 2) return fail(nullptr, ISDC_ERR_INVALID_ARG, "use_graphs must be 0, 1 or 2");
   if (o.fused_transfer < -1 || o.fused_transfer > 1)
     return fail(nullptr, ISDC_ERR_INVALID_ARG, "fused_transfer must be -1, 0 or 1");
   if (o.stencil != 0 && o.stencil != 1) return fail(nullptr, ISDC_ERR_INVALID_ARG, "unknown stencil %d", o.stencil);

@@ -16,6 +16,12 @@
 
 namespace isdc {
 
+// Entry of every kernel: when the kernel was launched through a programmatic
+// edge of a replayed graph (its launch overlapping the end of the kernel before
+// it), wait until that kernel has completed and its writes are visible; after
+// an ordinary launch this returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 constexpr int kBX = 32;  // threads along x (one warp)
 constexpr int kBY = 8;   // rows per block
 
@@ -54,6 +60,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_jacobi(int n, T kappa, T omega, const T* __restrict__ x, const T* __restrict__ beta,
              T* __restrict__ xo, int zero_guess) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -76,6 +83,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs2(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+  grid_dep_wait();
   const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (j >= n) return;
   // (i+1)+(j+1) parity == colour  <=>  i parity == (colour + j) & 1
@@ -98,6 +106,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs3(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess, int zb) {
+  grid_dep_wait();
   const int ih = blockIdx.x * kBX + threadIdx.x;
   const int jd = int(blockIdx.y * kBY + threadIdx.y) - (zb - 1);
   const int k0 = blockIdx.z * zb;
@@ -143,6 +152,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T, int ZB>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs3_burst(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+  grid_dep_wait();
   const int ih = blockIdx.x * kBX + threadIdx.x;
   const int jd = int(blockIdx.y * kBY + threadIdx.y) - (ZB - 1);
   const int k0 = blockIdx.z * ZB;
@@ -207,6 +217,7 @@ inline void launch_rbgs(cudaStream_t st, int n, T kappa, int colour, T* x, const
 template <typename T, int DIM, bool RED_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
     k_residual(int n, T kappa, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ r) {
+  grid_dep_wait();
   const int t = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int i = RED_ONLY ? 2 * t + ((j + (DIM == 3 ? k : 0) + DIM) & 1) : t;
@@ -267,6 +278,7 @@ __device__ __forceinline__ T restrict_point(int nc, T wscale, const T* __restric
 template <typename T, int DIM, bool RED_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
     k_restrict(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
+  grid_dep_wait();
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= nc || J >= nc) return;
@@ -341,6 +353,7 @@ __device__ __forceinline__ void prolong_cell(int nc, const T* __restrict__ ec, T
 template <typename T, int DIM, bool BLACK_ONLY = false>
 __global__ void __launch_bounds__(kBX* kBY)
     k_prolong_add(int nc, const T* __restrict__ ec, T* __restrict__ x) {
+  grid_dep_wait();
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   const int K = blockIdx.z;
   if (I > nc || J > nc) return;
@@ -355,6 +368,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_defect(int n, double kappa, const double* __restrict__ x, const double* __restrict__ beta,
              float* __restrict__ r32) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -365,6 +379,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 // beta = b / d (scaling of a caller's right-hand side).
 template <typename T>
 __global__ void k_scale(size_t N, T s, const T* __restrict__ b, T* __restrict__ beta) {
+  grid_dep_wait();
   for (size_t p = blockIdx.x * size_t(blockDim.x) + threadIdx.x; p < N; p += size_t(gridDim.x) * blockDim.x)
     beta[p] = s * b[p];
 }
@@ -372,6 +387,7 @@ __global__ void k_scale(size_t N, T s, const T* __restrict__ b, T* __restrict__ 
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_update(int n, double* __restrict__ x, const float* __restrict__ e32) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -415,6 +431,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_defect_split(int n, double kappa, const double* __restrict__ x, const double* __restrict__ beta,
                    float* __restrict__ r0, float* __restrict__ r1) {
+  grid_dep_wait();
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
@@ -436,6 +453,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_update_split(int n, double* __restrict__ x, const float* __restrict__ e0, const float* __restrict__ e1) {
+  grid_dep_wait();
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
@@ -455,6 +473,7 @@ template <int DIM, int ZB>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs_split(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
                  const float* __restrict__ bc, int zero_guess) {
+  grid_dep_wait();
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int H = (n + 1) >> 1;
   if (j >= n) return;
@@ -481,6 +500,7 @@ template <int DIM, int ZB>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs_split4(int n, float kappa, int colour, float* __restrict__ xc, const float* __restrict__ xo,
                   const float* __restrict__ bc, int zero_guess) {
+  grid_dep_wait();
   const int h = (blockIdx.x * kBX + threadIdx.x) * 4, j = blockIdx.y * kBY + threadIdx.y;
   const int H = (n + 1) >> 1;
   if (j >= n || h >= H) return;
@@ -696,6 +716,7 @@ __global__ void __launch_bounds__(kTbThreads, 2)
     k_rbgs_split_tb(int n, float kappa, const float* __restrict__ xb_in, float* __restrict__ xr_out,
                     float* __restrict__ xb_out, const float* __restrict__ br, const float* __restrict__ bb,
                     int zero_guess, int zc) {
+  grid_dep_wait();
   using Sh = TbShape<S>;
   extern __shared__ float sm[];
   const int H = (n + 1) >> 1;
@@ -739,6 +760,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_residual_red_split(int n, float kappa, const float* __restrict__ xr, const float* __restrict__ xb,
                          const float* __restrict__ br, float* __restrict__ rr) {
+  grid_dep_wait();
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
@@ -754,6 +776,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_restrict_red_split(int nc, float wscale, const float* __restrict__ rr, float* __restrict__ bc) {
+  grid_dep_wait();
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= nc || J >= nc) return;
@@ -778,6 +801,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_prolong_black_split(int nc, const float* __restrict__ ec, float* __restrict__ x0, float* __restrict__ x1) {
+  grid_dep_wait();
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   const int K = blockIdx.z;
   if (I > nc || J > nc) return;
@@ -941,6 +965,7 @@ __device__ __forceinline__ void bottom_vcycle(const BottomParams<T>& P, const T*
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBottomThreads)
     k_bottom(BottomParams<T> P, const T* __restrict__ b_top, T* __restrict__ x_top, int load_x) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bottom_vcycle<T, DIM>(P, b_top, x_top, load_x, smem_raw);
 }

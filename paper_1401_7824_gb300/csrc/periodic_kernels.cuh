@@ -35,6 +35,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_jacobi_per(int n, T kappa, T omega, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ xo,
                  int zero_guess) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = plin<DIM>(i, j, k, n);
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_rbgs_per(int n, T kappa, int colour, T* __restrict__ x, const T* __restrict__ beta, int zero_guess) {
+  grid_dep_wait();
   const int ih = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   if (2 * ih >= n || j >= n) return;
   const int i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0)) & 1);
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_residual_per(int n, T kappa, const T* __restrict__ x, const T* __restrict__ beta, T* __restrict__ r) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int p = plin<DIM>(i, j, k, n);
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_restrict_per(int nc, T wscale, const T* __restrict__ r, T* __restrict__ bc) {
+  grid_dep_wait();
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y, K = blockIdx.z;
   if (I >= nc || J >= nc) return;
   const int n = 2 * nc, w = n - 1;
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(kBX* kBY)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_prolong_per(int nc, const T* __restrict__ ec, T* __restrict__ x) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   const int n = 2 * nc, w = nc - 1;
   if (i >= n || j >= n) return;
@@ -122,6 +127,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_resnorm_per(int n, double kappa, double d, const double* __restrict__ x, const double* __restrict__ beta,
                   unsigned long long* __restrict__ out) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   unsigned long long rb = 0;
   if (i < n && j < n) {
@@ -175,6 +181,7 @@ __device__ void btp_smooth(const BottomParamsPer& P, int l, double* x, const dou
 template <int DIM>
 __global__ void __launch_bounds__(kBottomThreads)
     k_bottom_per(BottomParamsPer P, const double* __restrict__ b_top, double* __restrict__ x_top, int load_x) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* base = reinterpret_cast<double*>(smem_raw);
   double *X[kMaxLevels], *B[kMaxLevels], *Tt[kMaxLevels];
@@ -375,6 +382,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_spread_b(int n, size_t N, double nu_h2, double inv_h, int P, const double* __restrict__ u,
                double* __restrict__ U, double* __restrict__ F, double* __restrict__ FE) {
+  grid_dep_wait();
   __shared__ WenoTile S;
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   const double fe = burgers_fe<DIM>(u, k, n, inv_h, S);  // every thread of the block takes part
@@ -394,6 +402,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_eval_f_b(int n, double nu_h2, double inv_h, const double* __restrict__ u, double* __restrict__ f,
                double* __restrict__ fe) {
+  grid_dep_wait();
   __shared__ WenoTile S;
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   const double e = burgers_fe<DIM>(u, k, n, inv_h, S);
@@ -413,6 +422,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_rhs_b(int n, double nu_h2, double inv_h, double dtm, double inv_d, const double* __restrict__ Um,
             const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm,
             double* __restrict__ FEm, int fresh) {
+  grid_dep_wait();
   __shared__ WenoTile S;
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   const double fnew = fresh ? burgers_fe<DIM>(Um, k, n, inv_h, S) : 0.0;  // fresh is uniform
@@ -437,6 +447,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_sweep_end_b(int n, size_t N, double nu_h2, double inv_h, SweepTables tb, const double* __restrict__ U,
                   double* __restrict__ F, double* __restrict__ FE, double* __restrict__ C,
                   unsigned long long* __restrict__ Rbits) {
+  grid_dep_wait();
   constexpr int M = P - OFF;
   static_assert(M >= 2 && M <= kMaxM && P <= kMaxP, "point count out of range");
   __shared__ WenoTile S;

@@ -167,6 +167,7 @@ template <typename T, int DIM, bool RED_ONLY>
 __global__ void __launch_bounds__(kRrThreads)
     k_resrestrict(int nc, T kappa, T wscale, const T* __restrict__ x, const T* __restrict__ beta,
                   T* __restrict__ bc, int kc) {
+  grid_dep_wait();
   const ResNatural<T, DIM> src{x, beta, kappa, 2 * nc + 1};
   resrestrict_tile<T, DIM, RED_ONLY>(src, nc, wscale, bc, kc);
 }
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kRrThreads)
     k_resrestrict_red_split(int nc, float kappa, float wscale, const float* __restrict__ xr,
                             const float* __restrict__ xb, const float* __restrict__ br, float* __restrict__ bc,
                             int kc) {
+  grid_dep_wait();
   const int n = 2 * nc + 1;
   const ResSplitRed<DIM> src{xr, xb, br, kappa, n, (n + 1) >> 1};
   resrestrict_tile<float, DIM, true>(src, nc, wscale, bc, kc);

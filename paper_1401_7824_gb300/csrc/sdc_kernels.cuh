@@ -27,6 +27,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_spread(int n, size_t N, double nu_h2, int reaction, int M, const double* __restrict__ u,
              double* __restrict__ U, double* __restrict__ F, double* __restrict__ FE) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -46,6 +47,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_eval_f(int n, double nu_h2, int reaction, const double* __restrict__ u, double* __restrict__ f,
              double* __restrict__ fe_out) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_rhs(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
           const double* __restrict__ Cm, double* __restrict__ beta, double* __restrict__ Fm,
           double* __restrict__ FEm) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_rhs_defect(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
                  const double* __restrict__ Cm, double* __restrict__ Fm, double* __restrict__ FEm,
                  float* __restrict__ r32) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -123,6 +127,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_rhs_defect_split(int n, double nu_h2, int reaction, double dtm, double inv_d, const double* __restrict__ Um,
                        const double* __restrict__ Cm, double* __restrict__ Fm, double* __restrict__ FEm,
                        float* __restrict__ r0, float* __restrict__ r1) {
+  grid_dep_wait();
   const int h = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   const int H = (n + 1) >> 1;
@@ -169,6 +174,7 @@ __global__ void __launch_bounds__(kBX* kBY)
     k_sweep_end(int n, size_t N, double nu_h2, int reaction, int cmode, SweepTables tb,
                 const double* __restrict__ U, double* __restrict__ F, const double* __restrict__ FE,
                 double* __restrict__ C, unsigned long long* __restrict__ Rbits) {
+  grid_dep_wait();
   constexpr int M = P - OFF;  // nodes; node j is point j + OFF
   static_assert(M >= 2 && M <= kMaxM && P <= kMaxP, "point count out of range");
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
@@ -233,6 +239,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_gauss_end(int n, size_t N, EndWeights ew, const double* __restrict__ U, const double* __restrict__ F,
                 double* __restrict__ u) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= n || j >= n) return;
@@ -249,6 +256,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX* kBY)
     k_resnorm(int n, double kappa, double d, const double* __restrict__ x, const double* __restrict__ beta,
               unsigned long long* __restrict__ out) {
+  grid_dep_wait();
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   const int k = blockIdx.z;
   unsigned long long rb = 0;

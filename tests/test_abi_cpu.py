@@ -88,7 +88,7 @@ def test_host_validation_without_gpu():
     # option values outside their sets are refused before any device work
     for field, bad in [("rb_run", 3), ("rb_run", -16), ("rb_run", 64), ("temporal_blocking", 3),
                        ("smoother", 2), ("nu1", 17), ("stencil", 2), ("reaction", 5), ("max_sweeps", 0),
-                       ("fused_transfer", 2), ("fused_transfer", -2)]:
+                       ("fused_transfer", 2), ("fused_transfer", -2), ("use_graphs", 3), ("use_graphs", -1)]:
         o = G.isdc_default_options()
         setattr(o, field, bad)
         with pytest.raises(G.IsdcError) as e:

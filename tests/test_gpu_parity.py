@@ -240,21 +240,27 @@ def test_invalid_arguments_are_rejected():
 
 
 @pytest.mark.parametrize("fp32", [False, True])
-def test_sweep_graph_replay_is_bitwise_identical(fp32):
-    """A sweep replayed from its captured CUDA graph runs the same kernels in
-    the same order as launching them one by one."""
-    p = O.Problem(3, 31, 0.1, 5, 0.02, smoother=RB, nu1=2, nu2=2)
-    u0 = initial_condition(3, 31, seed=21)
+@pytest.mark.parametrize("dim,n,sm", [(3, 31, RB), (3, 127, RB), (2, 255, J)])
+def test_sweep_graph_replay_is_bitwise_identical(fp32, dim, n, sm):
+    """A sweep replayed from its captured CUDA graph (with programmatic
+    dependencies between kernels, the default, and with ordinary ones) runs the
+    same kernels in the same order as launching them one by one: the same
+    values bit for bit, so every kernel's entry wait orders it after the one
+    before it."""
+    p = O.Problem(dim, n, 0.1, 5, 0.02, smoother=sm, nu1=2, nu2=2, max_sweeps=150)
+    u0 = initial_condition(dim, n, seed=21)
     outs = []
-    for graphs in (True, False):
-        g = make_gpu(p, vcycle_fp32=fp32, use_graphs=graphs)
+    for graphs in (1, 2, 0):
+        g = make_gpu(p, vcycle_fp32=fp32, use_graphs=graphs, fused_transfer=0, rb_run=4 if dim == 3 else 0)
         u = to_dev(u0)
         for _ in range(2):
             g.step(u, 0, 2)
         outs.append((u.cpu().numpy(), g.stats(), g.history()))
-    np.testing.assert_array_equal(outs[0][0], outs[1][0])
-    assert outs[0][1] == outs[1][1]
-    assert outs[0][2] == outs[1][2]
+        g.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0][0], o[0])
+        assert outs[0][1] == o[1]
+        assert outs[0][2] == o[2]
 
 
 def test_fp32_red_black_2d_split_layout_converges_to_oracle():
