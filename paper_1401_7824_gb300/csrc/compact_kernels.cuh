@@ -301,6 +301,24 @@ __global__ void __launch_bounds__(kBX* kBY)
   rout[base + p] = fma(-0.125, e, 1.5 * rho[base + p]);
 }
 
+// One Chebyshev semi-iteration step for the same system (Golub-Varga, for
+// y = T y + c with the spectrum of T = -(1/8) E inside [-1/2, 1/2]):
+//   y_{k+1} = omega (T y_k + c - y_{k-1}) + y_{k-1},  c = (3/2) rho,
+// with y_{k-1} = 0 when yprev == nullptr.  yout may be yprev (every point
+// reads its own y_{k-1} before writing it).
+__global__ void __launch_bounds__(kBX* kBY)
+    k_winv_cheb(int n, size_t N, double omega, const double* __restrict__ rho, const double* __restrict__ ycur,
+                const double* yprev, double* yout) {
+  grid_dep_wait();
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const size_t base = size_t(blockIdx.z) * N;
+  const int p = i + n * j;
+  const double jac = fma(-0.125, nbsum<double, 2>(ycur + base, i, j, 0, n, p), 1.5 * rho[base + p]);
+  const double yp = yprev ? yprev[base + p] : 0.0;
+  yout[base + p] = fma(omega, jac - yp, yp);
+}
+
 // Max-norm over total values (grid-stride), integer max of the bit patterns.
 __global__ void __launch_bounds__(256) k_maxabs(size_t total, const double* __restrict__ v,
                                                 unsigned long long* __restrict__ out) {

@@ -816,26 +816,40 @@ isdc_status node_residual_norm9(isdc_ctx* ctx, double a, const double* x, const 
   return ISDC_OK;
 }
 
-// W^{-1} of `count` arrays rho (each N) by Jacobi steps r <- (3/2) rho - E(r)/8,
-// starting from 0; the result is in *res (one of the two scratch sets).
-constexpr int kWinvSweepIters = 16;  // residual for the stopping test: error <= 4.5 * 2^-16 relative
-constexpr int kWinvEndIters = 54;    // Gauss-Legendre end value: error below FP64 rounding
+// W^{-1} of `count` arrays rho (each N) by the Chebyshev semi-iteration on the
+// Jacobi splitting r <- (3/2) rho - E(r)/8 (W = (2/3)(I + E/8); the Jacobi
+// iteration matrix -E/8 has its spectrum inside [-1/2, 1/2]), starting from 0:
+// after k steps the error is at most 2 / T_k(2) of the initial one in the
+// 2-norm (T_k the Chebyshev polynomial), against 2^-k for plain Jacobi steps
+// at three quarters of the traffic per step.  The result is in *res (one of the
+// two scratch sets; each step overwrites the iterate two steps back).
+constexpr int kWinvSweepIters = 12;  // residual for the stopping test: 2 / T_12(2) = 5.4e-7 relative
+constexpr int kWinvEndIters = 29;    // Gauss-Legendre end value: 2 / T_29(2) below FP64 rounding
 isdc_status w_inverse(isdc_ctx* ctx, int count, const double* rho, double* s0, double* s1, int iters,
                       const double** res) {
   const int n = ctx->n;
   const size_t N = ctx->N;
   const dim3 g(unsigned((n + kBX - 1) / kBX), unsigned((n + kBY - 1) / kBY), unsigned(count));
-  const double* in = nullptr;
-  for (int it = 0; it < iters; ++it) {
-    double* out = (it & 1) ? s1 : s0;
+  {
+    ProfScope ps(ctx, PC_WINV, 2.0 * 8.0 * double(N) * count, 1.0 * double(N) * count, true);
+    k_winv_jacobi<<<g, kBlock, 0, ctx->stream>>>(n, N, rho, nullptr, s0);  // y_1 = (3/2) rho
+  }
+  LAUNCH_CHECK(ctx);
+  const double* prev = nullptr;  // y_{k-1} (y_0 = 0)
+  double* cur = s0;              // y_k
+  double omega = 1.0;
+  for (int k = 1; k < iters; ++k) {
+    omega = k == 1 ? 2.0 / (2.0 - 0.25) : 1.0 / (1.0 - 0.0625 * omega);  // rho^2 = 1/4
+    double* out = prev ? const_cast<double*>(prev) : s1;
     {
-      ProfScope ps(ctx, PC_WINV, (it ? 3.0 : 2.0) * 8.0 * double(N) * count, 6.0 * double(N) * count, true);
-      k_winv_jacobi<<<g, kBlock, 0, ctx->stream>>>(n, N, rho, in, out);
+      ProfScope ps(ctx, PC_WINV, (prev ? 4.0 : 3.0) * 8.0 * double(N) * count, 8.0 * double(N) * count, true);
+      k_winv_cheb<<<g, kBlock, 0, ctx->stream>>>(n, N, omega, rho, cur, prev, out);
     }
     LAUNCH_CHECK(ctx);
-    in = out;
+    prev = cur;
+    cur = out;
   }
-  *res = in;
+  *res = cur;
   return ISDC_OK;
 }
 
