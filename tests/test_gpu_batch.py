@@ -91,6 +91,32 @@ def test_batch_temporal_blocking_depths_match_fp64_oracle(depth):
         assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_batch_every_node_count_matches_fp64_oracle(ndim):
+    """The sweep end is compiled per node count (one work list per M): an
+    engine with max_M = 7 holding instances with M = 2, 4, 6 and 7 (2D damped
+    Jacobi, fused passes; 3D red-black with side 63, two grid-wide levels above
+    the per-instance bottom block) against the FP64 oracle."""
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    if ndim == 2:
+        probs = [(127, 0.2, 2, 0.05, 2), (255, 0.05, 4, 0.02, 1), (63, 0.5, 6, 0.05, 1), (127, 0.02, 7, 0.1, 1)]
+        eng = G.Batch(2, 255, 7, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+        sm, nu1 = O.SMOOTHER_JACOBI, 1
+    else:
+        probs = [(63, 0.1, 2, 0.05, 1), (63, 0.05, 4, 0.02, 1), (31, 0.5, 6, 0.05, 1), (15, 1.0, 7, 0.02, 1)]
+        eng = G.Batch(3, 63, 7, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_RBGS, nu1=2, nu2=2, max_sweeps=150)
+        sm, nu1 = O.SMOOTHER_RBGS, 2
+    got = _run(eng, probs, ndim, 170)
+    eng.close()
+    for q, (n, nu, M, dt, steps) in enumerate(probs):
+        p = O.Problem(ndim, n, nu, M, dt, smoother=sm, nu1=nu1, nu2=nu1, max_sweeps=150)
+        with O.all_cores():
+            ref = O.integrate(p, initial_condition(ndim, n, 170 + q), steps, 0, 2)
+        assert all(s == 0 for s in ref.status)
+        assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
+
+
 def test_batch_launch_shapes_give_identical_results():
     """An instance admitted into a fresh engine sweeps through the autotuner's
     trial ticks (every graph shape, then the persistent one-launch ticks), the

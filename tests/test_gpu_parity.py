@@ -432,6 +432,17 @@ def test_fused_transfer_whole_steps_match_two_launch_form():
     g.close()
 
 
+def test_transfer_tuner_skips_fused_form_on_underfilled_levels():
+    """The fused residual + restriction is offered to the autotuner only on
+    levels whose fused grid has at least two blocks per SM: on the 127^2
+    workload (coarse sides 63 and below) every level keeps the two launches."""
+    p = O.Problem(2, 127, 0.1, 3, 0.05)
+    g = make_gpu(p)
+    kc = g.tuning()["transfer_kc"]
+    g.close()
+    assert len(kc) >= 1 and all(k == 0 for k in kc), kc
+
+
 def test_red_black_run_option_is_validated():
     import paper_1401_7824_gb300 as G
     p = O.Problem(3, 31, 0.1, 3, 0.02, smoother=RB, nu1=2, nu2=2)
