@@ -455,31 +455,43 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """256 independent 2D instances (sides 2^j - 1, j in 6..10; nu, dt, M drawn
-    from seed 4) in one batch engine: FP32 V-cycles, FP64 SDC state, damped
-    Jacobi V(1,1), L = 2.  One bench step = one tick = one SDC sweep of every
-    running instance (one CUDA graph launch).  Warm-up ticks include the
-    autotuner's trial ticks."""
+    """batch_2d_256: 256 independent 2D instances (sides 2^j - 1, j in 6..10;
+    nu, dt, M drawn from seed 4), damped Jacobi V(1,1).  batch_3d_32: 32
+    independent 3D instances (sides 63..255, seed 6), red-black Gauss-Seidel
+    V(2,2).  One batch engine each: FP32 V-cycles, FP64 SDC state, L = 2.  One
+    bench step = one tick = one SDC sweep of every running instance (one CUDA
+    graph launch).  Warm-up ticks include the autotuner's trial ticks."""
     import torch
     import paper_1401_7824_gb300 as G
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    insts = W.batch_instances(args.instances, seed=4)
+    ndim = 3 if args.workload.startswith("batch_3d") else 2
+    if ndim == 2:
+        insts = W.batch_instances(args.instances, seed=4)
+    else:
+        insts = W.batch_instances_3d(min(args.instances, 32), seed=6)
     stream = torch.cuda.Stream()
     o = G.isdc_default_options()
-    o.smoother, o.nu1, o.nu2, o.vcycle_fp32, o.tol, o.max_sweeps = G.ISDC_SMOOTHER_JACOBI, 1, 1, 1, 1e-10, 150
+    if ndim == 2:
+        o.smoother, o.nu1, o.nu2 = G.ISDC_SMOOTHER_JACOBI, 1, 1
+    else:
+        o.smoother, o.nu1, o.nu2 = G.ISDC_SMOOTHER_RBGS, 2, 2
+    o.vcycle_fp32, o.tol, o.max_sweeps = 1, 1e-10, 150
     o.temporal_blocking = -1 if args.temporal_blocking < 0 else min(args.temporal_blocking, 1)
+    o.use_graphs = args.use_graphs
     import ctypes
     o.stream = ctypes.c_void_p(stream.cuda_stream)
-    eng = G.isdc_batch_create(2, 1023, 5, 200 << 30, 2, o)
+    eng = G.isdc_batch_create(ndim, 1023 if ndim == 2 else 255, 5, 200 << 30, 2, o)
     sides = {}
     for q, w in enumerate(insts):
-        slot = G.isdc_batch_admit(eng, w.n, w.nu, w.M, w.dt, w.steps, W.initial_condition(2, w.n, w.seed))
+        slot = G.isdc_batch_admit(eng, w.n, w.nu, w.M, w.dt, w.steps, W.initial_condition(ndim, w.n, w.seed))
         assert slot is not None
         sides[slot] = w.n
-    warm = max(args.warmup, 6)
-    for _ in range(warm):
+    # warm-up: the requested ticks, and at least until the autotuner has kept a shape
+    warm = 0
+    while warm < args.warmup or (not G.isdc_batch_stats(eng).tuned and warm < 64):
         G.isdc_batch_tick(eng)
+        warm += 1
     info = G.isdc_batch_stats(eng)
     launches0 = info.kernel_launches
     torch.cuda.synchronize()
@@ -491,7 +503,7 @@ def run_batch(args):
     e0.record(stream)
     for _ in range(args.steps):
         live = [s for s in sides if G.isdc_batch_query(eng, s).state == G.ISDC_SLOT_RUNNING]
-        dofs += sum(float(sides[s] ** 2) for s in live)
+        dofs += sum(float(sides[s] ** ndim) for s in live)
         G.isdc_batch_tick(eng)
         tick_bytes += G.isdc_batch_stats(eng).bytes_last_tick  # host-side counter, no device work
     e1.record(stream)
@@ -505,10 +517,11 @@ def run_batch(args):
             "steps": args.steps, "warmup": warm, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 V-cycles)",
             "data": "synthetic (seeded)",
-            "config": {"workload": "batch_2d_256" if len(insts) == 256 else f"batch_2d_{len(insts)}",
+            "config": {"workload": f"batch_{ndim}d_{len(insts)}",
                        "instances": len(insts),
-                       "dofs_total": int(sum(w.n ** 2 for w in insts)),
-                       "sides": "2^j - 1, j uniform in 6..10", "smoother": "wjacobi V(1,1)", "L_vcycles": 2,
+                       "dofs_total": int(sum(w.n ** ndim for w in insts)),
+                       "sides": "2^j - 1, j uniform in " + ("6..10" if ndim == 2 else "6..8"),
+                       "smoother": "wjacobi V(1,1)" if ndim == 2 else "rbgs V(2,2)", "L_vcycles": 2,
                        "vcycle_precision": "fp32", "tol": 1e-10,
                        "l2": "inputs larger than L2 (all instances resident, tens of GB)",
                        "launch_shape": {"threads_per_block": info.threads_per_block,
@@ -528,18 +541,19 @@ def run_batch(args):
                                 "are bound by FP64 issue, so the whole tick stays below the HBM bound"}
     line["config"]["fused_smoother"] = int(info.fused)
     line["config"]["kernels_per_tick"] = int(info.kernels_per_tick)
+    line["config"]["launch_shape"]["graph_dependencies"] = "programmatic" if info.programmatic else "ordinary"
     if args.compare_fp64:
         # the same instances one at a time through the FP64 single-instance path
         tot_dofs, tot_t = 0.0, 0.0
         for w in insts[:args.compare_fp64]:
-            g = G.Isdc(2, w.n, w.nu, w.M, w.dt, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
-            u = torch.from_numpy(W.initial_condition(2, w.n, w.seed)).cuda()
+            g = G.Isdc(ndim, w.n, w.nu, w.M, w.dt, smoother=o.smoother, nu1=o.nu1, nu2=o.nu2, max_sweeps=150)
+            u = torch.from_numpy(W.initial_condition(ndim, w.n, w.seed)).cuda()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g.step(u, 0, 2)
             torch.cuda.synchronize()
             tot_t += time.perf_counter() - t0
-            tot_dofs += w.n ** 2 * g.stats()[0]
+            tot_dofs += w.n ** ndim * g.stats()[0]
             g.close()
         line["fp64_single_instance"] = {"value": tot_dofs / tot_t, "unit": "DOF-sweeps/s",
                                         "instances": args.compare_fp64,
@@ -584,7 +598,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="3d_n255_M5_fp64",
-                    choices=sorted(workloads()) + ["batch_2d_256", "serve_poisson"])
+                    choices=sorted(workloads()) + ["batch_2d_256", "batch_3d_32", "serve_poisson"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the FP32-V-cycle 255^3 and 511^3 lines")
@@ -594,7 +608,8 @@ def main():
                          "comes from the untimed fully profiled step")
     ap.add_argument("--compare-fp64", type=int, default=0, help="batch: also time N instances on the FP64 path")
     ap.add_argument("--instances", type=int, default=256,
-                    help="batch: number of instances (the first K of the seeded 256; smaller for profiling)")
+                    help="batch: number of instances (the first K of the seeded 256 2D or 32 3D; smaller for "
+                         "profiling)")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--fused-transfer", type=int, default=-1, choices=[-1, 0, 1],
@@ -618,7 +633,7 @@ def main():
         print(json.dumps({"fp64_probe": r, "clocks": clocks.stop()}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch_2d_256":
+    elif args.workload in ("batch_2d_256", "batch_3d_32"):
         run_batch(args)
     elif args.workload == "serve_poisson":
         run_serve(args)

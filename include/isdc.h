@@ -311,6 +311,7 @@ typedef struct {
     int     kernels_per_tick;   /* kernel launches of one tick in the shape in use */
     double  bytes_last_tick;    /* algorithmic device-memory bytes of the last tick (each phase
                                    reads each input once and writes each output once) */
+    int     programmatic;       /* 1: the tick graph in use has programmatic dependencies */
 } isdc_batch_info;
 
 /* ndim 2 or 3; max_side: the largest side that will be admitted (sets the
@@ -320,7 +321,11 @@ typedef struct {
  * temporal_blocking for 2D damped-Jacobi V(1, nu2 <= 1) engines: -1 or 1 fuse
  * the sweep into the transfer passes, 0 keeps it a separate phase; other
  * values INVALID_ARG; the two round differently, so the choice is fixed for
- * the engine's life).  The first ticks try several launch shapes (tile size,
+ * the engine's life; use_graphs 1 (default): the autotuner also tries tick
+ * graphs with programmatic dependencies between their kernels, 0 or 2:
+ * ordinary dependencies only; a tick is always one graph launch or, in 2D
+ * fused mode, one cooperative launch).  The first ticks try several launch
+ * shapes (tile size, dependency form,
  * blocks per SM; all give the same result bit for bit) and keep the fastest
  * (autotuner).
  * Errors: INVALID_ARG, OOM, CUDA. */

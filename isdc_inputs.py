@@ -126,6 +126,22 @@ def batch_instances(count: int = 256, seed: int = 4, j_range=(6, 10)):
     return out
 
 
+def batch_instances_3d(count: int = 32, seed: int = 6, j_range=(6, 8)):
+    """Independent 3D instances (the 3D share of the request mix): side
+    2^j - 1 with j uniform in j_range, nu log-uniform in [0.01, 1], dt uniform
+    in [0.01, 0.1], M in {3, 5}; red-black Gauss-Seidel V(2,2) settings."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(count):
+        j = int(rng.integers(j_range[0], j_range[1] + 1))
+        nu = _log_uniform(rng, 0.01, 1.0)
+        dt = float(rng.uniform(0.01, 0.1))
+        M = int(rng.choice([3, 5]))
+        out.append(Workload(f"batch3d{b}", 3, 2 ** j - 1, nu, M, dt, 10, 2, 1, 2, 2,
+                            vcycle_fp32=True, seed=seed * 100003 + b))
+    return out
+
+
 def request_stream(count: int = 2000, rate: float = 200.0, seed: int = 5):
     """Poisson arrivals at `rate` per second; 70 % 2D (side 127..1023), 30 % 3D
     (side 63..255); M in {3, 5}; nu, dt drawn as for the batch; 10 steps each.

@@ -15,8 +15,9 @@
 // within an HBM budget, and returned when its result is taken.
 //
 // Autotuning: the first ticks run with different launch shapes (threads per
-// block = tile size, persistent blocks per SM); each tick's DOF-sweep rate is
-// measured with events and the fastest shape is kept for the engine's life.
+// block = tile size, persistent blocks per SM, ordinary or programmatic graph
+// edges, one cooperative launch); each tick's DOF-sweep rate is measured with
+// events and the fastest shape is kept for the engine's life.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +40,12 @@ namespace {
 
 thread_local char g_batch_error[512] = "";
 
-enum ListKind { LK_FULL = 0, LK_HALF = 1, LK_CPTS = 2, LK_CELLS = 3, LK_TILE = 4, LK_KINDS = 5 };
+// Work-list kinds per (node solve, level): every point, coarse points and
+// coarse cells (one thread each); fused 2D tiles; rows of the level, of its
+// coarse grid and of its coarse cells (one warp each).
+enum ListKind {
+  LK_FULL = 0, LK_CPTS = 1, LK_CELLS = 2, LK_TILE = 3, LK_ROWS = 4, LK_CROWS = 5, LK_CELLROWS = 6, LK_KINDS = 7
+};
 
 struct Slot {
   int state = ISDC_SLOT_FREE;
@@ -51,15 +57,21 @@ struct Slot {
 };
 
 // Launch shape of the grid-wide phases: threads per block (the point-wise
-// phases' tile; the fused 2D phases' tile is 32 x threads/32 coarse points),
-// blocks per SM, and whether the whole tick is one persistent cooperative
-// launch (fused 2D mode only; blocks per SM from the occupancy calculator)
-// instead of a graph of one launch per phase.  Every shape gives the same
-// result bit for bit, so the autotuner's trial ticks are real sweeps.
+// phases' tile; the fused 2D phases' tile is 32 x threads/32 coarse points;
+// the row-structured phases' tile is threads/32 rows), blocks per SM, whether
+// the whole tick is one persistent cooperative launch (fused 2D mode only;
+// blocks per SM from the occupancy calculator) instead of a graph of one
+// launch per phase, and whether the graph's kernel-to-kernel edges are
+// programmatic (a kernel launched once every block of the one before it has
+// started, waiting at entry for its completion) or ordinary.  Every shape
+// gives the same result bit for bit, so the autotuner's trial ticks are real
+// sweeps.
 struct Shape {
-  int threads, blocks_per_sm, persistent;
+  int threads, blocks_per_sm, persistent, programmatic;
 };
-const Shape kShapes[] = {{256, 8, 0}, {128, 16, 0}, {512, 4, 0}, {256, 16, 0}, {128, 8, 0}, {256, 0, 1}, {512, 0, 1}};
+const Shape kShapes[] = {{256, 8, 0, 0}, {128, 16, 0, 0}, {512, 4, 0, 0}, {256, 16, 0, 0}, {128, 8, 0, 0},
+                         {256, 8, 0, 1}, {128, 16, 0, 1}, {512, 4, 0, 1}, {256, 16, 0, 1}, {128, 8, 0, 1},
+                         {256, 0, 1, 0}, {512, 0, 1, 0}};
 constexpr int kNumShapes = int(sizeof(kShapes) / sizeof(kShapes[0]));
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -169,8 +181,9 @@ enum TickMode { MODE_LEGACY = 0, MODE_FUSED2D = 1, MODE_RB_BOTTOM = 2 };
 // How a tick runs its V-cycles.  Fused 2D damped Jacobi (V(1, nu2 <= 1)):
 // one fused pass per leg and grid-wide level, the coarse levels in one block
 // per instance.  Red-black Gauss-Seidel: the separate phases on the grid-wide
-// levels, the coarse levels in one block per instance.  Otherwise (and for
-// the unfused Jacobi shapes): every phase of every level as its own pass.
+// levels as row-structured passes, the coarse levels in one block per
+// instance.  Otherwise (damped Jacobi outside the fused form): every phase of
+// every level as its own point-wise pass.
 int tick_mode(const isdc_batch* b, const Shape&) {
   const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
   if (!jac) return MODE_RB_BOTTOM;
@@ -212,14 +225,22 @@ void build_lists(isdc_batch* b, const Shape& sh) {
       add(list_coarse(b, m), i, dim == 2 ? 9 : 27);
       add_tiles(list_bottom(b, m), i, 1);
       int side = S.n;
+      auto add_rows = [&](int li, int s) { add_tiles(li, i, int(((dim == 2 ? s : s * s) + ty - 1) / ty)); };
       for (int l = 0; l < S.nlev - 1; ++l) {
         const int sc = (side - 1) / 2;
-        if (l == 0 || l < grid_levels) add(list_index(b, m, l, LK_FULL), i, pts(dim, side));  // level 0: rhs, update
+        if (l == 0 || (mode == MODE_LEGACY && l < grid_levels))  // level 0: rhs, update
+          add(list_index(b, m, l, LK_FULL), i, pts(dim, side));
         if (l < grid_levels) {
-          add(list_index(b, m, l, LK_HALF), i, size_t((side + 1) / 2) * (dim == 2 ? side : size_t(side) * side));
-          add(list_index(b, m, l, LK_CPTS), i, pts(dim, sc));
-          add(list_index(b, m, l, LK_CELLS), i, pts(dim, sc + 1));
-          add_tiles(list_index(b, m, l, LK_TILE), i, ((sc + kFtX - 1) / kFtX) * ((sc + ty - 1) / ty));
+          if (mode == MODE_LEGACY) {
+            add(list_index(b, m, l, LK_CPTS), i, pts(dim, sc));
+            add(list_index(b, m, l, LK_CELLS), i, pts(dim, sc + 1));
+          } else if (mode == MODE_FUSED2D) {
+            add_tiles(list_index(b, m, l, LK_TILE), i, ((sc + kFtX - 1) / kFtX) * ((sc + ty - 1) / ty));
+          } else {
+            add_rows(list_index(b, m, l, LK_ROWS), side);
+            add_rows(list_index(b, m, l, LK_CROWS), sc);
+            add_rows(list_index(b, m, l, LK_CELLROWS), sc + 1);
+          }
         }
         side = sc;
       }
@@ -310,13 +331,13 @@ void record_tick(isdc_batch* b, const Shape& sh) {
             else if (ty == 8) kb_down2<8><<<grid, 256, 0, st>>>(I, tl, m, l, omega, zero);
             else kb_down2<16><<<grid, 512, 0, st>>>(I, tl, m, l, omega, zero);
           } else {
-            const List* half = Ls + list_index(b, m, l, LK_HALF);
+            const List* rows = Ls + list_index(b, m, l, LK_ROWS);
             for (int s = 0; s < nu1; ++s) {
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 0, zero && s == 0);
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 1, 0);
+              kb_rbgs_rows<DIM><<<grid, blk, 0, st>>>(I, rows, m, l, 0, zero && s == 0);
+              kb_rbgs_rows<DIM><<<grid, blk, 0, st>>>(I, rows, m, l, 1, 0);
             }
-            kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, half, m, l, 0);
-            kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+            kb_residual_red_rows<DIM><<<grid, blk, 0, st>>>(I, rows, m, l);
+            kb_restrict_red_rows<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CROWS), m, l);
           }
         }
         kb_bottom<DIM><<<kMaxInst, kBottomThreads, bottom_smem(DIM), st>>>(I, Ls + list_bottom(b, m), m, c > 0 ? 1 : 0,
@@ -328,65 +349,43 @@ void record_tick(isdc_batch* b, const Shape& sh) {
             else if (ty == 8) kb_up2<8><<<grid, 256, 0, st>>>(I, tl, m, l, omega, nu2);
             else kb_up2<16><<<grid, 512, 0, st>>>(I, tl, m, l, omega, nu2);
           } else {
-            const List* half = Ls + list_index(b, m, l, LK_HALF);
-            const List* cells = Ls + list_index(b, m, l, LK_CELLS);
-            if (nu2 >= 1) kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
-            else kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+            const List* rows = Ls + list_index(b, m, l, LK_ROWS);
+            const List* cells = Ls + list_index(b, m, l, LK_CELLROWS);
+            if (nu2 >= 1) kb_prolong_rows<DIM, true><<<grid, blk, 0, st>>>(I, cells, l);
+            else kb_prolong_rows<DIM, false><<<grid, blk, 0, st>>>(I, cells, l);
             for (int s = 0; s < nu2; ++s) {
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 0, 0);
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, half, m, l, 1, 0);
+              kb_rbgs_rows<DIM><<<grid, blk, 0, st>>>(I, rows, m, l, 0, 0);
+              kb_rbgs_rows<DIM><<<grid, blk, 0, st>>>(I, rows, m, l, 1, 0);
             }
           }
         }
       }
-    } else {
+    } else {  // damped Jacobi, every phase of every level as its own pass
       for (int c = 0; c < b->L; ++c) {
         for (int l = 0; l < b->Lmax - 1; ++l) {
           const bool zero = l > 0 || c == 0;
+          const List* full = Ls + list_index(b, m, l, LK_FULL);
           int loc = l == 0 ? loc0 : 0;
           for (int s = 0; s < nu1; ++s) {
-            if (jac) {
-              kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, omega, loc,
-                                                   zero && s == 0);
-              loc ^= 1;
-            } else {
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, zero && s == 0);
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
-            }
+            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, full, m, l, omega, loc, zero && s == 0);
+            loc ^= 1;
           }
-          if (!jac)
-            kb_residual<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0);
-          else
-            kb_residual<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, loc);
-          if (!jac)
-            kb_restrict<DIM, true><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
-          else
-            kb_restrict<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
+          kb_residual<DIM><<<grid, blk, 0, st>>>(I, full, m, l, loc);
+          kb_restrict<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CPTS), m, l);
         }
         // every instance's coarsest grid; the result goes where a smoothed level's
-        // iterate would be (t after an odd Jacobi sweep count) so the prolongation
-        // reads one location for all instances
-        kb_coarse<DIM><<<grid, blk, 0, st>>>(I, Ls + list_coarse(b, m), m, jac ? par : 0);
+        // iterate would be (t after an odd sweep count) so the prolongation reads
+        // one location for all instances
+        kb_coarse<DIM><<<grid, blk, 0, st>>>(I, Ls + list_coarse(b, m), m, par);
         for (int l = b->Lmax - 2; l >= 0; --l) {
-          int loc = jac ? ((l == 0 ? loc0 : 0) ^ (nu1 & 1)) : 0;
-          const List* cells = Ls + list_index(b, m, l, LK_CELLS);
-          if (jac)
-            kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, loc, par);
-          else if (nu2 >= 1)  // a red half sweep follows and overwrites the red points
-            kb_prolong<DIM, true><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
-          else
-            kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, cells, l, 0, 0);
+          int loc = (l == 0 ? loc0 : 0) ^ (nu1 & 1);
+          kb_prolong<DIM, false><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_CELLS), l, loc, par);
           for (int s = 0; s < nu2; ++s) {
-            if (jac) {
-              kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, omega, loc, 0);
-              loc ^= 1;
-            } else {
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 0, 0);
-              kb_rbgs<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_HALF), m, l, 1, 0);
-            }
+            kb_jacobi<DIM><<<grid, blk, 0, st>>>(I, Ls + list_index(b, m, l, LK_FULL), m, l, omega, loc, 0);
+            loc ^= 1;
           }
         }
-        if (jac) loc0 ^= par;
+        loc0 ^= par;
       }
     }
     kb_update<DIM><<<grid, blk, 0, st>>>(I, full0, m, loc0);
@@ -460,6 +459,12 @@ isdc_status launch_persistent(isdc_batch* b, int shape, bool* unusable) {
   return ISDC_OK;
 }
 
+bool shape_allowed(const isdc_batch* b, int shape) {
+  const Shape& sh = kShapes[shape];
+  if (sh.persistent && tick_mode(b, sh) != MODE_FUSED2D) return false;
+  return !sh.programmatic || b->opt.use_graphs == 1;
+}
+
 isdc_status capture(isdc_batch* b, int shape) {
   if (b->exec[shape] || kShapes[shape].persistent) return ISDC_OK;
   cudaGraph_t g = nullptr;
@@ -477,7 +482,7 @@ isdc_status capture(isdc_batch* b, int shape) {
           ++b->kernel_nodes[shape];
       }
   }
-  if ((e = host::programmatic_edges(g)) != cudaSuccess) {
+  if (kShapes[shape].programmatic && (e = host::programmatic_edges(g)) != cudaSuccess) {
     cudaGraphDestroy(g);
     return bfail(b, ISDC_ERR_CUDA, "tick graph edges: %s", cudaGetErrorString(e));
   }
@@ -558,6 +563,8 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   if (opt) o = *opt; else isdc_default_options(&o);
   if (o.smoother != ISDC_SMOOTHER_JACOBI && o.smoother != ISDC_SMOOTHER_RBGS)
     return bfail(nullptr, ISDC_ERR_INVALID_ARG, "unknown smoother");
+  if (o.use_graphs < 0 || o.use_graphs > 2)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "use_graphs must be 0, 1 or 2");
   if (o.smoother == ISDC_SMOOTHER_JACOBI && !(o.omega > 0 && o.omega <= 1))
     return bfail(nullptr, ISDC_ERR_INVALID_ARG, "the Jacobi damping omega must be in (0, 1]");
   if (o.nu1 < 1 || o.nu2 < 0 || o.nu1 > 8 || o.nu2 > 8)
@@ -713,8 +720,9 @@ ISDC_API isdc_status isdc_batch_tick(isdc_batch* b, int* running_out, int* finis
     }
   int finished = 0;
   if (running) {
-    // the persistent shapes serve the fused 2D mode only; the tuner skips them otherwise
-    while (!b->tuned && kShapes[b->tune_next].persistent && tick_mode(b, kShapes[b->tune_next]) != MODE_FUSED2D) {
+    // the persistent shapes serve the fused 2D mode only, the programmatic ones
+    // engines with use_graphs == 1; the tuner skips them otherwise
+    while (!b->tuned && !shape_allowed(b, b->tune_next)) {
       b->tune_rate[b->tune_next] = 0.0;
       if (++b->tune_next == kNumShapes) break;
     }
@@ -847,6 +855,7 @@ ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info
   info->threads_per_block = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].threads;
   info->blocks_per_sm = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].blocks_per_sm;
   info->fused = tick_mode(b, kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes]) == MODE_FUSED2D;
+  info->programmatic = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].programmatic;
   {
     const int sh = b->tuned ? b->shape : b->tune_next % kNumShapes;
     info->kernels_per_tick = kShapes[sh].persistent ? 1 : b->kernel_nodes[sh];

@@ -63,17 +63,6 @@ __device__ __forceinline__ void decode(int q, int n, int& i, int& j, int& k) {
   if (DIM == 2) { j = r; k = 0; } else { j = r % n; k = r / n; }
 }
 
-// Colour grid: q indexes (ih, j, k) with ih in [0, (n+1)/2).
-template <int DIM>
-__device__ __forceinline__ bool decode_colour(int q, int n, int colour, int& i, int& j, int& k) {
-  const int H = (n + 1) >> 1;
-  const int ih = q % H;
-  const int r = q / H;
-  if (DIM == 2) { j = r; k = 0; } else { j = r % n; k = r / n; }
-  i = 2 * ih + ((colour + j + (DIM == 3 ? k : 0) + DIM) & 1);
-  return i < n && j < n && k < (DIM == 3 ? n : 1);
-}
-
 template <int DIM>
 __device__ __forceinline__ int npts(int n) { return DIM == 2 ? n * n : n * n * n; }
 
@@ -224,38 +213,152 @@ __global__ void kb_jacobi(const Inst* __restrict__ insts, const List* __restrict
   BATCH_END
 }
 
+// Scaled residual of level l at every point (damped-Jacobi V-cycles).
 template <int DIM>
-__global__ void kb_rbgs(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, int colour,
-                        int zero) {
-  grid_dep_wait();
-  const List& L = *list;
-  BATCH_LOOP(L)
-    const Level& V = I.lev[l];
-    int i, j, k;
-    if (!decode_colour<DIM>(q, V.n, colour, i, j, k)) continue;
-    const int p = lin<DIM>(i, j, k, V.n);
-    V.x[p] = zero ? V.b[p] : fmaf(I.kappa[m][l], nbsum<float, DIM>(V.x, i, j, k, V.n, p), V.b[p]);
-  BATCH_END
-}
-
-// Scaled residual of level l (red points only after a red-black sweep).
-template <int DIM, bool RED_ONLY>
 __global__ void kb_residual(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, int src_t) {
   grid_dep_wait();
   const List& L = *list;
   BATCH_LOOP(L)
     const Level& V = I.lev[l];
+    if (q >= npts<DIM>(V.n)) continue;
     int i, j, k;
-    if (RED_ONLY) {
-      if (!decode_colour<DIM>(q, V.n, 0, i, j, k)) continue;
-    } else {
-      if (q >= npts<DIM>(V.n)) continue;
-      decode<DIM>(q, V.n, i, j, k);
-    }
+    decode<DIM>(q, V.n, i, j, k);
     const float* x = src_t ? V.t : V.x;
-    const int p = lin<DIM>(i, j, k, V.n);
-    V.r[p] = fmaf(I.kappa[m][l], nbsum<float, DIM>(x, i, j, k, V.n, p), V.b[p]) - x[p];
+    V.r[q] = fmaf(I.kappa[m][l], nbsum<float, DIM>(x, i, j, k, V.n, q), V.b[q]) - x[q];
   BATCH_END
+}
+
+// ---------------------------------------------------------------------------
+// Row-structured work lists (red-black Gauss-Seidel V-cycles).  A row is a
+// fixed (j, k) of a grid of side s; there are s (2D) or s^2 (3D) of them.
+// Tile t of an instance covers rows [t NW, t NW + NW) (NW = warps per block):
+// warp w takes row t NW + w and its lanes walk the row's points.  The row's
+// (j, k), base address and j/k validity are formed once per row, so the
+// per-point work is the stencil itself.
+// ---------------------------------------------------------------------------
+// Every launch shape holds 2048 threads per SM (threads x blocks per SM), so
+// the row kernels are held to 32 registers: one wave of blocks is resident and
+// the grid-stride loop has no tail wave.
+constexpr int kRowsMaxThreads = 512, kRowsMinBlocks = 4;
+
+template <int DIM, class SideOf, class Body>
+__device__ __forceinline__ void for_list_rows(const Inst* __restrict__ insts, const List& L, const SideOf& side_of,
+                                              const Body& body) {
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int g = blockIdx.x; g < L.total; g += gridDim.x) {
+    const int e = find_entry(L, g);
+    const Inst& I = insts[L.inst[e]];
+    const int s = side_of(I);
+    const int r = (g - L.start[e]) * nw + warp;
+    if (r >= (DIM == 2 ? s : s * s)) continue;
+    body(I, s, DIM == 2 ? r : r % s, DIM == 2 ? 0 : r / s, lane);
+  }
+}
+
+// nbsum of point i of the row starting at xr (same terms, same order).
+template <int DIM>
+__device__ __forceinline__ float row_nbsum(const float* __restrict__ xr, int i, int n, bool jlo, bool jhi, bool klo,
+                                           bool khi) {
+  const float sx = (i > 0 ? xr[i - 1] : 0.f) + (i < n - 1 ? xr[i + 1] : 0.f);
+  const float sy = (jlo ? xr[i - n] : 0.f) + (jhi ? xr[i + n] : 0.f);
+  if (DIM == 3) {
+    const int sz = n * n;
+    const float szv = (klo ? xr[i - sz] : 0.f) + (khi ? xr[i + sz] : 0.f);
+    return (sx + sy) + szv;
+  }
+  return sx + sy;
+}
+
+// One colour of a Gauss-Seidel sweep of level l: points i of row (j, k) with
+// i = j + k + DIM + colour (mod 2), x = kappa * sum + b (b on zero guesses).
+template <int DIM>
+__global__ void __launch_bounds__(kRowsMaxThreads, kRowsMinBlocks) kb_rbgs_rows(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l,
+                             int colour, int zero) {
+  grid_dep_wait();
+  for_list_rows<DIM>(insts, *list, [l](const Inst& I) { return I.lev[l].n; },
+                     [&](const Inst& I, int n, int j, int k, int lane) {
+                       const Level& V = I.lev[l];
+                       const int base = lin<DIM>(0, j, k, n);
+                       float* xr = V.x + base;
+                       const float* br = V.b + base;
+                       const int i0 = 2 * lane + ((colour + j + k + DIM) & 1);
+                       if (zero) {
+                         for (int i = i0; i < n; i += 64) xr[i] = br[i];
+                         return;
+                       }
+                       const float kap = I.kappa[m][l];
+                       const bool jlo = j > 0, jhi = j < n - 1, klo = k > 0, khi = k < n - 1;
+                       // two points per iteration, both loaded before either is stored
+                       // (same colour: the stores alias none of the loads)
+#pragma unroll 1
+                       for (int i = i0; i < n; i += 128) {
+                         const bool two = i + 64 < n;
+                         const float s1 = row_nbsum<DIM>(xr, i, n, jlo, jhi, klo, khi), b1 = br[i];
+                         float s2 = 0.f, b2 = 0.f;
+                         if (two) {
+                           s2 = row_nbsum<DIM>(xr, i + 64, n, jlo, jhi, klo, khi);
+                           b2 = br[i + 64];
+                         }
+                         xr[i] = fmaf(kap, s1, b1);
+                         if (two) xr[i + 64] = fmaf(kap, s2, b2);
+                       }
+                     });
+}
+
+// Scaled residual of level l at its red points (after a red-black sweep the
+// black residual is zero).
+template <int DIM>
+__global__ void __launch_bounds__(kRowsMaxThreads, kRowsMinBlocks) kb_residual_red_rows(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l) {
+  grid_dep_wait();
+  for_list_rows<DIM>(insts, *list, [l](const Inst& I) { return I.lev[l].n; },
+                     [&](const Inst& I, int n, int j, int k, int lane) {
+                       const Level& V = I.lev[l];
+                       const int base = lin<DIM>(0, j, k, n);
+                       const float* xr = V.x + base;
+                       const float* br = V.b + base;
+                       float* rr = V.r + base;
+                       const float kap = I.kappa[m][l];
+                       const bool jlo = j > 0, jhi = j < n - 1, klo = k > 0, khi = k < n - 1;
+#pragma unroll 1
+                       for (int i = 2 * lane + ((j + k + DIM) & 1); i < n; i += 128) {
+                         const bool two = i + 64 < n;
+                         const float s1 = row_nbsum<DIM>(xr, i, n, jlo, jhi, klo, khi), b1 = br[i], x1 = xr[i];
+                         float s2 = 0.f, b2 = 0.f, x2 = 0.f;
+                         if (two) {
+                           s2 = row_nbsum<DIM>(xr, i + 64, n, jlo, jhi, klo, khi);
+                           b2 = br[i + 64];
+                           x2 = xr[i + 64];
+                         }
+                         rr[i] = fmaf(kap, s1, b1) - x1;
+                         if (two) rr[i + 64] = fmaf(kap, s2, b2) - x2;
+                       }
+                     });
+}
+
+// Full weighting of level l's red residual to b_{l+1}, one coarse row per warp.
+template <int DIM>
+__global__ void __launch_bounds__(kRowsMaxThreads, kRowsMinBlocks) kb_restrict_red_rows(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l) {
+  grid_dep_wait();
+  for_list_rows<DIM>(insts, *list, [l](const Inst& I) { return I.lev[l + 1].n; },
+                     [&](const Inst& I, int nc, int cj, int ck, int lane) {
+                       float* bc = I.lev[l + 1].b + lin<DIM>(0, cj, ck, nc);
+                       const float w = I.wscale[m][l];
+                       for (int ci = lane; ci < nc; ci += 32)
+                         bc[ci] = restrict_point<float, DIM, true>(nc, w, I.lev[l].r, ci, cj, ck);
+                     });
+}
+
+// x_l += P x_{l+1}, one row of coarse cells (side nc + 1) per warp; BLACK_ONLY
+// when a red half sweep follows and overwrites the red points.
+template <int DIM, bool BLACK_ONLY>
+__global__ void __launch_bounds__(kRowsMaxThreads, kRowsMinBlocks) kb_prolong_rows(const Inst* __restrict__ insts, const List* __restrict__ list, int l) {
+  grid_dep_wait();
+  for_list_rows<DIM>(insts, *list, [l](const Inst& I) { return I.lev[l + 1].n + 1; },
+                     [&](const Inst& I, int ncell, int cj, int ck, int lane) {
+                       const int nc = ncell - 1;
+                       for (int ci = lane; ci < ncell; ci += 32)
+                         prolong_cell<float, DIM, BLACK_ONLY>(nc, I.lev[l + 1].x, I.lev[l].x, ci, cj, ck);
+                     });
 }
 
 template <int DIM, bool RED_ONLY>

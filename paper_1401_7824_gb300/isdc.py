@@ -68,7 +68,8 @@ class isdc_batch_info(ctypes.Structure):
     _fields_ = [("ticks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
                 ("running", ctypes.c_int),
                 ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("fused", ctypes.c_int), ("kernels_per_tick", ctypes.c_int), ("bytes_last_tick", ctypes.c_double)]
+                ("fused", ctypes.c_int), ("kernels_per_tick", ctypes.c_int), ("bytes_last_tick", ctypes.c_double),
+                ("programmatic", ctypes.c_int)]
 
 
 ISDC_SLOT_FREE, ISDC_SLOT_RUNNING, ISDC_SLOT_FINISHED, ISDC_SLOT_FAILED = 0, 1, 2, 3

@@ -94,6 +94,10 @@ def test_host_validation_without_gpu():
         with pytest.raises(G.IsdcError) as e:
             G.isdc_create(3, 31, 0.1, 3, 0.05, o)
         assert e.value.status == G.ISDC_ERR_INVALID_ARG, field
+        if field in ("use_graphs", "smoother"):  # the batch engine checks them before any device work too
+            with pytest.raises(G.IsdcError) as e:
+                G.isdc_batch_create(3, 31, 3, 1 << 30, 2, o)
+            assert e.value.status == G.ISDC_ERR_INVALID_ARG, field
     o = G.isdc_default_options()
     o.equation = 1
     with pytest.raises(G.IsdcError) as e:

@@ -117,29 +117,54 @@ def test_batch_every_node_count_matches_fp64_oracle(ndim):
         assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
 
 
-def test_batch_launch_shapes_give_identical_results():
-    """An instance admitted into a fresh engine sweeps through the autotuner's
-    trial ticks (every graph shape, then the persistent one-launch ticks), the
-    same instance admitted after tuning sweeps in the chosen shape only: the
-    results agree bit for bit, so no launch form changes the arithmetic."""
+def test_batch_rbgs_2d_matches_fp64_oracle():
+    """2D red-black Gauss-Seidel V(2,2) engine (row-structured passes on the
+    grid-wide levels 255 and 127, the levels from 63 down in one block per
+    instance) against the FP64 oracle."""
     import paper_1401_7824_gb300 as G
     torch_cuda()
-    prob = (255, 0.1, 5, 0.02, 1)
+    probs = [(255, 0.05, 3, 0.02, 1), (127, 0.3, 5, 0.05, 2), (63, 1.0, 5, 0.01, 1)]
+    eng = G.Batch(2, 255, 5, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_RBGS, nu1=2, nu2=2, max_sweeps=150)
+    got = _run(eng, probs, 2, 190)
+    eng.close()
+    for q, (n, nu, M, dt, steps) in enumerate(probs):
+        p = O.Problem(2, n, nu, M, dt, smoother=O.SMOOTHER_RBGS, nu1=2, nu2=2, max_sweeps=150)
+        ref = O.integrate(p, initial_condition(2, n, 190 + q), steps, 0, 2)
+        assert all(s == 0 for s in ref.status)
+        assert rel_l2(got[q][0], ref.u) <= 1e-9, (q, rel_l2(got[q][0], ref.u))
 
-    def engine():
-        return G.Batch(2, 255, 5, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_batch_launch_shapes_give_identical_results(ndim):
+    """An instance admitted into a fresh engine sweeps through the autotuner's
+    trial ticks (every graph shape, then, in 2D damped Jacobi, the persistent
+    one-launch ticks), the same instance admitted after tuning sweeps in the
+    chosen shape only: the results agree bit for bit, so no launch form (nor
+    the rows per tile of the 3D red-black passes) changes the arithmetic."""
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    if ndim == 2:
+        prob, warm_n = (255, 0.1, 5, 0.02, 1), 63
+
+        def engine():
+            return G.Batch(2, 255, 5, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_JACOBI, nu1=1, nu2=1, max_sweeps=150)
+    else:
+        prob, warm_n = (63, 0.1, 5, 0.02, 1), 15
+
+        def engine():
+            return G.Batch(3, 63, 5, 8 << 30, 2, smoother=G.ISDC_SMOOTHER_RBGS, nu1=2, nu2=2, max_sweeps=150)
 
     fresh = engine()
-    r_fresh = _run(fresh, [prob], 2, 150)
+    r_fresh = _run(fresh, [prob], ndim, 150)
     fresh.close()
     tuned = engine()
-    warm = tuned.admit(63, 0.5, 3, 0.05, 50, initial_condition(2, 63, 9))
+    warm = tuned.admit(warm_n, 0.5, 3, 0.05, 50, initial_condition(ndim, warm_n, 9))
     for _ in range(20):
         tuned.tick()
         if tuned.stats().tuned:
             break
     assert tuned.stats().tuned == 1
-    r_tuned = _run_keep(tuned, [prob], 2, 150, ignore=[warm])
+    r_tuned = _run_keep(tuned, [prob], ndim, 150, ignore=[warm])
     tuned.close()
     np.testing.assert_array_equal(r_fresh[0][0], r_tuned[0][0])
     assert r_fresh[0][1] == r_tuned[0][1]
