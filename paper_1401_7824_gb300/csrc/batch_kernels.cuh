@@ -319,18 +319,29 @@ __global__ void __launch_bounds__(kRowsMaxThreads, kRowsMinBlocks) kb_residual_r
                        float* rr = V.r + base;
                        const float kap = I.kappa[m][l];
                        const bool jlo = j > 0, jhi = j < n - 1, klo = k > 0, khi = k < n - 1;
+                       // point pairs (2q, 2q + 1): the red one gets its residual, the
+                       // black one 0 (never read by the red-only restriction), so every
+                       // sector of r is written whole and none is read back from DRAM
+                       const int par = (j + k + DIM) & 1;
 #pragma unroll 1
-                       for (int i = 2 * lane + ((j + k + DIM) & 1); i < n; i += 128) {
-                         const bool two = i + 64 < n;
-                         const float s1 = row_nbsum<DIM>(xr, i, n, jlo, jhi, klo, khi), b1 = br[i], x1 = xr[i];
-                         float s2 = 0.f, b2 = 0.f, x2 = 0.f;
-                         if (two) {
+                       for (int q = lane; 2 * q < n; q += 64) {
+                         const int i = 2 * q + par, ib = 2 * q + 1 - par;
+                         const bool red1 = i < n, two = 2 * q + 64 < n, red2 = i + 64 < n;
+                         float s1 = 0.f, b1 = 0.f, x1 = 0.f, s2 = 0.f, b2 = 0.f, x2 = 0.f;
+                         if (red1) {
+                           s1 = row_nbsum<DIM>(xr, i, n, jlo, jhi, klo, khi);
+                           b1 = br[i];
+                           x1 = xr[i];
+                         }
+                         if (red2) {
                            s2 = row_nbsum<DIM>(xr, i + 64, n, jlo, jhi, klo, khi);
                            b2 = br[i + 64];
                            x2 = xr[i + 64];
                          }
-                         rr[i] = fmaf(kap, s1, b1) - x1;
-                         if (two) rr[i + 64] = fmaf(kap, s2, b2) - x2;
+                         if (red1) rr[i] = fmaf(kap, s1, b1) - x1;
+                         if (ib < n) rr[ib] = 0.f;
+                         if (red2) rr[i + 64] = fmaf(kap, s2, b2) - x2;
+                         if (two && ib + 64 < n) rr[ib + 64] = 0.f;
                        }
                      });
 }
