@@ -541,7 +541,7 @@ def run_batch(args):
                                 "are bound by FP64 issue, so the whole tick stays below the HBM bound"}
     line["config"]["fused_smoother"] = int(info.fused)
     line["config"]["kernels_per_tick"] = int(info.kernels_per_tick)
-    line["config"]["launch_shape"]["graph_dependencies"] = "programmatic" if info.programmatic else "ordinary"
+    line["config"]["launch_shape"]["lanes"] = int(info.lanes)
     if args.compare_fp64:
         # the same instances one at a time through the FP64 single-instance path
         tot_dofs, tot_t = 0.0, 0.0

@@ -311,7 +311,8 @@ typedef struct {
     int     kernels_per_tick;   /* kernel launches of one tick in the shape in use */
     double  bytes_last_tick;    /* algorithmic device-memory bytes of the last tick (each phase
                                    reads each input once and writes each output once) */
-    int     programmatic;       /* 1: the tick graph in use has programmatic dependencies */
+    int     lanes;              /* independent chains of the tick graph in use, each over its own
+                                   share of the running instances (run concurrently) */
 } isdc_batch_info;
 
 /* ndim 2 or 3; max_side: the largest side that will be admitted (sets the
@@ -321,13 +322,12 @@ typedef struct {
  * temporal_blocking for 2D damped-Jacobi V(1, nu2 <= 1) engines: -1 or 1 fuse
  * the sweep into the transfer passes, 0 keeps it a separate phase; other
  * values INVALID_ARG; the two round differently, so the choice is fixed for
- * the engine's life; use_graphs 1 (default): the autotuner also tries tick
- * graphs with programmatic dependencies between their kernels, 0 or 2:
- * ordinary dependencies only; a tick is always one graph launch or, in 2D
- * fused mode, one cooperative launch).  The first ticks try several launch
- * shapes (tile size, dependency form,
- * blocks per SM; all give the same result bit for bit) and keep the fastest
- * (autotuner).
+ * the engine's life; use_graphs must be 0, 1 or 2 but is not used: a tick is
+ * always one graph launch with ordinary dependencies or, in 2D fused mode, one
+ * cooperative launch).  The first ticks try several launch shapes (tile size,
+ * blocks per SM, one launch per tick, then 1 to 4 lanes: concurrent chains of
+ * the tick graph over disjoint shares of the instances; all give the same
+ * result bit for bit) and keep the fastest (autotuner).
  * Errors: INVALID_ARG, OOM, CUDA. */
 isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, size_t hbm_budget_bytes, int n_vcycles,
                               const isdc_options *opt, isdc_batch **out);

@@ -15,9 +15,9 @@
 // within an HBM budget, and returned when its result is taken.
 //
 // Autotuning: the first ticks run with different launch shapes (threads per
-// block = tile size, persistent blocks per SM, ordinary or programmatic graph
-// edges, one cooperative launch); each tick's DOF-sweep rate is measured with
-// events and the fastest shape is kept for the engine's life.
+// block = tile size, persistent blocks per SM, one cooperative launch), then
+// with 2..4 lanes of the fastest graph shape; each tick's DOF-sweep rate is
+// measured with events and the fastest shape is kept for the engine's life.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,18 +61,21 @@ struct Slot {
 // the row-structured phases' tile is threads/32 rows), blocks per SM, whether
 // the whole tick is one persistent cooperative launch (fused 2D mode only;
 // blocks per SM from the occupancy calculator) instead of a graph of one
-// launch per phase, and whether the graph's kernel-to-kernel edges are
-// programmatic (a kernel launched once every block of the one before it has
-// started, waiting at entry for its completion) or ordinary.  Every shape
-// gives the same result bit for bit, so the autotuner's trial ticks are real
-// sweeps.
+// launch per phase, and the number of lanes: the running instances are dealt
+// to that many independent chains of the tick graph (balanced by work), which
+// the graph runs concurrently, so one lane's FP64-bound phases overlap another
+// lane's HBM-bound V-cycle phases.  Every shape gives the same result bit for
+// bit, so the autotuner's trial ticks are real sweeps.
 struct Shape {
-  int threads, blocks_per_sm, persistent, programmatic;
+  int threads, blocks_per_sm, persistent, lanes;
 };
-const Shape kShapes[] = {{256, 8, 0, 0}, {128, 16, 0, 0}, {512, 4, 0, 0}, {256, 16, 0, 0}, {128, 8, 0, 0},
-                         {256, 8, 0, 1}, {128, 16, 0, 1}, {512, 4, 0, 1}, {256, 16, 0, 1}, {128, 8, 0, 1},
-                         {256, 0, 1, 0}, {512, 0, 1, 0}};
-constexpr int kNumShapes = int(sizeof(kShapes) / sizeof(kShapes[0]));
+constexpr int kMaxLanes = 4;
+// the autotuner's first candidates (one lane); lane counts 2..kMaxLanes of the
+// fastest graph shape are appended once these have run
+const Shape kBaseShapes[] = {{256, 8, 0, 1}, {128, 16, 0, 1}, {512, 4, 0, 1}, {256, 16, 0, 1}, {128, 8, 0, 1},
+                             {256, 0, 1, 1}, {512, 0, 1, 1}};
+constexpr int kNumBase = int(sizeof(kBaseShapes) / sizeof(kBaseShapes[0]));
+constexpr int kMaxCands = kNumBase + kMaxLanes - 1;
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -92,23 +95,29 @@ struct isdc_batch {
   int nlists = 0;
   unsigned long long *d_rbits = nullptr, *d_dummy = nullptr, *h_rbits = nullptr;
   Slot slots[kMaxInst];
-  // graph per launch shape
-  cudaGraphExec_t exec[kNumShapes] = {};
-  int shape = 0;         // shape in use
+  // autotuner candidates, with a graph per graph shape
+  Shape cands[kMaxCands] = {};
+  int ncands = 0;
+  bool lanes_added = false;  // lane-count candidates appended
+  cudaGraphExec_t exec[kMaxCands] = {};
+  int shape = 0;         // candidate in use
   int tuned = 0;         // 1 once the autotuner has chosen
-  int tune_next = 0;     // next shape to try
+  int tune_next = 0;     // next candidate to try
   bool tune_warm = false;  // the first tick (every instance's spread) is run but not scored
-  double tune_rate[kNumShapes] = {};
+  double tune_rate[kMaxCands] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // lanes 1.. of a multi-lane tick graph: their capture streams, fork and join events
+  cudaStream_t lane_st[kMaxLanes - 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes - 1] = {};
   long long ticks = 0;
   long long kernel_launches = 0;   // kernel nodes executed by all ticks
   double last_tick_bytes = 0.0;    // algorithmic bytes of the last tick (tick_bytes)
-  int kernel_nodes[kNumShapes] = {};  // kernel nodes per tick graph
+  int kernel_nodes[kMaxCands] = {};  // kernel nodes per tick graph
   // persistent tick: phase table, grid barrier, resident blocks per SM per shape
   Phase* d_phases = nullptr;
   int nphases = 0;
   GridBarrier *d_gb = nullptr, *h_gb = nullptr;
-  int pers_bps[kNumShapes] = {};
+  int pers_bps[kMaxCands] = {};
   char err[512] = "";
 };
 
@@ -190,17 +199,37 @@ int tick_mode(const isdc_batch* b, const Shape&) {
   return b->fused ? MODE_FUSED2D : MODE_LEGACY;
 }
 
-// Rebuild every work list for the current running set and launch shape.
+// Rebuild every work list for the current running set and launch shape.  With
+// several lanes, lane q's lists start at h_lists + q * nlists, and each running
+// instance goes to the lane with the least work so far (largest instances
+// first; work ~ points x node solves, M - 1).
 void build_lists(isdc_batch* b, const Shape& sh) {
   const int tile = sh.threads, ty = sh.threads / 32;
   const int mode = tick_mode(b, sh);
-  for (int q = 0; q < b->nlists; ++q) {
+  for (int q = 0; q < b->nlists * sh.lanes; ++q) {
     b->h_lists[q].count = 0;
     b->h_lists[q].total = 0;
     b->h_lists[q].start[0] = 0;
   }
+  int lane_of[kMaxInst];
+  {
+    int order[kMaxInst], cnt = 0;
+    for (int i = 0; i < kMaxInst; ++i)
+      if (b->slots[i].state == ISDC_SLOT_RUNNING) order[cnt++] = i;
+    auto work = [&](int i) { return double(pts(b->dim, b->slots[i].n)) * (b->slots[i].M - 1); };
+    std::stable_sort(order, order + cnt, [&](int x, int y) { return work(x) > work(y); });
+    double load[kMaxLanes] = {};
+    for (int c = 0; c < cnt; ++c) {
+      int best = 0;
+      for (int q = 1; q < sh.lanes; ++q)
+        if (load[q] < load[best]) best = q;
+      lane_of[order[c]] = best;
+      load[best] += work(order[c]);
+    }
+  }
+  int lane = 0;  // lane of the instance being added
   auto add_tiles = [&](int li, int inst, int tiles) {
-    List& L = b->h_lists[li];
+    List& L = b->h_lists[lane * b->nlists + li];
     L.inst[L.count] = inst;
     L.start[L.count] = L.total;
     L.total += tiles;
@@ -212,6 +241,7 @@ void build_lists(isdc_batch* b, const Shape& sh) {
   for (int i = 0; i < kMaxInst; ++i) {
     const Slot& S = b->slots[i];
     if (S.state != ISDC_SLOT_RUNNING) continue;
+    lane = lane_of[i];
     const size_t N = pts(dim, S.n);
     if (S.spread_next) {
       add(list_spread(b), i, N);
@@ -298,13 +328,12 @@ void launch_sweep_end(int M, dim3 grid, dim3 blk, cudaStream_t st, const Inst* I
   }
 }
 
-// Record one tick's launches on the stream (inside a capture).
+// Record one lane's launches of a tick on stream st, over the lane's work
+// lists Ls (inside a capture).
 template <int DIM>
-void record_tick(isdc_batch* b, const Shape& sh) {
+void record_lane(isdc_batch* b, const Shape& sh, cudaStream_t st, const List* Ls) {
   const dim3 grid(sh.blocks_per_sm * b->sms), blk(sh.threads);
-  cudaStream_t st = b->stream;
   const Inst* I = b->d_insts;
-  const List* Ls = b->d_lists;
   const int reaction = b->opt.reaction;
   const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
   const int nu1 = b->opt.nu1, nu2 = b->opt.nu2;
@@ -312,7 +341,6 @@ void record_tick(isdc_batch* b, const Shape& sh) {
   const int mode = tick_mode(b, sh);
   const int ty = sh.threads / 32;
   const int par = (nu1 + nu2) & 1;  // Jacobi: a level's iterate ends in t after an odd sweep count
-  cudaMemsetAsync(b->d_rbits, 0, sizeof(unsigned long long) * kMaxInst, st);
   kb_spread<DIM><<<grid, blk, 0, st>>>(I, Ls + list_spread(b), reaction);
   for (int M = 2; M <= b->Mmax; ++M)
     launch_sweep_end<DIM>(M, grid, blk, st, I, Ls + list_spread_m(b, M), reaction, b->d_dummy);
@@ -392,6 +420,26 @@ void record_tick(isdc_batch* b, const Shape& sh) {
   }
   for (int M = 2; M <= b->Mmax; ++M)
     launch_sweep_end<DIM>(M, grid, blk, st, I, Ls + list_sweep_m(b, M), reaction, b->d_rbits);
+}
+
+// Record one tick on the engine's stream (inside a capture): the lanes fork
+// from it and join back before the residuals are read.  Lanes hold disjoint
+// instances, so their only shared writes are atomic maxima into per-instance
+// residual words and into the spread phase's scratch word.
+template <int DIM>
+void record_tick(isdc_batch* b, const Shape& sh) {
+  cudaStream_t st = b->stream;
+  cudaMemsetAsync(b->d_rbits, 0, sizeof(unsigned long long) * kMaxInst, st);
+  if (sh.lanes > 1) {
+    cudaEventRecord(b->ev_fork, st);
+    for (int q = 1; q < sh.lanes; ++q) cudaStreamWaitEvent(b->lane_st[q - 1], b->ev_fork, 0);
+  }
+  for (int q = 0; q < sh.lanes; ++q)
+    record_lane<DIM>(b, sh, q ? b->lane_st[q - 1] : st, b->d_lists + size_t(q) * b->nlists);
+  for (int q = 1; q < sh.lanes; ++q) {
+    cudaEventRecord(b->ev_join[q - 1], b->lane_st[q - 1]);
+    cudaStreamWaitEvent(st, b->ev_join[q - 1], 0);
+  }
   cudaMemcpyAsync(b->h_rbits, b->d_rbits, sizeof(unsigned long long) * kMaxInst, cudaMemcpyDeviceToHost, st);
 }
 
@@ -423,7 +471,7 @@ isdc_status build_phases(isdc_batch* b) {
 // One tick as one cooperative launch; *unusable when the shape cannot be
 // resident (the tuner then skips it).
 isdc_status launch_persistent(isdc_batch* b, int shape, bool* unusable) {
-  const Shape& sh = kShapes[shape];
+  const Shape& sh = b->cands[shape];
   *unusable = false;
   isdc_status st = build_phases(b);
   if (st != ISDC_OK) return st;
@@ -460,16 +508,40 @@ isdc_status launch_persistent(isdc_batch* b, int shape, bool* unusable) {
 }
 
 bool shape_allowed(const isdc_batch* b, int shape) {
-  const Shape& sh = kShapes[shape];
-  if (sh.persistent && tick_mode(b, sh) != MODE_FUSED2D) return false;
-  return !sh.programmatic || b->opt.use_graphs == 1;
+  const Shape& sh = b->cands[shape];
+  return !sh.persistent || tick_mode(b, sh) == MODE_FUSED2D;  // the persistent tick serves fused 2D only
+}
+
+// The autotuner has run every candidate so far: append the lane counts
+// 2..kMaxLanes of the fastest graph shape (first time), else keep the fastest
+// candidate for the engine's life.
+void tuner_round_done(isdc_batch* b) {
+  int best = 0;
+  for (int s = 1; s < b->ncands; ++s)
+    if (b->tune_rate[s] > b->tune_rate[best]) best = s;
+  if (!b->lanes_added) {
+    b->lanes_added = true;
+    int g = -1;
+    for (int s = 0; s < b->ncands; ++s)
+      if (!b->cands[s].persistent && b->tune_rate[s] > 0.0 && (g < 0 || b->tune_rate[s] > b->tune_rate[g])) g = s;
+    if (g >= 0) {
+      for (int q = 2; q <= kMaxLanes; ++q) {
+        Shape sh = b->cands[g];
+        sh.lanes = q;
+        b->cands[b->ncands++] = sh;
+      }
+      return;  // tune_next now points at the first lane candidate
+    }
+  }
+  b->shape = best;
+  b->tuned = 1;
 }
 
 isdc_status capture(isdc_batch* b, int shape) {
-  if (b->exec[shape] || kShapes[shape].persistent) return ISDC_OK;
+  if (b->exec[shape] || b->cands[shape].persistent) return ISDC_OK;
   cudaGraph_t g = nullptr;
   B_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  if (b->dim == 2) record_tick<2>(b, kShapes[shape]); else record_tick<3>(b, kShapes[shape]);
+  if (b->dim == 2) record_tick<2>(b, b->cands[shape]); else record_tick<3>(b, b->cands[shape]);
   cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess) return bfail(b, ISDC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   size_t nn = 0;
@@ -481,10 +553,6 @@ isdc_status capture(isdc_batch* b, int shape) {
         if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
           ++b->kernel_nodes[shape];
       }
-  }
-  if (kShapes[shape].programmatic && (e = host::programmatic_edges(g)) != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return bfail(b, ISDC_ERR_CUDA, "tick graph edges: %s", cudaGetErrorString(e));
   }
   e = cudaGraphInstantiate(&b->exec[shape], g, 0);
   cudaGraphDestroy(g);
@@ -614,10 +682,10 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   CB(cudaMalloc(&b->d_insts, sizeof(Inst) * kMaxInst));
   CB(cudaMemset(b->d_insts, 0, sizeof(Inst) * kMaxInst));
   CB(cudaMallocHost(&b->h_insts, sizeof(Inst) * kMaxInst));
-  CB(cudaMalloc(&b->d_lists, sizeof(List) * b->nlists));
-  CB(cudaMallocHost(&b->h_lists, sizeof(List) * b->nlists));
-  std::memset(b->h_lists, 0, sizeof(List) * b->nlists);
-  CB(cudaMemset(b->d_lists, 0, sizeof(List) * b->nlists));
+  CB(cudaMalloc(&b->d_lists, sizeof(List) * b->nlists * kMaxLanes));
+  CB(cudaMallocHost(&b->h_lists, sizeof(List) * b->nlists * kMaxLanes));
+  std::memset(b->h_lists, 0, sizeof(List) * b->nlists * kMaxLanes);
+  CB(cudaMemset(b->d_lists, 0, sizeof(List) * b->nlists * kMaxLanes));
   CB(cudaMalloc(&b->d_rbits, sizeof(unsigned long long) * kMaxInst));
   CB(cudaMalloc(&b->d_dummy, sizeof(unsigned long long) * kMaxInst));
   CB(cudaMallocHost(&b->h_rbits, sizeof(unsigned long long) * kMaxInst));
@@ -628,6 +696,13 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   CB(cudaFuncSetAttribute(kb_bottom<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bottom_smem(3))));
   CB(cudaEventCreate(&b->ev0));
   CB(cudaEventCreate(&b->ev1));
+  for (int q = 0; q < kMaxLanes - 1; ++q) {
+    CB(cudaStreamCreateWithFlags(&b->lane_st[q], cudaStreamNonBlocking));
+    CB(cudaEventCreateWithFlags(&b->ev_join[q], cudaEventDisableTiming));
+  }
+  CB(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  for (int q = 0; q < kNumBase; ++q) b->cands[q] = kBaseShapes[q];
+  b->ncands = kNumBase;
 #undef CB
   *out = b;
   return ISDC_OK;
@@ -639,8 +714,13 @@ ISDC_API void isdc_batch_destroy(isdc_batch* b) {
   for (int i = 0; i < kMaxInst; ++i)
     if (b->slots[i].mem) cudaFreeAsync(b->slots[i].mem, b->stream);
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (int s = 0; s < kNumShapes; ++s)
+  for (int s = 0; s < kMaxCands; ++s)
     if (b->exec[s]) cudaGraphExecDestroy(b->exec[s]);
+  for (int q = 0; q < kMaxLanes - 1; ++q) {
+    if (b->lane_st[q]) cudaStreamDestroy(b->lane_st[q]);
+    if (b->ev_join[q]) cudaEventDestroy(b->ev_join[q]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->d_insts);
   cudaFreeHost(b->h_insts);
   cudaFree(b->d_lists);
@@ -720,61 +800,52 @@ ISDC_API isdc_status isdc_batch_tick(isdc_batch* b, int* running_out, int* finis
     }
   int finished = 0;
   if (running) {
-    // the persistent shapes serve the fused 2D mode only, the programmatic ones
-    // engines with use_graphs == 1; the tuner skips them otherwise
-    while (!b->tuned && !shape_allowed(b, b->tune_next)) {
-      b->tune_rate[b->tune_next] = 0.0;
-      if (++b->tune_next == kNumShapes) break;
-    }
-    if (!b->tuned && b->tune_next == kNumShapes) {
-      int best = 0;
-      for (int s = 1; s < kNumShapes; ++s)
-        if (b->tune_rate[s] > b->tune_rate[best]) best = s;
-      b->shape = best;
-      b->tuned = 1;
+    // the persistent shapes serve the fused 2D mode only; the tuner skips them otherwise
+    for (;;) {
+      while (!b->tuned && b->tune_next < b->ncands && !shape_allowed(b, b->tune_next))
+        b->tune_rate[b->tune_next++] = 0.0;
+      if (b->tuned || b->tune_next < b->ncands) break;
+      tuner_round_done(b);
     }
     int shape = b->tuned ? b->shape : b->tune_next;
     isdc_status st = capture(b, shape);
     if (st != ISDC_OK) return st;
-    build_lists(b, kShapes[shape]);
-    b->last_tick_bytes = tick_bytes(b, kShapes[shape]);
-    B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice, b->stream));
+    auto upload_lists = [&](const Shape& sh) -> isdc_status {
+      build_lists(b, sh);
+      B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists * sh.lanes, cudaMemcpyHostToDevice,
+                               b->stream));
+      return ISDC_OK;
+    };
+    if ((st = upload_lists(b->cands[shape])) != ISDC_OK) return st;
+    b->last_tick_bytes = tick_bytes(b, b->cands[shape]);
     B_TRY(b, cudaEventRecord(b->ev0, b->stream));
     bool skip = false;
     const int tried = shape;
-    if (kShapes[shape].persistent) {
+    if (b->cands[shape].persistent) {
       if ((st = launch_persistent(b, shape, &skip)) != ISDC_OK) return st;
       if (skip) {  // cannot be resident: take the first graph shape for this tick
         shape = 0;
         if ((st = capture(b, shape)) != ISDC_OK) return st;
-        build_lists(b, kShapes[shape]);
-        B_TRY(b, cudaMemcpyAsync(b->d_lists, b->h_lists, sizeof(List) * b->nlists, cudaMemcpyHostToDevice,
-                                 b->stream));
+        if ((st = upload_lists(b->cands[shape])) != ISDC_OK) return st;
       } else {
         b->kernel_launches += 1;
       }
     }
-    if (!kShapes[shape].persistent) {
+    if (!b->cands[shape].persistent) {
       B_TRY(b, cudaGraphLaunch(b->exec[shape], b->stream));
       b->kernel_launches += b->kernel_nodes[shape];
     }
     B_TRY(b, cudaEventRecord(b->ev1, b->stream));
     B_TRY(b, cudaStreamSynchronize(b->stream));
-    if (kShapes[shape].persistent && b->h_gb->err)
+    if (b->cands[shape].persistent && b->h_gb->err)
       return bfail(b, ISDC_ERR_CUDA, "a grid barrier of the persistent tick waited longer than its limit");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
     if (!b->tuned && !b->tune_warm) {
       b->tune_warm = true;  // warm-up tick: not scored, the same shape is tried again next tick
-    } else if (!b->tuned) {  // autotuner: one real tick per launch shape, keep the fastest
+    } else if (!b->tuned) {  // autotuner: one real tick per candidate, keep the fastest
       b->tune_rate[tried] = skip ? 0.0 : dofs / std::max(ms, 1e-3f);
-      if (++b->tune_next == kNumShapes) {
-        int best = 0;
-        for (int s = 1; s < kNumShapes; ++s)
-          if (b->tune_rate[s] > b->tune_rate[best]) best = s;
-        b->shape = best;
-        b->tuned = 1;
-      }
+      if (++b->tune_next == b->ncands) tuner_round_done(b);
     }
     ++b->ticks;
     for (int i = 0; i < kMaxInst; ++i) {
@@ -852,14 +923,15 @@ ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info
   info->kernel_launches = b->kernel_launches;
   info->bytes_in_use = b->used;
   info->tuned = b->tuned;
-  info->threads_per_block = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].threads;
-  info->blocks_per_sm = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].blocks_per_sm;
-  info->fused = tick_mode(b, kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes]) == MODE_FUSED2D;
-  info->programmatic = kShapes[b->tuned ? b->shape : b->tune_next % kNumShapes].programmatic;
+  const Shape& cur = b->cands[b->tuned ? b->shape : b->tune_next % b->ncands];
+  info->threads_per_block = cur.threads;
+  info->blocks_per_sm = cur.blocks_per_sm;
+  info->fused = tick_mode(b, cur) == MODE_FUSED2D;
+  info->lanes = cur.lanes;
   {
-    const int sh = b->tuned ? b->shape : b->tune_next % kNumShapes;
-    info->kernels_per_tick = kShapes[sh].persistent ? 1 : b->kernel_nodes[sh];
-    if (kShapes[sh].persistent) info->blocks_per_sm = b->pers_bps[sh];
+    const int sh = b->tuned ? b->shape : b->tune_next % b->ncands;
+    info->kernels_per_tick = b->cands[sh].persistent ? 1 : b->kernel_nodes[sh];
+    if (b->cands[sh].persistent) info->blocks_per_sm = b->pers_bps[sh];
   }
   info->bytes_last_tick = b->last_tick_bytes;
   int r = 0;

@@ -137,10 +137,11 @@ def test_batch_rbgs_2d_matches_fp64_oracle():
 @pytest.mark.parametrize("ndim", [2, 3])
 def test_batch_launch_shapes_give_identical_results(ndim):
     """An instance admitted into a fresh engine sweeps through the autotuner's
-    trial ticks (every graph shape, then, in 2D damped Jacobi, the persistent
-    one-launch ticks), the same instance admitted after tuning sweeps in the
-    chosen shape only: the results agree bit for bit, so no launch form (nor
-    the rows per tile of the 3D red-black passes) changes the arithmetic."""
+    trial ticks (every graph shape, in 2D damped Jacobi the persistent
+    one-launch ticks, then 2 to 4 lanes), the same instance admitted after
+    tuning sweeps in the chosen shape only, dealt to a lane beside another
+    instance: the results agree bit for bit, so no launch form (nor the rows per
+    tile of the red-black passes, nor the lane) changes the arithmetic."""
     import paper_1401_7824_gb300 as G
     torch_cuda()
     if ndim == 2:
