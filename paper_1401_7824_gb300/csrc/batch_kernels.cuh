@@ -490,21 +490,34 @@ __device__ __forceinline__ FTile fused_tile(const Inst* __restrict__ insts, cons
 }
 
 // Row-structured access to a tile region: warp w takes rows w, w + NW, ...
-// and lane l columns l, l + 32, l + 64 of each, so a row's base address and
-// validity are formed once per row and no index is divided.  Every loop has a
-// compile-time trip count and is unrolled, so a thread's loads of several
-// rows are in flight together.
+// and lane l columns l, l + 32 of each, so a row's base address and validity
+// are formed once per row.  Every loop has a compile-time trip count and is
+// unrolled, so a thread's loads of several rows are in flight together.
+// Regions 64 or more columns wide (the fine tiles with their halos) take
+// their first 64 columns this way, two full lane steps per row, and the 1..32
+// columns beyond as one flattened range over the whole block, so no lane step
+// covers only a few halo columns.
 template <int H, int W, int NW, class Body>
 __device__ __forceinline__ void for_rows(int warp, int lane, const Body& body) {
+  constexpr int WM = W >= 64 ? 64 : W;  // columns walked row by row
 #pragma unroll
   for (int t = 0; t < (H + NW - 1) / NW; ++t) {
     const int r = warp + NW * t;
     if (r < H) {
 #pragma unroll
-      for (int k = 0; k < (W + 31) / 32; ++k) {
+      for (int k = 0; k < (WM + 31) / 32; ++k) {
         const int c = lane + 32 * k;
-        if (c < W) body(r, c);
+        if (c < WM) body(r, c);
       }
+    }
+  }
+  if constexpr (W > 64) {
+    static_assert(W - 64 <= 32, "halo wider than one lane step");
+    constexpr int TW = W - 64, TN = H * TW;
+#pragma unroll
+    for (int e0 = 0; e0 < TN; e0 += 32 * NW) {
+      const int e = e0 + 32 * warp + lane;
+      if (e < TN) body(e / TW, 64 + e % TW);
     }
   }
 }
@@ -674,13 +687,13 @@ __global__ void __launch_bounds__(kBottomThreads)
   pb_bottom<DIM>(insts, list, m, load_x, smoother, nu1, nu2, omega, smem_raw);
 }
 template <int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, 64 / TY)
     kb_down2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int zero) {
   grid_dep_wait();
   pb_down2<TY>(insts, list, m, l, omega, zero);
 }
 template <int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, 64 / TY)
     kb_up2(const Inst* __restrict__ insts, const List* __restrict__ list, int m, int l, float omega, int nu2) {
   grid_dep_wait();
   pb_up2<TY>(insts, list, m, l, omega, nu2);
