@@ -304,7 +304,8 @@ typedef struct {
     int     running;
     int     tuned;              /* 1 once the autotuner has picked the launch shape */
     int     threads_per_block;  /* launch shape in use (tile = one point per thread; the fused 2D
-                                   phases' tile is 32 x threads/32 coarse points) */
+                                   phases' tile is 32 x threads/32 coarse points, the red-black
+                                   phases' tile threads/32 grid rows) */
     int     blocks_per_sm;      /* persistent blocks per SM */
     int     fused;              /* 1: the 2D damped-Jacobi smoother is fused into the transfer
                                    passes (one pass per leg and level); 0: separate phases */
