@@ -187,13 +187,19 @@ def _run_keep(eng, probs, ndim, seed0, ignore=()):
     return out
 
 
-def test_batch_alone_equals_in_the_mix():
-    mix = _engine(2)
-    together = _run(mix, PROBS_2D, 2, 70)
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_batch_alone_equals_in_the_mix(ndim):
+    """Each instance of a mix gives the same result bit for bit as when it runs
+    alone: in the mix it shares work lists and launches with the others and,
+    once the autotuner tries 2 to 4 lanes, is dealt to one of several
+    concurrent chains of the tick graph (3D: red-black row-structured passes)."""
+    probs = PROBS_2D if ndim == 2 else PROBS_3D + [(31, 0.3, 3, 0.05, 1), (31, 0.02, 5, 0.1, 1)]
+    mix = _engine(ndim)
+    together = _run(mix, probs, ndim, 70)
     mix.close()
-    for q, prob in enumerate(PROBS_2D):
-        alone_eng = _engine(2)
-        alone = _run(alone_eng, [prob], 2, 70 + q)
+    for q, prob in enumerate(probs):
+        alone_eng = _engine(ndim)
+        alone = _run(alone_eng, [prob], ndim, 70 + q)
         alone_eng.close()
         np.testing.assert_array_equal(alone[0][0], together[q][0])
         assert alone[0][1] == together[q][1]
