@@ -542,6 +542,7 @@ def run_batch(args):
     line["config"]["fused_smoother"] = int(info.fused)
     line["config"]["kernels_per_tick"] = int(info.kernels_per_tick)
     line["config"]["launch_shape"]["lanes"] = int(info.lanes)
+    line["config"]["launch_shape"]["lane_split"] = int(info.lane_split)
     if args.compare_fp64:
         # the same instances one at a time through the FP64 single-instance path
         tot_dofs, tot_t = 0.0, 0.0

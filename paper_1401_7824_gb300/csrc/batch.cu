@@ -16,8 +16,9 @@
 //
 // Autotuning: the first ticks run with different launch shapes (threads per
 // block = tile size, persistent blocks per SM, one cooperative launch), then
-// with 2..4 lanes of the fastest graph shape; each tick's DOF-sweep rate is
-// measured with events and the fastest shape is kept for the engine's life.
+// with 2..4 lanes of the fastest graph shape, each lane's launches taking all
+// or 1/lanes of its blocks per SM; each tick's DOF-sweep rate is measured with
+// events and the fastest shape is kept for the engine's life.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,16 +67,20 @@ struct Slot {
 // the graph runs concurrently, so one lane's FP64-bound phases overlap another
 // lane's HBM-bound V-cycle phases.  Every shape gives the same result bit for
 // bit, so the autotuner's trial ticks are real sweeps.
+// With split set, each lane's launches take blocks_per_sm / lanes blocks per
+// SM (rounded up), so the lanes' blocks are resident side by side and an
+// FP64-bound phase of one lane shares the SMs with an HBM-bound phase of
+// another; without it every launch takes the whole blocks_per_sm.
 struct Shape {
-  int threads, blocks_per_sm, persistent, lanes;
+  int threads, blocks_per_sm, persistent, lanes, split;
 };
 constexpr int kMaxLanes = 4;
 // the autotuner's first candidates (one lane); lane counts 2..kMaxLanes of the
-// fastest graph shape are appended once these have run
-const Shape kBaseShapes[] = {{256, 8, 0, 1}, {128, 16, 0, 1}, {512, 4, 0, 1}, {256, 16, 0, 1}, {128, 8, 0, 1},
-                             {256, 0, 1, 1}, {512, 0, 1, 1}};
+// fastest graph shape, whole and split, are appended once these have run
+const Shape kBaseShapes[] = {{256, 8, 0, 1, 0}, {128, 16, 0, 1, 0}, {512, 4, 0, 1, 0}, {256, 16, 0, 1, 0},
+                             {128, 8, 0, 1, 0}, {256, 0, 1, 1, 0}, {512, 0, 1, 1, 0}};
 constexpr int kNumBase = int(sizeof(kBaseShapes) / sizeof(kBaseShapes[0]));
-constexpr int kMaxCands = kNumBase + kMaxLanes - 1;
+constexpr int kMaxCands = kNumBase + 2 * (kMaxLanes - 1);
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -332,7 +337,8 @@ void launch_sweep_end(int M, dim3 grid, dim3 blk, cudaStream_t st, const Inst* I
 // lists Ls (inside a capture).
 template <int DIM>
 void record_lane(isdc_batch* b, const Shape& sh, cudaStream_t st, const List* Ls) {
-  const dim3 grid(sh.blocks_per_sm * b->sms), blk(sh.threads);
+  const int bps = sh.split ? (sh.blocks_per_sm + sh.lanes - 1) / sh.lanes : sh.blocks_per_sm;
+  const dim3 grid(bps * b->sms), blk(sh.threads);
   const Inst* I = b->d_insts;
   const int reaction = b->opt.reaction;
   const bool jac = b->opt.smoother == ISDC_SMOOTHER_JACOBI;
@@ -525,11 +531,13 @@ void tuner_round_done(isdc_batch* b) {
     for (int s = 0; s < b->ncands; ++s)
       if (!b->cands[s].persistent && b->tune_rate[s] > 0.0 && (g < 0 || b->tune_rate[s] > b->tune_rate[g])) g = s;
     if (g >= 0) {
-      for (int q = 2; q <= kMaxLanes; ++q) {
-        Shape sh = b->cands[g];
-        sh.lanes = q;
-        b->cands[b->ncands++] = sh;
-      }
+      for (int split = 0; split <= 1; ++split)
+        for (int q = 2; q <= kMaxLanes; ++q) {
+          Shape sh = b->cands[g];
+          sh.lanes = q;
+          sh.split = split;
+          b->cands[b->ncands++] = sh;
+        }
       return;  // tune_next now points at the first lane candidate
     }
   }
@@ -928,6 +936,7 @@ ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info
   info->blocks_per_sm = cur.blocks_per_sm;
   info->fused = tick_mode(b, cur) == MODE_FUSED2D;
   info->lanes = cur.lanes;
+  info->lane_split = cur.split;
   {
     const int sh = b->tuned ? b->shape : b->tune_next % b->ncands;
     info->kernels_per_tick = b->cands[sh].persistent ? 1 : b->kernel_nodes[sh];

@@ -69,7 +69,7 @@ class isdc_batch_info(ctypes.Structure):
                 ("running", ctypes.c_int),
                 ("tuned", ctypes.c_int), ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("fused", ctypes.c_int), ("kernels_per_tick", ctypes.c_int), ("bytes_last_tick", ctypes.c_double),
-                ("lanes", ctypes.c_int)]
+                ("lanes", ctypes.c_int), ("lane_split", ctypes.c_int)]
 
 
 ISDC_SLOT_FREE, ISDC_SLOT_RUNNING, ISDC_SLOT_FINISHED, ISDC_SLOT_FAILED = 0, 1, 2, 3
