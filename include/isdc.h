@@ -315,7 +315,9 @@ typedef struct {
     int     lanes;              /* independent chains of the tick graph in use, each over its own
                                    share of the running instances (run concurrently) */
     int     lane_split;         /* 1: each lane's launches take blocks_per_sm / lanes blocks per SM,
-                                   so the lanes' blocks share the SMs; 0: all blocks_per_sm */
+                                   so the lanes' blocks share the SMs; 2: the same, and lane q
+                                   starts once lane q-1's first right-hand side is done (lanes a
+                                   phase apart); 0: all blocks_per_sm */
 } isdc_batch_info;
 
 /* ndim 2 or 3; max_side: the largest side that will be admitted (sets the
@@ -330,8 +332,8 @@ typedef struct {
  * cooperative launch).  The first ticks try several launch shapes (tile size,
  * blocks per SM, one launch per tick, then 1 to 4 lanes: concurrent chains of
  * the tick graph over disjoint shares of the instances, each with all or
- * 1/lanes of the blocks per SM; all give the same result bit for bit) and keep
- * the fastest (autotuner).
+ * 1/lanes of the blocks per SM, the latter also staggered by a phase; all give
+ * the same result bit for bit) and keep the fastest (autotuner).
  * Errors: INVALID_ARG, OOM, CUDA. */
 isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, size_t hbm_budget_bytes, int n_vcycles,
                               const isdc_options *opt, isdc_batch **out);

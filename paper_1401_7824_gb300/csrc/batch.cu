@@ -17,8 +17,9 @@
 // Autotuning: the first ticks run with different launch shapes (threads per
 // block = tile size, persistent blocks per SM, one cooperative launch), then
 // with 2..4 lanes of the fastest graph shape, each lane's launches taking all
-// or 1/lanes of its blocks per SM; each tick's DOF-sweep rate is measured with
-// events and the fastest shape is kept for the engine's life.
+// or 1/lanes of its blocks per SM, the latter also with staggered lanes; each
+// tick's DOF-sweep rate is measured with events and the fastest shape is kept
+// for the engine's life.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,17 +71,20 @@ struct Slot {
 // With split set, each lane's launches take blocks_per_sm / lanes blocks per
 // SM (rounded up), so the lanes' blocks are resident side by side and an
 // FP64-bound phase of one lane shares the SMs with an HBM-bound phase of
-// another; without it every launch takes the whole blocks_per_sm.
+// another; without it every launch takes the whole blocks_per_sm.  With
+// stagger set, lane q starts once lane q-1's first right-hand-side phase has
+// completed, so the lanes run a phase apart instead of in step.
 struct Shape {
-  int threads, blocks_per_sm, persistent, lanes, split;
+  int threads, blocks_per_sm, persistent, lanes, split, stagger;
 };
 constexpr int kMaxLanes = 4;
 // the autotuner's first candidates (one lane); lane counts 2..kMaxLanes of the
 // fastest graph shape, whole and split, are appended once these have run
-const Shape kBaseShapes[] = {{256, 8, 0, 1, 0}, {128, 16, 0, 1, 0}, {512, 4, 0, 1, 0}, {256, 16, 0, 1, 0},
-                             {128, 8, 0, 1, 0}, {256, 0, 1, 1, 0}, {512, 0, 1, 1, 0}};
+const Shape kBaseShapes[] = {{256, 8, 0, 1, 0, 0}, {128, 16, 0, 1, 0, 0}, {512, 4, 0, 1, 0, 0},
+                             {256, 16, 0, 1, 0, 0}, {128, 8, 0, 1, 0, 0}, {256, 0, 1, 1, 0, 0},
+                             {512, 0, 1, 1, 0, 0}};
 constexpr int kNumBase = int(sizeof(kBaseShapes) / sizeof(kBaseShapes[0]));
-constexpr int kMaxCands = kNumBase + 2 * (kMaxLanes - 1);
+constexpr int kMaxCands = kNumBase + 3 * (kMaxLanes - 1);
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -114,6 +118,7 @@ struct isdc_batch {
   // lanes 1.. of a multi-lane tick graph: their capture streams, fork and join events
   cudaStream_t lane_st[kMaxLanes - 1] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes - 1] = {};
+  cudaEvent_t ev_stage[kMaxLanes - 1] = {};  // lane q's first right-hand side done (staggered lanes)
   long long ticks = 0;
   long long kernel_launches = 0;   // kernel nodes executed by all ticks
   double last_tick_bytes = 0.0;    // algorithmic bytes of the last tick (tick_bytes)
@@ -336,7 +341,7 @@ void launch_sweep_end(int M, dim3 grid, dim3 blk, cudaStream_t st, const Inst* I
 // Record one lane's launches of a tick on stream st, over the lane's work
 // lists Ls (inside a capture).
 template <int DIM>
-void record_lane(isdc_batch* b, const Shape& sh, cudaStream_t st, const List* Ls) {
+void record_lane(isdc_batch* b, const Shape& sh, cudaStream_t st, const List* Ls, cudaEvent_t after_rhs0) {
   const int bps = sh.split ? (sh.blocks_per_sm + sh.lanes - 1) / sh.lanes : sh.blocks_per_sm;
   const dim3 grid(bps * b->sms), blk(sh.threads);
   const Inst* I = b->d_insts;
@@ -353,6 +358,7 @@ void record_lane(isdc_batch* b, const Shape& sh, cudaStream_t st, const List* Ls
   for (int m = 0; m < b->Mmax - 1; ++m) {
     const List* full0 = Ls + list_index(b, m, 0, LK_FULL);
     kb_rhs<DIM><<<grid, blk, 0, st>>>(I, full0, m, reaction);
+    if (m == 0 && after_rhs0) cudaEventRecord(after_rhs0, st);
     int loc0 = 0;  // level-0 error: in x (0) or t (1)
     if (mode != MODE_LEGACY) {
       const int Lg = bottom_level(DIM, b->max_side);
@@ -440,8 +446,12 @@ void record_tick(isdc_batch* b, const Shape& sh) {
     cudaEventRecord(b->ev_fork, st);
     for (int q = 1; q < sh.lanes; ++q) cudaStreamWaitEvent(b->lane_st[q - 1], b->ev_fork, 0);
   }
-  for (int q = 0; q < sh.lanes; ++q)
-    record_lane<DIM>(b, sh, q ? b->lane_st[q - 1] : st, b->d_lists + size_t(q) * b->nlists);
+  for (int q = 0; q < sh.lanes; ++q) {
+    cudaStream_t sq = q ? b->lane_st[q - 1] : st;
+    if (sh.stagger && q > 0) cudaStreamWaitEvent(sq, b->ev_stage[q - 1], 0);
+    record_lane<DIM>(b, sh, sq, b->d_lists + size_t(q) * b->nlists,
+                     sh.stagger && q + 1 < sh.lanes ? b->ev_stage[q] : nullptr);
+  }
   for (int q = 1; q < sh.lanes; ++q) {
     cudaEventRecord(b->ev_join[q - 1], b->lane_st[q - 1]);
     cudaStreamWaitEvent(st, b->ev_join[q - 1], 0);
@@ -531,11 +541,12 @@ void tuner_round_done(isdc_batch* b) {
     for (int s = 0; s < b->ncands; ++s)
       if (!b->cands[s].persistent && b->tune_rate[s] > 0.0 && (g < 0 || b->tune_rate[s] > b->tune_rate[g])) g = s;
     if (g >= 0) {
-      for (int split = 0; split <= 1; ++split)
+      for (int form = 0; form < 3; ++form)  // whole, split, split and staggered
         for (int q = 2; q <= kMaxLanes; ++q) {
           Shape sh = b->cands[g];
           sh.lanes = q;
-          sh.split = split;
+          sh.split = form >= 1;
+          sh.stagger = form == 2;
           b->cands[b->ncands++] = sh;
         }
       return;  // tune_next now points at the first lane candidate
@@ -707,6 +718,7 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   for (int q = 0; q < kMaxLanes - 1; ++q) {
     CB(cudaStreamCreateWithFlags(&b->lane_st[q], cudaStreamNonBlocking));
     CB(cudaEventCreateWithFlags(&b->ev_join[q], cudaEventDisableTiming));
+    CB(cudaEventCreateWithFlags(&b->ev_stage[q], cudaEventDisableTiming));
   }
   CB(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
   for (int q = 0; q < kNumBase; ++q) b->cands[q] = kBaseShapes[q];
@@ -727,6 +739,7 @@ ISDC_API void isdc_batch_destroy(isdc_batch* b) {
   for (int q = 0; q < kMaxLanes - 1; ++q) {
     if (b->lane_st[q]) cudaStreamDestroy(b->lane_st[q]);
     if (b->ev_join[q]) cudaEventDestroy(b->ev_join[q]);
+    if (b->ev_stage[q]) cudaEventDestroy(b->ev_stage[q]);
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->d_insts);
@@ -936,7 +949,7 @@ ISDC_API isdc_status isdc_batch_stats(const isdc_batch* b, isdc_batch_info* info
   info->blocks_per_sm = cur.blocks_per_sm;
   info->fused = tick_mode(b, cur) == MODE_FUSED2D;
   info->lanes = cur.lanes;
-  info->lane_split = cur.split;
+  info->lane_split = cur.split + cur.stagger;
   {
     const int sh = b->tuned ? b->shape : b->tune_next % b->ncands;
     info->kernels_per_tick = b->cands[sh].persistent ? 1 : b->kernel_nodes[sh];

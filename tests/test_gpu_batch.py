@@ -160,7 +160,7 @@ def test_batch_launch_shapes_give_identical_results(ndim):
     fresh.close()
     tuned = engine()
     warm = tuned.admit(warm_n, 0.5, 3, 0.05, 50, initial_condition(ndim, warm_n, 9))
-    for _ in range(20):
+    for _ in range(30):
         tuned.tick()
         if tuned.stats().tuned:
             break
