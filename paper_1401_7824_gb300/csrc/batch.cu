@@ -79,7 +79,8 @@ struct Shape {
 };
 constexpr int kMaxLanes = 4;
 // the autotuner's first candidates (one lane); lane counts 2..kMaxLanes of the
-// fastest graph shape, whole and split, are appended once these have run
+// fastest graph shape, whole, split, and split and staggered, are appended
+// once these have run
 const Shape kBaseShapes[] = {{256, 8, 0, 1, 0, 0}, {128, 16, 0, 1, 0, 0}, {512, 4, 0, 1, 0, 0},
                              {256, 16, 0, 1, 0, 0}, {128, 8, 0, 1, 0, 0}, {256, 0, 1, 1, 0, 0},
                              {512, 0, 1, 1, 0, 0}};
