@@ -67,6 +67,21 @@ def test_workload_initial_dispatch_and_periodic_bump():
     np.testing.assert_array_equal(W.workload_initial(heat), W.initial_condition(2, 31, 3))
 
 
+def test_batch_instances_3d_recipe():
+    """The 3D batch: 32 instances with the 3D request mix's sides (2^j - 1,
+    j in 6..8), red-black V(2,2) settings, seeded and reproducible."""
+    inst = W.batch_instances_3d()
+    assert len(inst) == 32
+    assert {w.n for w in inst} == {63, 127, 255}
+    for w in inst:
+        assert w.ndim == 3 and w.M in (3, 5) and 0.01 <= w.nu <= 1.0 and 0.01 <= w.dt <= 0.1
+        assert (w.smoother, w.nu1, w.nu2, w.n_vcycles) == (1, 2, 2, 2) and w.vcycle_fp32
+    assert len({w.seed for w in inst}) == 32
+    again = W.batch_instances_3d()
+    assert [(w.n, w.nu, w.M, w.dt, w.seed) for w in inst] == [(w.n, w.nu, w.M, w.dt, w.seed) for w in again]
+    assert sum(w.n ** 3 for w in inst) == 167_425_504  # the bench line's dofs_total
+
+
 def test_batch_instances_recipe():
     inst = W.batch_instances()
     assert len(inst) == 256
