@@ -3,8 +3,11 @@
 // Many independent instances (each its own grid side n, nu, M, dt) are swept
 // together: every phase of an SDC sweep is one persistent, grid-stride launch
 // over a work list of (instance, tile) pairs that spans all instances taking
-// part in that phase.  Node state and the SDC update are FP64; the V-cycles
-// run in FP32 on the error equation (defect correction, as in isdc.cu).
+// part in that phase.  A tile is a run of points (one per thread), a 2D tile
+// of coarse points (the fused damped-Jacobi passes) or a few grid rows (the
+// red-black passes, one row per warp).  Node state and the SDC update are
+// FP64; the V-cycles run in FP32 on the error equation (defect correction, as
+// in isdc.cu).
 #pragma once
 #include "sdc_kernels.cuh"
 
