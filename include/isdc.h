@@ -363,6 +363,18 @@ const char *isdc_batch_last_error(const isdc_batch *b);
 
 void isdc_batch_destroy(isdc_batch *b);
 
+/* Self-test of the bounded grid barrier of the one-launch batch tick (no
+ * paper counterpart; failure detection).  One cooperative launch of `blocks`
+ * blocks (all resident) runs two barrier rounds that expect `phantom` more
+ * arrivals than there are blocks.  *failed = 0 when both rounds complete
+ * (phantom = 0), 1 when a wait ran out after limit_s seconds; in that case
+ * every block sets the error flag and returns, the kernel ends normally and
+ * the device stays usable.  Synchronises the device.
+ * Errors: INVALID_ARG (blocks outside [1, 1024] or more than can be resident,
+ * phantom outside [0, 1024], limit_s outside (0, 10], failed NULL; checked
+ * before any device work except the occupancy query), CUDA. */
+isdc_status isdc_batch_barrier_selftest(int blocks, int phantom, double limit_s, int *failed);
+
 /* Per-kernel-class timing (not from the paper: instrumentation for the
  * roofline).  While enabled, every launch of the context is bracketed by CUDA
  * events on its stream, and the algorithmic bytes and floating-point

@@ -729,6 +729,36 @@ ISDC_API isdc_status isdc_batch_create(int ndim, int64_t max_side, int max_M, si
   return ISDC_OK;
 }
 
+ISDC_API isdc_status isdc_batch_barrier_selftest(int blocks, int phantom, double limit_s, int* failed) {
+  if (!failed || blocks < 1 || blocks > 1024 || phantom < 0 || phantom > 1024 || !(limit_s > 0.0 && limit_s <= 10.0))
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG,
+                 "barrier self-test: 1 <= blocks <= 1024, 0 <= phantom <= 1024, 0 < limit_s <= 10");
+  *failed = -1;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_barrier_selftest, 32, 0);
+  if (e != cudaSuccess) return bfail(nullptr, ISDC_ERR_CUDA, "barrier self-test: %s", cudaGetErrorString(e));
+  if (blocks > sms * per_sm)
+    return bfail(nullptr, ISDC_ERR_INVALID_ARG, "barrier self-test: %d blocks cannot all be resident", blocks);
+  GridBarrier* d = nullptr;
+  GridBarrier h{};
+  e = cudaMalloc(&d, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(GridBarrier));
+  if (e == cudaSuccess) {
+    unsigned int ph = unsigned(phantom);
+    unsigned long long ns = (unsigned long long)(limit_s * 1e9);
+    void* args[] = {&d, &ph, &ns};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kb_barrier_selftest), dim3(blocks), dim3(32), args,
+                                    0, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(GridBarrier), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return bfail(nullptr, ISDC_ERR_CUDA, "barrier self-test: %s", cudaGetErrorString(e));
+  *failed = h.err ? 1 : 0;
+  return ISDC_OK;
+}
+
 ISDC_API void isdc_batch_destroy(isdc_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);

@@ -733,7 +733,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Returns false when the tick has failed (a wait ran out here or elsewhere).
-__device__ __forceinline__ bool grid_barrier(GridBarrier* gb) {
+// expected: the arrivals that complete the barrier (gridDim.x in the tick);
+// limit_ns: how long a block waits for them before it sets the error flag.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int expected, unsigned long long limit_ns) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -741,14 +743,14 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* gb) {
     volatile int* verr = &gb->err;
     const unsigned int g0 = *vgen;  // read before arriving: the generation cannot move until we arrive
     __threadfence();
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&gb->count, 1u) == expected - 1) {
       atomicExch(&gb->count, 0u);
       __threadfence();
       atomicAdd(&gb->gen, 1u);
     } else {
       const unsigned long long t0 = global_ns();
       while (*vgen == g0 && !*verr) {
-        if (global_ns() - t0 > kBarrierNs) {
+        if (global_ns() - t0 > limit_ns) {
           atomicExch(&gb->err, 1);
           break;
         }
@@ -792,8 +794,17 @@ __global__ void __launch_bounds__(32 * TY)
       case PH_UP: pb_up2<TY>(insts, L, P.m, P.l, omega, nu2); break;
       default: pb_update<2>(insts, L, P.m, 0); break;
     }
-    if (q + 1 < nphases && !grid_barrier(gb)) return;
+    if (q + 1 < nphases && !grid_barrier(gb, gridDim.x, kBarrierNs)) return;
   }
+}
+
+// Self-test of the bounded barrier (cooperative launch, every block resident):
+// two barrier rounds that expect `phantom` more arrivals than there are
+// blocks.  With phantom = 0 both complete; otherwise every block's wait runs
+// out after limit_ns, the error flag is set and every block returns.
+__global__ void kb_barrier_selftest(GridBarrier* gb, unsigned int phantom, unsigned long long limit_ns) {
+  for (int r = 0; r < 2; ++r)
+    if (!grid_barrier(gb, gridDim.x + phantom, limit_ns)) return;
 }
 
 #undef BATCH_LOOP

@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True):
         "isdc_batch_stats": (I, [_ctx_p, ctypes.POINTER(isdc_batch_info)]),
         "isdc_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
         "isdc_batch_destroy": (None, [_ctx_p]),
+        "isdc_batch_barrier_selftest": (I, [I, I, ctypes.c_double, ctypes.POINTER(I)]),
         "isdc_profile_enable": (I, [_ctx_p, I]),
         "isdc_profile_read": (I, [_ctx_p, ctypes.POINTER(isdc_kernel_stat), I, ctypes.POINTER(I)]),
         "isdc_tuning": (I, [_ctx_p, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),

@@ -105,6 +105,19 @@ def test_host_validation_without_gpu():
     assert e.value.status == G.ISDC_ERR_INVALID_ARG
 
 
+def test_barrier_selftest_arguments_are_refused_before_device_work():
+    """The grid-barrier self-test checks its arguments before any CUDA call."""
+    import paper_1401_7824_gb300 as G
+    lib = G.load()
+    failed = ctypes.c_int(7)
+    for blocks, phantom, limit in [(0, 0, 0.1), (2000, 0, 0.1), (4, -1, 0.1), (4, 2000, 0.1), (4, 0, 0.0),
+                                   (4, 0, 11.0), (4, 0, float("nan"))]:
+        st = lib.isdc_batch_barrier_selftest(blocks, phantom, limit, ctypes.byref(failed))
+        assert st == G.ISDC_ERR_INVALID_ARG, (blocks, phantom, limit)
+    assert lib.isdc_batch_barrier_selftest(4, 0, 0.1, None) == G.ISDC_ERR_INVALID_ARG
+    assert failed.value == 7
+
+
 def test_oversized_grids_and_bad_damping_are_refused_before_device_work():
     """Sides whose hierarchy would need more than 12 multigrid levels (2D 16383,
     32767) and Jacobi damping outside (0, 1] are refused by argument checks that

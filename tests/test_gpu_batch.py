@@ -205,6 +205,28 @@ def test_batch_alone_equals_in_the_mix(ndim):
         assert alone[0][1] == together[q][1]
 
 
+def test_grid_barrier_wait_is_bounded_and_reported():
+    """The one-launch tick's grid barrier never waits without bound: when the
+    arrivals it expects never come (phantom blocks), every block's wait ends
+    after the limit, the failure is reported to the host, and the device is
+    still usable (failure detection without a GPU fault)."""
+    import ctypes
+    import time
+    import paper_1401_7824_gb300 as G
+    torch_cuda()
+    lib = G.load()
+    failed = ctypes.c_int(-1)
+    assert lib.isdc_batch_barrier_selftest(152, 0, 1.0, ctypes.byref(failed)) == G.ISDC_OK and failed.value == 0
+    t0 = time.perf_counter()
+    assert lib.isdc_batch_barrier_selftest(152, 1, 0.05, ctypes.byref(failed)) == G.ISDC_OK and failed.value == 1
+    assert time.perf_counter() - t0 < 5.0
+    assert lib.isdc_batch_barrier_selftest(152, 0, 1.0, ctypes.byref(failed)) == G.ISDC_OK and failed.value == 0
+    eng = _engine(2)  # and an engine still runs
+    got = _run(eng, PROBS_2D[:1], 2, 40)
+    eng.close()
+    assert np.isfinite(got[0][0]).all()
+
+
 def test_batch_budget_admission_is_soft():
     import paper_1401_7824_gb300 as G
     eng = _engine(2, budget=1)
